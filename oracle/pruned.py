@@ -1,0 +1,156 @@
+"""Pruned H.a, the adaption set function and the observables (FP64).
+
+Notation follows Sec. 2.1 and Sec. 2.2.2: a multi-index I = i_1..i_D, the
+active set A is a subset of the direct-product lattice, stored as sorted
+int64 row-major linear indices (last mode fastest).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def strides_of(dims):
+    """Row-major strides of the lattice (last mode has stride 1)."""
+    s = [1] * len(dims)
+    for k in range(len(dims) - 2, -1, -1):
+        s[k] = s[k + 1] * int(dims[k + 1])
+    return s
+
+
+def digits(A, dims):
+    """The multi-index digits i_kappa of every active point, shape (D, N)."""
+    return np.array(np.unravel_index(np.asarray(A, dtype=np.int64), dims),
+                    dtype=np.int64).reshape(len(dims), -1)
+
+
+def lookup(A, keys):
+    """Positions of ``keys`` in the sorted array A and a found-mask."""
+    A = np.asarray(A, dtype=np.int64)
+    pos = np.searchsorted(A, keys)
+    pos_c = np.minimum(pos, max(len(A) - 1, 0))
+    found = (pos < len(A)) & (A[pos_c] == keys) if len(A) else np.zeros(len(keys), bool)
+    return pos_c, found
+
+
+def potential_diag(A, dims, grids, vfunc):
+    """V_II = V(x_I) at every active point (DVR potential is diagonal,
+    Sec. 2.1 and Sec. 2.4)."""
+    dg = digits(A, dims)
+    q = np.stack([np.asarray(grids[k])[dg[k]] for k in range(len(dims))], axis=-1)
+    return vfunc(q)
+
+
+def apply_H(A, psi, dims, Ts, vdiag):
+    """y = P_A H P_A a on the active set, for a DVR Hamiltonian
+    H = sum_kappa T^(kappa) (x) 1 + V with diagonal V (Sec. 2.1, Sec. 2.2.2
+    pruned sets I, J(i), K(i,j); Appendix, last-dimension transform).
+
+    Written as the definition y_I = sum_{J in A} H_IJ a_J: for a kinetic factor
+    along mode kappa, H_IJ = T_{i_kappa j_kappa} when I and J agree in every
+    other digit, so J runs over I[kappa -> j] for j = 0..n_kappa-1 and only the
+    members of A contribute.  ``vdiag`` holds V(x_I) for I in A.
+    """
+    A = np.asarray(A, dtype=np.int64)
+    psi = np.asarray(psi, dtype=np.complex128)
+    y = np.asarray(vdiag, dtype=np.float64) * psi
+    if len(A) == 0:
+        return y
+    dg = digits(A, dims)
+    st = strides_of(dims)
+    for kappa, n in enumerate(dims):
+        T = np.asarray(Ts[kappa], dtype=np.float64)
+        ik = dg[kappa]
+        for j in range(int(n)):
+            target = A + (j - ik) * st[kappa]
+            pos, found = lookup(A, target)
+            y[found] += T[ik[found], j] * psi[pos[found]]
+    return y
+
+
+def neighbour_offsets(axes, radius=1):
+    """The phase-space-ball neighbour rule of Sec. 3.1 on a lattice with the
+    given axes: radius 1 adds +-1 along each lattice axis (2 per axis)."""
+    if radius != 1:
+        raise NotImplementedError("only the radius-1 neighbour rule is built")
+    out = []
+    for a in range(len(axes)):
+        for s in (-1, 1):
+            d = [0] * len(axes)
+            d[a] = s
+            out.append(tuple(d))
+    return out
+
+
+def significant(psi, theta):
+    """The keep-test of Sec. 2.5: |a_I| >= theta, evaluated as
+    fl(fl(re*re) + fl(im*im)) >= fl(theta*theta) in FP64 (FP32 inputs are
+    widened exactly first)."""
+    p = np.asarray(psi).astype(np.complex128)
+    re, im = p.real, p.imag
+    mag2 = re * re + im * im
+    return mag2 >= np.float64(theta) * np.float64(theta)
+
+
+def adapt_set(S, axes, radius=1):
+    """A' = S union N(S) as a sorted array (N: lattice neighbours, clipped at
+    the lattice edges, Sec. 2.5 and Sec. 3.1)."""
+    S = np.asarray(S, dtype=np.int64)
+    if len(S) == 0:
+        return np.zeros(0, np.int64)
+    cand = [S]
+    dg = digits(S, axes)
+    st = strides_of(axes)
+    for off in neighbour_offsets(axes, radius):
+        ok = np.ones(len(S), dtype=bool)
+        delta = 0
+        for a, d in enumerate(off):
+            if d:
+                nd = dg[a] + d
+                ok &= (nd >= 0) & (nd < axes[a])
+                delta += d * st[a]
+        cand.append(S[ok] + delta)
+    return np.unique(np.concatenate(cand))
+
+
+def prune(A, psi, axes, theta, radius=1):
+    """Adaption of Sec. 2.5 (one threshold theta, nearest neighbours of
+    Sec. 3.1).  S = {I in A : |a_I| >= theta};  A' = S union N(S), where N adds
+    the lattice neighbours (clipped at the lattice edges).  Coefficients of
+    members of A that stay are kept; newly added members start at zero.
+
+    ``axes`` are the lattice axes (one per DVR mode, two -- x and p -- per
+    phase-space mode); the row-major linear index over the axes equals the one
+    over the modes.  Returns (A', a').
+    """
+    A = np.asarray(A, dtype=np.int64)
+    psi = np.asarray(psi)
+    Anew = adapt_set(A[significant(psi, theta)], axes, radius)
+    pos, found = lookup(A, Anew)
+    out = np.zeros(len(Anew), dtype=psi.dtype if psi.dtype.kind == "c" else np.complex128)
+    out[found] = psi[pos[found]]
+    return Anew, out
+
+
+def packet_factors(grids, weights, q0, p0, width, gfunc):
+    """Per-mode coefficient vectors of a product packet, a^k_i =
+    sqrt(w_i) g_k(x_i) (DVR projection, Sec. 2.1), each normalised; the
+    normalised full-lattice packet is their direct product."""
+    out = []
+    for k in range(len(grids)):
+        v = np.sqrt(np.asarray(weights[k])) * gfunc(np.asarray(grids[k]), q0[k], p0[k], width[k])
+        out.append(v / np.linalg.norm(v))
+    return out
+
+
+def product_on(A, dims, factors):
+    """The product state prod_k f^k_{i_k} at the active points."""
+    dg = digits(A, dims)
+    v = np.ones(len(dg[0]) if len(dims) else 0, dtype=np.complex128)
+    for k in range(len(dims)):
+        v = v * np.asarray(factors[k])[dg[k]]
+    return v
+
+
+def autocorrelation(A, psi, a0_on_A):
+    """C(t) = <Psi(0)|Psi(t)> = sum_{I in A(t)} conj(a0_I) a_I(t) (Eq. acorr)."""
+    return np.vdot(a0_on_A, np.asarray(psi, dtype=np.complex128))

@@ -1,0 +1,306 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix:
+closed forms, library routines of a different construction, dense brute
+force on tiny lattices.  Each test names the mistake it would catch."""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import workloads as W
+from oracle import bases, models, pruned, sil, propagate
+
+
+# ---------------------------------------------------------------- 1D bases
+
+def test_sine_dvr_free_particle_levels():
+    # Closed form: a particle in a box of length L has E_k = (k pi / L)^2 / 2m,
+    # and the sine DVR is exact for it for k <= n (catches a wrong U, L or m).
+    for n, lo, hi, m in [(32, 0.5, 6.0, 1836.0), (7, -1.0, 2.5, 1.0)]:
+        x, w, T = bases.sine_dvr(n, lo, hi, m)
+        L = hi - lo
+        ev = np.linalg.eigvalsh(T)
+        ref = (np.arange(1, n + 1) * np.pi / L) ** 2 / (2 * m)
+        np.testing.assert_allclose(ev, ref, rtol=1e-12)
+        assert np.all(np.diff(x) > 0) and x[0] > lo and x[-1] < hi
+        np.testing.assert_allclose(np.diff(x), L / (n + 1), rtol=1e-12)
+        np.testing.assert_allclose(T, T.T, atol=0)
+
+
+def test_ho_dvr_levels_fig1_setup():
+    # Fig. 1 setup, H = (-d^2/dx^2 + x^2)/2: levels n + 1/2 (closed form).
+    # With a different m and omega: omega (n + 1/2) for V = m omega^2 x^2 / 2.
+    # (x^2 at the nodes differs from the FBR x^2 only in the top basis
+    # function, so the lower half of the spectrum is exact.)
+    for n, m, om in [(100, 1.0, 1.0), (24, 2.0, 0.5)]:
+        x, w, T = bases.ho_dvr(n, m, om)
+        ev = np.linalg.eigvalsh(T + np.diag(0.5 * m * om * om * x * x))
+        ref = om * (np.arange(n) + 0.5)
+        np.testing.assert_allclose(ev[:n // 2], ref[:n // 2], rtol=1e-11, atol=1e-12)
+        if n == 100:
+            # the first 42 states of Fig. 1
+            np.testing.assert_allclose(ev[:42], ref[:42], rtol=1e-12)
+
+
+def test_ho_dvr_nodes_weights_vs_gauss_hermite():
+    # The HO DVR for m = omega = 1 is the Gauss-Hermite quadrature: nodes are
+    # the roots of H_n and sqrt-weights turn grid values into coefficients:
+    # w_i = W_i exp(x_i^2) with W_i the Gauss-Hermite weights (numpy builds
+    # them by a different route).
+    n = 24
+    x, w, T = bases.ho_dvr(n)
+    gx, gw = np.polynomial.hermite.hermgauss(n)
+    np.testing.assert_allclose(x, gx, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(w, gw * np.exp(gx * gx), rtol=1e-10)
+
+
+def test_sine_dvr_morse_levels():
+    # Textbook Morse levels E_n = w(n+1/2) - [w(n+1/2)]^2/(4 De),
+    # w = a sqrt(2 De / m): catches a wrong mass or potential in the DVR.
+    De, a, m = 0.1, 1.0, 1836.0
+    x, w, T = bases.sine_dvr(96, 0.5, 6.0, m)
+    V = models.coupled_morse(x[:, None], De, a, 2.0, 0.0)
+    ev = np.linalg.eigvalsh(T + np.diag(V))
+    om = a * np.sqrt(2 * De / m)
+    nn = np.arange(6) + 0.5
+    ref = om * nn - (om * nn) ** 2 / (4 * De)
+    np.testing.assert_allclose(ev[:6], ref, rtol=1e-8)
+
+
+def test_henon_heiles_saddle():
+    # 2D Henon-Heiles: saddle at (0, 1/lam) with V = 1/(6 lam^2), zero
+    # gradient (catches a wrong sign or power in the cubic terms).
+    lam = 0.111803
+    q = np.array([0.0, 1.0 / lam])
+    assert abs(models.henon_heiles(q, lam) - 1 / (6 * lam ** 2)) < 1e-9
+    for qs in ([0.0, 1 / lam], [np.sqrt(3) / (2 * lam), -1 / (2 * lam)]):
+        qs = np.array(qs)
+        g = []
+        for k in range(2):
+            e = np.zeros(2); e[k] = 1e-5
+            g.append((models.henon_heiles(qs + e, lam) - models.henon_heiles(qs - e, lam)) / 2e-5)
+        np.testing.assert_allclose(g, 0, atol=1e-6)
+        assert abs(models.henon_heiles(qs, lam) - 1 / (6 * lam ** 2)) < 1e-9
+
+
+# ------------------------------------------------------------ pruned H.a
+
+def _dense_H(dims, Ts, vfull):
+    """Brute force H = sum_k 1 (x) .. T_k .. (x) 1 + diag(V) by Kronecker
+    products (row-major: mode 0 is the slowest index)."""
+    N = int(np.prod(dims))
+    H = np.diag(vfull).astype(np.float64)
+    for k in range(len(dims)):
+        mats = [np.eye(d) for d in dims]
+        mats[k] = Ts[k]
+        M = mats[0]
+        for mm in mats[1:]:
+            M = np.kron(M, mm)
+        H += M
+    assert H.shape == (N, N)
+    return H
+
+
+@pytest.mark.parametrize("dims,frac,seed", [((6, 5), 0.5, 1), ((4, 5, 3), 0.4, 2),
+                                            ((3, 2, 4, 3), 0.6, 3), ((9,), 0.7, 4),
+                                            ((4, 5, 3), 1.0, 5)])
+def test_pruned_apply_equals_PHP(dims, frac, seed):
+    # y = P_A H P_A a exactly for a DVR (diagonal V), and A = full gives the
+    # unpruned H (Sec. 2.2.2 / appendix).  Catches a transposed T, a wrong
+    # stride or digit, or a dropped mode.
+    rng = np.random.default_rng(seed)
+    Ts = []
+    for d in dims:
+        M = rng.standard_normal((d, d))
+        Ts.append(M)                      # non-symmetric: catches T vs T^T
+    N = int(np.prod(dims))
+    vfull = rng.standard_normal(N)
+    A = W.random_active_set(dims, frac, seed)
+    psi = W.random_psi(len(A), seed + 10)
+    y = pruned.apply_H(A, psi, dims, Ts, vfull[A])
+    H = _dense_H(dims, Ts, vfull)
+    ref = H[np.ix_(A, A)] @ psi
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_pruned_apply_empty():
+    y = pruned.apply_H(np.zeros(0, np.int64), np.zeros(0, complex), (3, 4),
+                       [np.eye(3), np.eye(4)], np.zeros(0))
+    assert y.shape == (0,)
+
+
+# ------------------------------------------------------------------ prune
+
+def _brute_prune(A, psi, axes, theta):
+    """Every lattice point L is tested directly against the rule of Sec. 2.5:
+    L is kept iff L itself or one of its +-1 axis neighbours is an active
+    point with |a| >= theta."""
+    Aset = {int(i): k for k, i in enumerate(A)}
+    big = {int(i) for k, i in enumerate(A) if abs(complex(psi[k])) ** 2 >= theta * theta}
+    out, coef = [], []
+    for L in range(int(np.prod(axes))):
+        dig = np.unravel_index(L, axes)
+        keep = L in big
+        for a in range(len(axes)):
+            for s in (-1, 1):
+                d = list(dig); d[a] += s
+                if 0 <= d[a] < axes[a] and int(np.ravel_multi_index(d, axes)) in big:
+                    keep = True
+        if keep:
+            out.append(L)
+            coef.append(psi[Aset[L]] if L in Aset else 0)
+    return np.array(out, dtype=np.int64), np.array(coef, dtype=complex)
+
+
+@pytest.mark.parametrize("axes,seed", [((7, 6), 0), ((4, 3, 5), 1), ((2, 2, 2, 3), 2), ((11,), 3)])
+def test_prune_bruteforce(axes, seed):
+    rng = np.random.default_rng(seed)
+    A = W.random_active_set(axes, 0.5, seed)
+    theta = 0.3
+    psi = (rng.uniform(0, 0.6, len(A)) * np.exp(2j * np.pi * rng.random(len(A))))
+    # exact ties |a| = theta (real, representable) must be kept
+    psi[::5] = theta
+    An, pn = pruned.prune(A, psi, axes, theta)
+    Ab, pb = _brute_prune(A, psi, axes, theta)
+    np.testing.assert_array_equal(An, Ab)
+    np.testing.assert_array_equal(pn, pb)
+
+
+def test_prune_edges_and_empty():
+    # one significant point in a corner: only in-lattice neighbours are added
+    An, pn = pruned.prune(np.array([0]), np.array([1.0 + 0j]), (3, 4), 0.5)
+    np.testing.assert_array_equal(An, [0, 1, 4])
+    np.testing.assert_array_equal(pn, [1, 0, 0])
+    An, pn = pruned.prune(np.array([0, 5]), np.array([0.1, 0.2 + 0j]), (3, 4), 0.5)
+    assert len(An) == 0 and len(pn) == 0
+
+
+# -------------------------------------------------------------------- SIL
+
+def test_sil_full_krylov_is_exact_exponential():
+    # K = dim: the Krylov space is the whole space and SIL is exp(-iH dt)
+    # (catches a wrong sign of i, a wrong e_1 column, bad re-orthogonalisation).
+    rng = np.random.default_rng(7)
+    n = 12
+    M = rng.standard_normal((n, n)); H = (M + M.T) / 2
+    psi = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    for dt in (0.05, 0.7):
+        out, info = sil.sil_step(psi, lambda v: H @ v, n, dt, return_info=True)
+        ref = scipy.linalg.expm(-1j * H * dt) @ psi
+        np.testing.assert_allclose(out, ref, rtol=1e-11, atol=1e-11)
+
+
+def test_sil_conserves_norm_and_energy():
+    rng = np.random.default_rng(8)
+    n = 40
+    M = rng.standard_normal((n, n)); H = (M + M.T) / 2
+    psi = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    out = sil.sil_step(psi, lambda v: H @ v, 6, 0.1)
+    assert abs(np.linalg.norm(out) - np.linalg.norm(psi)) < 1e-12 * np.linalg.norm(psi)
+    e0 = np.vdot(psi, H @ psi).real / np.vdot(psi, psi).real
+    e1 = np.vdot(out, H @ out).real / np.vdot(out, out).real
+    assert abs(e1 - e0) < 1e-12 * max(1, abs(e0))
+
+
+def test_sil_breakdown_invariant_subspace():
+    # psi in a 3-dim invariant subspace: Lanczos stops at 3 vectors and is exact
+    rng = np.random.default_rng(9)
+    n = 10
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.arange(n, dtype=float)
+    H = Q @ np.diag(lam) @ Q.T
+    psi = Q[:, :3] @ np.array([1.0, 2.0, 0.5])
+    out, info = sil.sil_step(psi, lambda v: H @ v, 8, 0.3, return_info=True)
+    assert info["K"] == 3
+    np.testing.assert_allclose(out, scipy.linalg.expm(-1j * H * 0.3) @ psi, atol=1e-12)
+
+
+# ------------------------------------------------------- whole propagation
+
+def _dense_problem_H(prob):
+    dims = prob.dims
+    full = np.arange(int(np.prod(dims)), dtype=np.int64)
+    return _dense_H(dims, prob.Ts, prob.vdiag(full))
+
+
+def test_theta0_is_unpruned_exact_dynamics():
+    # theta = 0: the active set is the full lattice at all times and the pruned
+    # run is the exact direct-product propagation (Sec. 3.1: at 100 % basis
+    # all methods agree).  K = dim makes SIL exact, so the run must equal
+    # exp(-i H t) a(0) by dense exponential.
+    cfg = W.scaled(W.MORSE2D, n=6)
+    prob = propagate.problem_from_config(cfg)
+    N = 36
+    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], 0.0, N, 10.0, 5)
+    assert all(o["n_active"] == N for o in r["obs"])
+    H = _dense_problem_H(prob)
+    a0 = pruned.product_on(np.arange(N), prob.dims, r["factors"])
+    ref = scipy.linalg.expm(-1j * H * 50.0) @ a0
+    np.testing.assert_allclose(r["a"], ref, rtol=1e-10, atol=1e-11)
+    # C(t) at every step
+    for s, o in enumerate(r["obs"]):
+        c = np.vdot(a0, scipy.linalg.expm(-1j * H * 10.0 * s) @ a0)
+        assert abs(o["C"] - c) < 1e-10
+
+
+def test_autocorrelation_2t_identity():
+    # Eq. acorr: for a real initial packet in a real DVR, C(2t) = sum_I a_I(t)^2.
+    cfg = W.scaled(W.MORSE2D, n=6)
+    prob = propagate.problem_from_config(cfg)
+    r = propagate.run(prob, cfg["q0"], (0.0, 0.0), cfg["width"], 0.0, 36, 10.0, 6)
+    # re-run keeping the states
+    A, a, f = propagate.initial_state(prob, cfg["q0"], (0.0, 0.0), cfg["width"], 0.0)
+    states = [a]
+    for _ in range(3):
+        a = sil.sil_step(a, lambda v: prob.apply(A, v), 36, 10.0)
+        states.append(a)
+    for s in range(4):
+        assert abs(r["obs"][2 * s]["C"] - np.sum(states[s] ** 2)) < 1e-11
+
+
+def test_hh_lambda0_coherent_state_closed_form():
+    # lambda = 0: the HH chain is a sum of HO, the packet at q0 = 2 with
+    # standard deviation 1/sqrt 2 is a coherent state, and
+    # C(t) = prod_k exp(-it/2) exp(-(q0^2/2)(1 - exp(-it))).
+    cfg = W.scaled(W.HH4D, D=2, lam=0.0)
+    prob = propagate.problem_from_config(cfg)
+    q0 = (2.0, 2.0)
+    # K = 16 makes the Krylov error negligible (the DVR is exact to 1e-15 for
+    # this packet); K = 10, the workload's order, stays within 1e-9 over 40
+    # steps (its per-step truncation error is about 1e-11).
+    for K, tol in ((16, 1e-13), (10, 1e-9)):
+        r = propagate.run(prob, q0, (0.0, 0.0), cfg["width"], 0.0, K, 0.1, 40)
+        for s, o in enumerate(r["obs"]):
+            t = 0.1 * s
+            ref = np.prod([np.exp(-0.5j * t) * np.exp(-(q * q / 2) * (1 - np.exp(-1j * t)))
+                           for q in q0])
+            assert abs(o["C"] - ref) < tol, (K, s, o["C"], ref)
+
+
+def test_initial_state_chunked_equals_full_prune():
+    cfg = W.MORSE2D
+    prob = propagate.problem_from_config(cfg)
+    A, a, f = propagate.initial_state(prob, cfg["q0"], cfg["p0"], cfg["width"], 1e-6, chunk=100)
+    full = np.arange(32 * 32)
+    Af, af = pruned.prune(full, pruned.product_on(full, prob.dims, f), prob.dims, 1e-6)
+    np.testing.assert_array_equal(A, Af)
+    np.testing.assert_array_equal(a, af)
+    assert abs(np.sum(np.abs(pruned.product_on(full, prob.dims, f)) ** 2) - 1) < 1e-13
+
+
+def test_pruned_infidelity_decreases_with_theta():
+    # Sec. 3.1 (Fig. 2/3 trend): a smaller threshold gives a larger basis and
+    # a smaller autocorrelation error against the unpruned run.
+    cfg = W.scaled(W.MORSE2D, n=16)
+    prob = propagate.problem_from_config(cfg)
+    args = (cfg["q0"], cfg["p0"], cfg["width"])
+    exact = propagate.run(prob, *args, 0.0, 8, 10.0, 30)
+    ce = np.array([o["C"] for o in exact["obs"]])
+    errs, sizes = [], []
+    for th in (1e-2, 1e-3, 1e-4, 1e-5):
+        r = propagate.run(prob, *args, th, 8, 10.0, 30)
+        c = np.array([o["C"] for o in r["obs"]])
+        errs.append(np.linalg.norm(c - ce))
+        sizes.append(np.mean([o["n_active"] for o in r["obs"]]))
+    assert all(np.diff(errs) < 0), errs
+    assert all(np.diff(sizes) > 0), sizes

@@ -1,0 +1,101 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and bench.py.
+
+This module holds plain parameter records and random-number draws only: it
+contains none of the method's arithmetic (no basis construction, no
+Hamiltonian, no propagation, no prune rule).  Both the CUDA library and the
+oracle consume what it returns, each through its own code.
+
+Workloads (parameters in atomic units unless stated):
+
+* ``morse2d`` -- 2D coupled Morse, sine-DVR 32 points per mode on the box
+  [0.5, 6] bohr, m = 1836, D = 0.1, a = 1, coupling 0.005 q1 q2, Gaussian
+  packet at (2.3, 2.3) with position standard deviation 0.2, SIL order 8,
+  dt = 10, 200 steps, threshold 1e-6, FP64.
+* ``hh4d`` -- 4D Henon-Heiles chain, lambda = 0.111803, HO-DVR 24 points per
+  mode (hbar = m = omega = 1), coherent packet at q_k = 2 (standard deviation
+  1/sqrt 2), SIL order 10, dt = 0.1, 1000 steps, threshold 1e-7.
+* ``hh6d`` -- the same chain in 6D (24^6 = 1.91e8 lattice points), threshold
+  1e-6, 500 steps; the throughput workload.
+* ``morse3d`` -- 3D coupled Morse (pairwise 0.005 q_i q_j), 64-point sine-DVR
+  per mode, phase-space lattices of 8 x 8 per mode, seed-drawn packet centres.
+* ``adjoint4d`` -- the hh4d model, T = 20, checkpoint every 25 steps.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+MORSE2D = dict(
+    name="morse2d", D=2, basis="sine", n=32, xmin=0.5, xmax=6.0, mass=1836.0,
+    morse_D=0.1, morse_a=1.0, morse_qe=2.0, coupling=0.005,
+    q0=(2.3, 2.3), p0=(0.0, 0.0), width=(0.2, 0.2),
+    K=8, dt=10.0, nsteps=200, theta=1e-6, radius=1,
+)
+
+HH4D = dict(
+    name="hh4d", D=4, basis="ho", n=24, mass=1.0, omega=1.0, lam=0.111803,
+    q0=(2.0,) * 4, p0=(0.0,) * 4, width=(0.5 ** 0.5,) * 4,
+    K=10, dt=0.1, nsteps=1000, theta=1e-7, radius=1,
+)
+
+HH6D = dict(
+    name="hh6d", D=6, basis="ho", n=24, mass=1.0, omega=1.0, lam=0.111803,
+    q0=(2.0,) * 6, p0=(0.0,) * 6, width=(0.5 ** 0.5,) * 6,
+    K=10, dt=0.1, nsteps=500, theta=1e-6, radius=1,
+)
+
+MORSE3D = dict(
+    name="morse3d", D=3, basis="sine", n=64, xmin=0.5, xmax=6.0, mass=1836.0,
+    morse_D=0.1, morse_a=1.0, morse_qe=2.0, coupling=0.005,
+    nx_lattice=8, np_lattice=8, width=(0.2,) * 3, p0=(0.0,) * 3,
+    K=10, dt=10.0, nsteps=400, theta=1e-6, radius=1, seed=1606,
+)
+
+ADJOINT4D = dict(HH4D, name="adjoint4d", nsteps=200, ckpt_every=25)
+
+CONFIGS = {c["name"]: c for c in (MORSE2D, HH4D, HH6D, MORSE3D, ADJOINT4D)}
+
+
+def morse3d_centres(seed: int = 1606) -> tuple:
+    """Packet centres of the 3D Morse workload: q0_k ~ U[2.1, 2.5] (PCG64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return tuple(float(v) for v in rng.uniform(2.1, 2.5, size=3))
+
+
+def scaled(cfg: dict, **over) -> dict:
+    """A copy of a workload record with some fields replaced (smaller cases)."""
+    out = dict(cfg)
+    out.update(over)
+    return out
+
+
+def random_psi(n: int, seed: int, dtype=np.complex128) -> np.ndarray:
+    """Complex standard-normal coefficients (PCG64), one per active point."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    return v.astype(dtype)
+
+
+def random_active_set(dims, frac: float, seed: int) -> np.ndarray:
+    """Sorted int64 linear indices (row-major, last mode fastest) of a random
+    subset of the direct-product lattice, each point kept with probability
+    ``frac``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    total = int(np.prod(dims))
+    keep = rng.random(total) < frac
+    return np.flatnonzero(keep).astype(np.int64)
+
+
+def ellipsoid_active_set(dims, radii, centre=None) -> np.ndarray:
+    """Sorted int64 linear indices of the lattice points inside the ellipsoid
+    sum_k ((i_k - c_k) / r_k)^2 <= 1 (the shape a Gaussian packet's active set
+    takes); ``centre`` defaults to the lattice centre."""
+    dims = tuple(int(d) for d in dims)
+    if centre is None:
+        centre = [(d - 1) / 2.0 for d in dims]
+    acc = np.zeros(dims, dtype=np.float64)
+    for k, d in enumerate(dims):
+        shape = [1] * len(dims)
+        shape[k] = d
+        g = ((np.arange(d) - centre[k]) / radii[k]) ** 2
+        acc = acc + g.reshape(shape)
+    return np.flatnonzero(acc.ravel() <= 1.0).astype(np.int64)
