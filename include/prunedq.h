@@ -1,0 +1,238 @@
+/*
+ * prunedq.h -- C ABI of the GB300 (sm_103a) pruned quantum-dynamics library.
+ *
+ * The library propagates a wavepacket that lives only on an active, non
+ * direct-product subset A of a direct-product basis (Larsson, Hartke, Tannor,
+ * arXiv:1606.04004).  A sum-of-products (SoP) Hamiltonian acts along the
+ * partial fibres of A (Sec. 2.2.2, Appendix), inside short-iterative-Lanczos
+ * steps (Sec. 3.1), and after each step a threshold prune plus a
+ * nearest-neighbour add rebuilds A (Sec. 2.5).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a pq_status; PQ_OK is 0.  No C++ exception crosses
+ *    the ABI.  pq_last_error() gives a message for the last failing call of
+ *    the calling thread.
+ *  - A lattice point is named by its row-major linear index (mode 0 slowest,
+ *    mode D-1 contiguous).  A is kept sorted by that index.  The product of
+ *    the mode sizes must be below 2^32 and every mode size at most 64.
+ *  - Coefficient vectors are complex, interleaved (re, im): double pairs for
+ *    PQ_FP64, float pairs for PQ_FP32MIX.  Vectors passed to the library as
+ *    "device" pointers live in device memory of the current CUDA device and
+ *    stay owned by the caller; the library never frees them.
+ *  - `stream` is a cudaStream_t handle passed as void*; NULL means the
+ *    legacy default stream.  Calls that take a stream enqueue their work on
+ *    it and return without synchronising unless stated.
+ *  - Objects (pq_basis, pq_state) are owned by the library; free them with
+ *    the matching *_free call.  They are not thread-safe: one host thread
+ *    (and one stream) at a time per object.
+ */
+#ifndef PRUNEDQ_H
+#define PRUNEDQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pq_status {
+    PQ_OK = 0,
+    PQ_EINVAL = 1,      /* bad argument (shape, size, range, null pointer)   */
+    PQ_ENOMEM = 2,      /* host or device allocation failed                   */
+    PQ_ECUDA = 3,       /* a CUDA runtime call failed                         */
+    PQ_ECAPACITY = 4,   /* the active set outgrew the state's capacity        */
+    PQ_ENUMERIC = 5,    /* NaN / Inf met in a norm or Lanczos coefficient     */
+    PQ_ETIMEOUT = 6,    /* a bounded device wait ran out                      */
+    PQ_EBREAKDOWN = 7,  /* Lanczos breakdown where it is not allowed          */
+    PQ_ENOTSUP = 8      /* valid request that this build does not implement   */
+} pq_status;
+
+typedef enum pq_basis_kind {
+    PQ_SINE_DVR = 0,  /* sine DVR on a box (Sec. 2.2: admissible non-periodic DVR) */
+    PQ_HO_DVR = 1,    /* harmonic-oscillator (Gauss-Hermite) DVR (Sec. 3.3)       */
+    PQ_PVB = 2,       /* biorthogonal projected von Neumann basis (Sec. 2.2)      */
+    PQ_PW = 3         /* projected Weylets (Sec. 2.4)                             */
+} pq_basis_kind;
+
+typedef enum pq_precision {
+    PQ_FP64 = 0,      /* complex FP64 storage and arithmetic                      */
+    PQ_FP32MIX = 1    /* complex FP32 H.psi, FP64 Lanczos scalars, norms and sums */
+} pq_precision;
+
+/* One mode of the direct-product basis.
+ *  kind   pq_basis_kind (this build: PQ_SINE_DVR, PQ_HO_DVR).
+ *  n      number of DVR points (2..64).
+ *  xmin, xmax  box edges of the sine DVR (points at xmin + j L/(n+1), j=1..n).
+ *  mass   mass in the kinetic energy -d^2/dx^2 / (2 mass).
+ *  omega  frequency of the HO-DVR's underlying oscillator (with `mass`).
+ *  nx_lattice, np_lattice  phase-space lattice of pvB / pW modes (unused for DVRs).
+ */
+typedef struct pq_mode_desc {
+    int kind;
+    int n;
+    double xmin, xmax;
+    double mass;
+    double omega;
+    int nx_lattice, np_lattice;
+} pq_mode_desc;
+
+typedef struct pq_basis pq_basis;
+typedef struct pq_state pq_state;
+
+/* Build the per-mode 1D bases (Sec. 2.1 direct-product expansion; DVR grid
+ * points x_j, weights w_j with a_j = sqrt(w_j) psi(x_j), and kinetic matrices).
+ * Host-only FP64 work.  *out is owned by the library: free with pq_basis_free.
+ * Errors: PQ_EINVAL for D outside 1..8, n outside 2..64, a lattice of 2^32
+ * points or more, or a kind this build does not provide (PQ_ENOTSUP). */
+pq_status pq_build_basis(const pq_mode_desc* modes, int D, pq_basis** out);
+void pq_basis_free(pq_basis* basis);
+
+/* Copy mode `mode`'s grid points and weights (n doubles each; either pointer
+ * may be NULL) or its kinetic matrix (n*n doubles, row-major) to host memory. */
+pq_status pq_basis_grid(const pq_basis* basis, int mode, double* x, double* w);
+pq_status pq_basis_kinetic(const pq_basis* basis, int mode, double* T);
+
+/* Sum-of-products Hamiltonian H = sum_l coef_l (x)_kappa h^(kappa,l)
+ * (Sec. 2.2.2).  Each term gives one factor per mode:
+ *   PQ_FACTOR_IDENTITY  the unit matrix;
+ *   PQ_FACTOR_KINETIC   the mode's kinetic matrix;
+ *   PQ_FACTOR_DIAG      a diagonal (potential) factor given by its n values
+ *                       at the DVR points (copied).
+ * In a DVR basis the potential is diagonal (Sec. 2.1), so a term is either
+ * kinetic (one KINETIC factor, IDENTITY elsewhere) or potential (only DIAG /
+ * IDENTITY factors).  Other combinations return PQ_ENOTSUP.  At most 64
+ * potential terms.  Replaces any previous SoP of the basis. */
+typedef enum pq_factor_kind {
+    PQ_FACTOR_IDENTITY = 0,
+    PQ_FACTOR_KINETIC = 1,
+    PQ_FACTOR_DIAG = 2
+} pq_factor_kind;
+
+typedef struct pq_factor {
+    int kind;              /* pq_factor_kind                               */
+    const double* values;  /* n values for PQ_FACTOR_DIAG, else ignored     */
+} pq_factor;
+
+typedef struct pq_sop_term {
+    double coef;
+    const pq_factor* factors;  /* D entries, one per mode                  */
+} pq_sop_term;
+
+pq_status pq_set_sop(pq_basis* basis, const pq_sop_term* terms, int nterms);
+
+/* Create a state holding a product Gaussian packet
+ *   psi(q) = prod_k (2 pi w_k^2)^(-1/4) exp(-(q_k-q0_k)^2/(4 w_k^2) + i p0_k (q_k-q0_k))
+ * projected on the DVR (a_I = prod_k sqrt(w_{i_k}) psi_k(x_{i_k}), each mode
+ * normalised, so ||a|| = 1 on the full lattice), followed by the initial
+ * adaption of Sec. 2.5 with threshold `theta` and neighbour radius `radius`
+ * (this build: 1).  q0, p0, width: D doubles each (host).  `capacity` is the
+ * largest active-set size the state can hold (0 = the full lattice); device
+ * memory for the Krylov space is taken when pq_propagate first needs it.
+ * The state keeps the normalised full-lattice packet (as its D factors) as
+ * Psi(0) for the autocorrelation.  The basis must outlive the state.
+ * Synchronises the device.  Errors: PQ_EINVAL, PQ_ENOMEM, PQ_ECAPACITY. */
+pq_status pq_init_packet(const pq_basis* basis, const double* q0, const double* p0,
+                         const double* width, double theta, int radius, int precision,
+                         size_t capacity, pq_state** out);
+void pq_state_free(pq_state* state);
+
+/* Replace the state's active set and coefficients (host arrays): `idx` holds
+ * n sorted, distinct linear indices, `psi` n complex values of the state's
+ * precision (may be NULL: zeros).  Synchronises.  PQ_EINVAL if idx is not
+ * strictly increasing or out of the lattice, PQ_ECAPACITY if n > capacity. */
+pq_status pq_state_load(pq_state* state, const int64_t* idx, int64_t n, const void* psi);
+
+/* Number of active points (synchronises the device). */
+pq_status pq_state_size(const pq_state* state, int64_t* n_active);
+
+/* Copy the active set (n_active int64 linear indices) and / or the
+ * coefficients (n_active complex values of the state's precision) to host
+ * memory; either pointer may be NULL.  Synchronises. */
+pq_status pq_state_read(const pq_state* state, int64_t* idx, void* psi);
+
+/* Device address of the state's coefficient vector (valid until the next
+ * call that changes the active set). */
+pq_status pq_state_psi_device(const pq_state* state, void** psi);
+
+/* Pruned H.psi on the state's current active set (Sec. 2.2.2 pruned
+ * sequential transform; Appendix, fibre transform over one mode at a time):
+ *   out_I = sum_kappa sum_{j : I[kappa->j] in A} T^kappa_{i_kappa j} in_{I[kappa->j]}
+ *           + V(x_I) in_I,     I in A,
+ * which equals P_A H P_A in for a DVR Hamiltonian (diagonal V, Sec. 2.1).
+ * in, out: device arrays of n_active complex values in A's order, of the type
+ * `precision` selects (it may differ from the state's own precision); they
+ * must not overlap.  No allocation.  Asynchronous on `stream`.  */
+pq_status pq_apply_H(const pq_state* state, const void* in, void* out, int precision,
+                     void* stream);
+
+/* Same operator with host buffers: copies `in` (host, n_active complex of
+ * `precision`) to the device, applies H, copies the result to `out` (host)
+ * and synchronises `stream`.  Uses the state's own device buffers. */
+pq_status pq_apply_H_host(pq_state* state, const void* in, void* out, int precision,
+                          void* stream);
+
+/* Adaption of Sec. 2.5 on the state's current coefficients: S = {I in A :
+ * |a_I| >= theta} (tested as fl(re*re) + fl(im*im) >= fl(theta*theta) in
+ * FP64, FP32 values widened exactly), A' = S union (nearest neighbours of S
+ * along each lattice axis, clipped at the edges); kept coefficients are
+ * carried over, new ones are zero.  Asynchronous; a capacity overflow is
+ * reported by the next synchronising call as PQ_ECAPACITY. */
+pq_status pq_prune(pq_state* state, double theta, int radius, void* stream);
+
+/* Propagation (Sec. 3.1): per step, a short-iterative-Lanczos step of order K
+ * with time step dt (each new Krylov vector orthogonalised against all
+ * previous ones when reorth = 1, against the previous two when reorth = 0;
+ * FP64 Lanczos scalars), then the adaption with (theta, radius), then the
+ * observables of the new state: t, C(t) = <Psi(0)|Psi(t)>, ||psi||^2,
+ * E = Re<psi|H psi>/||psi||^2, |A|, and the number of active points with
+ * |a| < theta.  Observables accumulate in the state (pq_observables_get).
+ * Asynchronous except for one synchronisation at the end that reads the
+ * device error word. */
+typedef struct pq_prop_desc {
+    int K;           /* Krylov dimension (H.psi products per step), 1..32     */
+    double dt;       /* time step                                            */
+    double theta;    /* adaption threshold                                    */
+    int radius;      /* neighbour radius (1)                                  */
+    int reorth;      /* 1 = full re-orthogonalisation, 0 = three-term         */
+} pq_prop_desc;
+
+pq_status pq_propagate(pq_state* state, const pq_prop_desc* desc, int nsteps, void* stream);
+
+/* Observables recorded so far, oldest first (index 0 = after the initial
+ * prune, t = 0).  The caller passes arrays of `capacity` entries (any may be
+ * NULL); *count receives the number of records (copied: min(count, capacity)).
+ * E of the newest record needs one more H.psi and is computed here. */
+typedef struct pq_observables {
+    int64_t capacity;
+    int64_t* count;
+    double* t;
+    double* c_re;
+    double* c_im;
+    double* norm2;
+    double* energy;
+    int64_t* n_active;
+    int64_t* n_wasted;
+} pq_observables;
+
+pq_status pq_observables_get(pq_state* state, pq_observables* out);
+
+/* Time spent in pq_apply_H-equivalent work inside pq_propagate, measured with
+ * CUDA events on the propagation stream while timing is enabled: total
+ * milliseconds, number of H.psi products and the summed active-set size over
+ * those products.  pq_set_timing(state, 1) enables and resets it. */
+pq_status pq_set_timing(pq_state* state, int enable);
+pq_status pq_timing_get(pq_state* state, double* apply_ms, int64_t* n_apply,
+                        double* coef_applied);
+
+/* Number of kernels the library has launched since load (all states). */
+int64_t pq_launch_count(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* pq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRUNEDQ_H */

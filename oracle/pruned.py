@@ -23,6 +23,31 @@ def digits(A, dims):
                     dtype=np.int64).reshape(len(dims), -1)
 
 
+DENSE_MAP_LIMIT = 1 << 26
+
+
+class PositionMap:
+    """Position of every lattice point in the sorted active set A (-1 when
+    not active): the set semantics of the paper's hash set (Sec. 2.5) as a
+    dense table for lattices up to DENSE_MAP_LIMIT points, else a binary
+    search in A."""
+
+    def __init__(self, A, nfull):
+        self.A = np.asarray(A, dtype=np.int64)
+        self.dense = None
+        if nfull <= DENSE_MAP_LIMIT:
+            self.dense = np.full(int(nfull), -1, dtype=np.int64)
+            self.dense[self.A] = np.arange(len(self.A))
+
+    def __call__(self, keys):
+        if self.dense is not None:
+            ok = (keys >= 0) & (keys < len(self.dense))
+            p = np.where(ok, self.dense[np.where(ok, keys, 0)], -1)
+            found = p >= 0
+            return np.where(found, p, 0), found
+        return lookup(self.A, keys)
+
+
 def lookup(A, keys):
     """Positions of ``keys`` in the sorted array A and a found-mask."""
     A = np.asarray(A, dtype=np.int64)
@@ -57,13 +82,35 @@ def apply_H(A, psi, dims, Ts, vdiag):
         return y
     dg = digits(A, dims)
     st = strides_of(dims)
+    where = PositionMap(A, int(np.prod(dims)))
     for kappa, n in enumerate(dims):
         T = np.asarray(Ts[kappa], dtype=np.float64)
         ik = dg[kappa]
         for j in range(int(n)):
             target = A + (j - ik) * st[kappa]
-            pos, found = lookup(A, target)
+            pos, found = where(target)
             y[found] += T[ik[found], j] * psi[pos[found]]
+    return y
+
+
+def apply_H_at(A, psi, dims, Ts, vdiag_at, pos):
+    """The same definition as ``apply_H`` evaluated only at the output
+    positions ``pos`` (indices into A); ``vdiag_at`` holds V(x_I) there.  Used
+    to check large cases on a sample of outputs."""
+    A = np.asarray(A, dtype=np.int64)
+    psi = np.asarray(psi, dtype=np.complex128)
+    pos = np.asarray(pos, dtype=np.int64)
+    I = A[pos]
+    y = np.asarray(vdiag_at, dtype=np.float64) * psi[pos]
+    dg = digits(I, dims)
+    st = strides_of(dims)
+    for kappa, n in enumerate(dims):
+        T = np.asarray(Ts[kappa], dtype=np.float64)
+        ik = dg[kappa]
+        for j in range(int(n)):
+            target = I + (j - ik) * st[kappa]
+            p, found = lookup(A, target)
+            y[found] += T[ik[found], j] * psi[p[found]]
     return y
 
 

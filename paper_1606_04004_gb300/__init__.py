@@ -1,0 +1,287 @@
+"""Python binding of libprunedq, the GB300 (sm_103a) pruned quantum-dynamics
+library (Larsson, Hartke, Tannor, arXiv:1606.04004).
+
+Thin ctypes marshalling over the C ABI in ``include/prunedq.h``: every
+computational step runs in the library's CUDA kernels.  PyTorch is used only
+for device memory and streams (tensors passed to ``State.apply_H``).  If the
+shared library is missing, importing this package raises ImportError: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libprunedq.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(
+        f"{_LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+_lib = C.CDLL(_LIB_PATH)
+
+# ----------------------------------------------------------------- enums
+OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, ENUMERIC, ETIMEOUT, EBREAKDOWN, ENOTSUP = range(9)
+SINE_DVR, HO_DVR, PVB, PW = range(4)
+FP64, FP32MIX = 0, 1
+FACTOR_IDENTITY, FACTOR_KINETIC, FACTOR_DIAG = range(3)
+_STATUS = {0: "PQ_OK", 1: "PQ_EINVAL", 2: "PQ_ENOMEM", 3: "PQ_ECUDA", 4: "PQ_ECAPACITY",
+           5: "PQ_ENUMERIC", 6: "PQ_ETIMEOUT", 7: "PQ_EBREAKDOWN", 8: "PQ_ENOTSUP"}
+
+
+class PQError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+# ----------------------------------------------------------------- structs
+class ModeDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n", C.c_int), ("xmin", C.c_double), ("xmax", C.c_double),
+                ("mass", C.c_double), ("omega", C.c_double), ("nx_lattice", C.c_int),
+                ("np_lattice", C.c_int)]
+
+
+class Factor(C.Structure):
+    _fields_ = [("kind", C.c_int), ("values", C.POINTER(C.c_double))]
+
+
+class SopTerm(C.Structure):
+    _fields_ = [("coef", C.c_double), ("factors", C.POINTER(Factor))]
+
+
+class PropDesc(C.Structure):
+    _fields_ = [("K", C.c_int), ("dt", C.c_double), ("theta", C.c_double), ("radius", C.c_int),
+                ("reorth", C.c_int)]
+
+
+class Observables(C.Structure):
+    _fields_ = [("capacity", C.c_int64), ("count", C.POINTER(C.c_int64)),
+                ("t", C.POINTER(C.c_double)), ("c_re", C.POINTER(C.c_double)),
+                ("c_im", C.POINTER(C.c_double)), ("norm2", C.POINTER(C.c_double)),
+                ("energy", C.POINTER(C.c_double)), ("n_active", C.POINTER(C.c_int64)),
+                ("n_wasted", C.POINTER(C.c_int64))]
+
+
+_vp = C.c_void_p
+_SIGS = {
+    "pq_build_basis": [C.POINTER(ModeDesc), C.c_int, C.POINTER(_vp)],
+    "pq_basis_free": [_vp],
+    "pq_basis_grid": [_vp, C.c_int, _vp, _vp],
+    "pq_basis_kinetic": [_vp, C.c_int, _vp],
+    "pq_set_sop": [_vp, C.POINTER(SopTerm), C.c_int],
+    "pq_init_packet": [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.c_int, C.c_size_t,
+                       C.POINTER(_vp)],
+    "pq_state_free": [_vp],
+    "pq_state_load": [_vp, _vp, C.c_int64, _vp],
+    "pq_state_size": [_vp, C.POINTER(C.c_int64)],
+    "pq_state_read": [_vp, _vp, _vp],
+    "pq_state_psi_device": [_vp, C.POINTER(_vp)],
+    "pq_apply_H": [_vp, _vp, _vp, C.c_int, _vp],
+    "pq_apply_H_host": [_vp, _vp, _vp, C.c_int, _vp],
+    "pq_prune": [_vp, C.c_double, C.c_int, _vp],
+    "pq_propagate": [_vp, C.POINTER(PropDesc), C.c_int, _vp],
+    "pq_observables_get": [_vp, C.POINTER(Observables)],
+    "pq_set_timing": [_vp, C.c_int],
+    "pq_timing_get": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+    "pq_launch_count": [],
+    "pq_last_error": [],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.pq_basis_free.restype = None
+_lib.pq_state_free.restype = None
+_lib.pq_launch_count.restype = C.c_int64
+_lib.pq_last_error.restype = C.c_char_p
+
+#: names the C ABI exports (checked against include/prunedq.h by the tests)
+EXPORTS = tuple(_SIGS)
+
+
+def _check(rc):
+    if rc != OK:
+        raise PQError(rc, _lib.pq_last_error().decode())
+
+
+def launch_count() -> int:
+    return int(_lib.pq_launch_count())
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_vp)
+
+
+# ------------------------------------------------------------------ basis
+class Basis:
+    """Per-mode 1D DVR bases (pq_build_basis) plus an SoP Hamiltonian."""
+
+    def __init__(self, modes):
+        arr = (ModeDesc * len(modes))()
+        for i, m in enumerate(modes):
+            arr[i] = ModeDesc(int(m.get("kind", 0)), int(m["n"]), float(m.get("xmin", 0.0)),
+                              float(m.get("xmax", 0.0)), float(m.get("mass", 1.0)),
+                              float(m.get("omega", 1.0)), int(m.get("nx_lattice", 0)),
+                              int(m.get("np_lattice", 0)))
+        h = _vp()
+        _check(_lib.pq_build_basis(arr, len(modes), C.byref(h)))
+        self._h = h
+        self.dims = tuple(int(m["n"]) for m in modes)
+        self.D = len(modes)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.pq_basis_free(self._h)
+            self._h = None
+
+    def grid(self, mode):
+        n = self.dims[mode]
+        x, w = np.zeros(n), np.zeros(n)
+        _check(_lib.pq_basis_grid(self._h, mode, _dptr(x), _dptr(w)))
+        return x, w
+
+    def kinetic(self, mode):
+        n = self.dims[mode]
+        T = np.zeros((n, n))
+        _check(_lib.pq_basis_kinetic(self._h, mode, _dptr(T)))
+        return T
+
+    def set_sop(self, terms):
+        """terms: list of (coef, [factor per mode]) with factor None (identity),
+        "T" (kinetic) or an array of n values (diagonal)."""
+        keep = []
+        carr = (SopTerm * max(1, len(terms)))()
+        for t, (coef, facs) in enumerate(terms):
+            if len(facs) != self.D:
+                raise ValueError("one factor per mode")
+            fa = (Factor * self.D)()
+            for k, f in enumerate(facs):
+                if f is None:
+                    fa[k] = Factor(FACTOR_IDENTITY, None)
+                elif isinstance(f, str) and f == "T":
+                    fa[k] = Factor(FACTOR_KINETIC, None)
+                else:
+                    v = np.ascontiguousarray(f, dtype=np.float64)
+                    if v.shape != (self.dims[k],):
+                        raise ValueError(f"factor of mode {k} needs {self.dims[k]} values")
+                    keep.append(v)
+                    fa[k] = Factor(FACTOR_DIAG, v.ctypes.data_as(C.POINTER(C.c_double)))
+            keep.append(fa)
+            carr[t] = SopTerm(float(coef), fa)
+        _check(_lib.pq_set_sop(self._h, carr, len(terms)))
+
+
+# ------------------------------------------------------------------ state
+def _cdtype(prec):
+    return np.complex128 if prec == FP64 else np.complex64
+
+
+class State:
+    """Active set + coefficients on the device (pq_init_packet / pq_state_load)."""
+
+    def __init__(self, basis: Basis, q0, p0, width, theta, precision=FP64, capacity=0, radius=1):
+        D = basis.D
+        q0 = np.ascontiguousarray(q0, dtype=np.float64).reshape(D)
+        p0 = np.ascontiguousarray(p0, dtype=np.float64).reshape(D)
+        w = np.ascontiguousarray(width, dtype=np.float64).reshape(D)
+        h = _vp()
+        _check(_lib.pq_init_packet(basis._h, _dptr(q0), _dptr(p0), _dptr(w), float(theta),
+                                   int(radius), int(precision), int(capacity), C.byref(h)))
+        self._h = h
+        self.basis = basis          # the basis must outlive the state
+        self.precision = precision
+        self.dtype = _cdtype(precision)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.pq_state_free(self._h)
+            self._h = None
+
+    def free(self):
+        self.__del__()
+
+    def load(self, idx, psi=None):
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        p = None
+        if psi is not None:
+            p = np.ascontiguousarray(psi, dtype=self.dtype)
+            if p.shape != idx.shape:
+                raise ValueError("psi must match idx")
+        _check(_lib.pq_state_load(self._h, _dptr(idx), len(idx), None if p is None else _dptr(p)))
+
+    def size(self) -> int:
+        n = C.c_int64()
+        _check(_lib.pq_state_size(self._h, C.byref(n)))
+        return int(n.value)
+
+    def read(self):
+        n = self.size()
+        idx = np.zeros(n, dtype=np.int64)
+        psi = np.zeros(n, dtype=self.dtype)
+        _check(_lib.pq_state_read(self._h, _dptr(idx), _dptr(psi)))
+        return idx, psi
+
+    def psi_device_ptr(self) -> int:
+        p = _vp()
+        _check(_lib.pq_state_psi_device(self._h, C.byref(p)))
+        return int(p.value or 0)
+
+    def apply_H(self, x, out, precision=None, stream=None):
+        """out = P_A H P_A x for torch CUDA tensors (complex64 or complex128)."""
+        import torch
+        prec = precision if precision is not None else (FP64 if x.dtype == torch.complex128 else FP32MIX)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        _check(_lib.pq_apply_H(self._h, _vp(x.data_ptr()), _vp(out.data_ptr()), int(prec),
+                               _vp(stream)))
+        return out
+
+    def apply_H_host(self, x: np.ndarray, precision=None) -> np.ndarray:
+        """The same operator through host buffers (copies inside the call)."""
+        prec = precision if precision is not None else (FP64 if x.dtype == np.complex128 else FP32MIX)
+        xin = np.ascontiguousarray(x, dtype=_cdtype(prec))
+        out = np.empty_like(xin)
+        _check(_lib.pq_apply_H_host(self._h, _dptr(xin), _dptr(out), int(prec), None))
+        return out
+
+    def prune(self, theta, radius=1, stream=None):
+        _check(_lib.pq_prune(self._h, float(theta), int(radius), _vp(stream or 0)))
+
+    def propagate(self, K, dt, theta, nsteps, reorth=1, radius=1, stream=None):
+        d = PropDesc(int(K), float(dt), float(theta), int(radius), int(reorth))
+        _check(_lib.pq_propagate(self._h, C.byref(d), int(nsteps), _vp(stream or 0)))
+
+    def observables(self) -> dict:
+        cnt = C.c_int64()
+        o = Observables(0, C.pointer(cnt))
+        _check(_lib.pq_observables_get(self._h, C.byref(o)))
+        n = int(cnt.value)
+        arrs = {k: np.zeros(n) for k in ("t", "c_re", "c_im", "norm2", "energy")}
+        ia = {k: np.zeros(n, dtype=np.int64) for k in ("n_active", "n_wasted")}
+        o = Observables(n, C.pointer(cnt), *[arrs[k].ctypes.data_as(C.POINTER(C.c_double))
+                                             for k in ("t", "c_re", "c_im", "norm2", "energy")],
+                        *[ia[k].ctypes.data_as(C.POINTER(C.c_int64)) for k in ("n_active", "n_wasted")])
+        _check(_lib.pq_observables_get(self._h, C.byref(o)))
+        out = dict(arrs)
+        out.update(ia)
+        out["C"] = arrs["c_re"] + 1j * arrs["c_im"]
+        return out
+
+    def set_timing(self, enable=True):
+        _check(_lib.pq_set_timing(self._h, int(enable)))
+
+    def timing(self):
+        ms, n, coef = C.c_double(), C.c_int64(), C.c_double()
+        _check(_lib.pq_timing_get(self._h, C.byref(ms), C.byref(n), C.byref(coef)))
+        return dict(apply_ms=ms.value, n_apply=int(n.value), coef_applied=coef.value)
+
+
+from .hamiltonians import (build_model, henon_heiles_terms, coupled_morse_terms,  # noqa: E402
+                           modes_of)

@@ -1,0 +1,228 @@
+// Host-side (FP64) construction of the 1D primitive bases and packet factors.
+// Sec. 2.1: a DVR basis chi_j has points x_j and weights w_j with coefficient
+// a_j = sqrt(w_j) psi(x_j); Sec. 2.2 (Eq. pvN_def) uses the same weights to
+// project functions onto the DVR.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "pq_internal.h"
+
+namespace pq {
+
+// Cyclic Jacobi eigendecomposition of a symmetric n x n matrix A (row-major,
+// destroyed).  On return evals ascending and evecs column j = eigenvector j.
+// Returns the number of sweeps used (< 0 if it did not converge).
+int jacobi_eigh(int n, std::vector<double>& A, std::vector<double>& evals,
+                std::vector<double>& evecs) {
+    evecs.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) evecs[(size_t)i * n + i] = 1.0;
+    int sweep = 0;
+    for (; sweep < 100; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < n; ++i) {
+            diag += A[(size_t)i * n + i] * A[(size_t)i * n + i];
+            for (int j = i + 1; j < n; ++j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+        }
+        if (off <= 1e-32 * (diag + 1e-300)) break;
+        for (int p = 0; p < n; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                // rotation angle that zeroes A_pq: tan(2 phi) = 2 apq / (aqq - app)
+                double tau = (aqq - app) / (2.0 * apq);
+                double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < n; ++k) {   // A <- A J (columns p, q)
+                    double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - s * akq;
+                    A[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {   // A <- J^T A (rows p, q)
+                    double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - s * aqk;
+                    A[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {   // V <- V J
+                    double vkp = evecs[(size_t)k * n + p], vkq = evecs[(size_t)k * n + q];
+                    evecs[(size_t)k * n + p] = c * vkp - s * vkq;
+                    evecs[(size_t)k * n + q] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+    // sort ascending
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(),
+              [&](int a, int b) { return A[(size_t)a * n + a] < A[(size_t)b * n + b]; });
+    evals.resize(n);
+    std::vector<double> V2((size_t)n * n);
+    for (int j = 0; j < n; ++j) {
+        evals[j] = A[(size_t)order[j] * n + order[j]];
+        for (int k = 0; k < n; ++k) V2[(size_t)k * n + j] = evecs[(size_t)k * n + order[j]];
+    }
+    evecs.swap(V2);
+    return sweep < 100 ? sweep : -1;
+}
+
+// Sine DVR on [xmin, xmax]: particle-in-a-box functions diagonalised in x.
+static void sine_dvr(int n, double xmin, double xmax, double mass, std::vector<double>& x,
+                     std::vector<double>& w, std::vector<double>& T) {
+    const double L = xmax - xmin;
+    x.resize(n);
+    w.assign(n, L / (n + 1));
+    for (int j = 0; j < n; ++j) x[j] = xmin + (j + 1) * L / (n + 1);
+    T.assign((size_t)n * n, 0.0);
+    const double pref = 2.0 / (n + 1);
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            double acc = 0.0;
+            for (int k = 1; k <= n; ++k) {
+                double ek = (k * M_PI / L) * (k * M_PI / L) / (2.0 * mass);
+                acc += sin((a + 1) * k * M_PI / (n + 1)) * ek * sin((b + 1) * k * M_PI / (n + 1));
+            }
+            T[(size_t)a * n + b] = pref * acc;
+        }
+}
+
+// Normalised HO functions phi_0..phi_{n} at x (three-term recurrence in
+// xi = sqrt(m omega) x): phi_{k+1} = sqrt(2/(k+1)) xi phi_k - sqrt(k/(k+1)) phi_{k-1}.
+static void ho_functions(int n, double mass, double omega, double x, double* phi) {
+    const double xi = sqrt(mass * omega) * x;
+    phi[0] = pow(mass * omega / M_PI, 0.25) * exp(-0.5 * xi * xi);
+    if (n >= 1) phi[1] = sqrt(2.0) * xi * phi[0];
+    for (int k = 1; k < n; ++k)
+        phi[k + 1] = sqrt(2.0 / (k + 1)) * xi * phi[k] - sqrt((double)k / (k + 1)) * phi[k - 1];
+}
+
+// HO (Gauss-Hermite) DVR: the DVR points are the eigenvalues of the position
+// matrix in the first n oscillator functions, i.e. the zeros of phi_n (found
+// by Jacobi, then polished by Newton on phi_n).  The transformation is
+// U_ki = sqrt(w_i) phi_k(x_i) with w_i = 1 / sum_k phi_k(x_i)^2 (the DVR
+// weight that turns grid values into coefficients); evaluating it from the
+// recurrence keeps full relative accuracy in the small edge components.
+// Kinetic energy exact in the oscillator basis, then transformed: T = U^T K U.
+static int ho_dvr(int n, double mass, double omega, std::vector<double>& x,
+                  std::vector<double>& w, std::vector<double>& T) {
+    std::vector<double> X((size_t)n * n, 0.0), Uj, ev;
+    for (int k = 0; k + 1 < n; ++k)
+        X[(size_t)k * n + k + 1] = X[(size_t)(k + 1) * n + k] = sqrt((k + 1) / (2.0 * mass * omega));
+    if (jacobi_eigh(n, X, ev, Uj) < 0) return -1;
+    std::vector<double> phi(n + 2);
+    const double s = sqrt(mass * omega);
+    for (int i = 0; i < n; ++i) {
+        double xi = ev[i];
+        for (int it = 0; it < 4; ++it) {   // Newton on phi_n: phi_n' = s (sqrt(n/2) phi_{n-1} - sqrt((n+1)/2) phi_{n+1})
+            ho_functions(n + 1, mass, omega, xi, phi.data());
+            const double d = s * (sqrt(n / 2.0) * phi[n - 1] - sqrt((n + 1) / 2.0) * phi[n + 1]);
+            if (d == 0.0) break;
+            xi -= phi[n] / d;
+        }
+        ev[i] = xi;
+    }
+    std::vector<double> U((size_t)n * n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        ho_functions(n - 1, mass, omega, ev[i], phi.data());
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc += phi[k] * phi[k];
+        w[i] = 1.0 / acc;
+        const double sw = sqrt(w[i]);
+        for (int k = 0; k < n; ++k) U[(size_t)k * n + i] = sw * phi[k];
+    }
+    std::vector<double> K((size_t)n * n, 0.0);   // p^2 / (2 m) in the HO basis
+    for (int k = 0; k < n; ++k) K[(size_t)k * n + k] = mass * omega * (k + 0.5) / (2.0 * mass);
+    for (int k = 0; k + 2 < n; ++k) {
+        double v = -0.5 * mass * omega * sqrt((k + 1.0) * (k + 2.0)) / (2.0 * mass);
+        K[(size_t)k * n + k + 2] = K[(size_t)(k + 2) * n + k] = v;
+    }
+    T.assign((size_t)n * n, 0.0);
+    std::vector<double> KU((size_t)n * n, 0.0);
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc += K[(size_t)a * n + k] * U[(size_t)k * n + b];
+            KU[(size_t)a * n + b] = acc;
+        }
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc += U[(size_t)k * n + a] * KU[(size_t)k * n + b];
+            T[(size_t)a * n + b] = acc;
+        }
+    for (int a = 0; a < n; ++a)   // symmetrise rounding
+        for (int b = a + 1; b < n; ++b) {
+            double m = 0.5 * (T[(size_t)a * n + b] + T[(size_t)b * n + a]);
+            T[(size_t)a * n + b] = T[(size_t)b * n + a] = m;
+        }
+    x = ev;
+    return 0;
+}
+
+pq_status build_dvr_mode(const pq_mode_desc& m, std::vector<double>& x, std::vector<double>& w,
+                         std::vector<double>& T) {
+    if (m.n < 2 || m.n > kMaxN) {
+        set_error("mode size %d outside 2..%d", m.n, kMaxN);
+        return PQ_EINVAL;
+    }
+    if (!(m.mass > 0)) {
+        set_error("mode mass must be positive");
+        return PQ_EINVAL;
+    }
+    if (m.kind == PQ_SINE_DVR) {
+        if (!(m.xmax > m.xmin)) {
+            set_error("sine DVR needs xmax > xmin");
+            return PQ_EINVAL;
+        }
+        sine_dvr(m.n, m.xmin, m.xmax, m.mass, x, w, T);
+        return PQ_OK;
+    }
+    if (m.kind == PQ_HO_DVR) {
+        if (!(m.omega > 0)) {
+            set_error("HO DVR needs omega > 0");
+            return PQ_EINVAL;
+        }
+        if (ho_dvr(m.n, m.mass, m.omega, x, w, T) != 0) {
+            set_error("HO DVR eigensolver did not converge");
+            return PQ_ENUMERIC;
+        }
+        return PQ_OK;
+    }
+    if (m.kind == PQ_PVB || m.kind == PQ_PW) {
+        set_error("phase-space bases (pvB, pW) are not provided by this build");
+        return PQ_ENOTSUP;
+    }
+    set_error("unknown basis kind %d", m.kind);
+    return PQ_EINVAL;
+}
+
+// f_k(i) = sqrt(w_i) (2 pi s^2)^(-1/4) exp(-(x_i - q0)^2/(4 s^2) + i p0 (x_i - q0)),
+// normalised per mode so that the full-lattice product has unit norm.
+void packet_factors(const Basis& b, const double* q0, const double* p0, const double* width,
+                    std::vector<double>& out, int lead_virtual) {
+    const int Dint = b.D_user + lead_virtual;
+    out.assign((size_t)Dint * kMaxN * 2, 0.0);
+    if (lead_virtual) out[0] = 1.0;   // virtual size-1 mode: factor 1
+    for (int k = 0; k < b.D_user; ++k) {
+        const int n = b.modes[k].n;
+        double* f = &out[(size_t)(k + lead_virtual) * kMaxN * 2];
+        const double s2 = width[k] * width[k];
+        const double amp = pow(2.0 * M_PI * s2, -0.25);
+        double nrm = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double dx = b.x[k][i] - q0[k];
+            double mag = sqrt(b.w[k][i]) * amp * exp(-dx * dx / (4.0 * s2));
+            double ph = p0[k] * dx;
+            f[2 * i] = mag * cos(ph);
+            f[2 * i + 1] = mag * sin(ph);
+            nrm += f[2 * i] * f[2 * i] + f[2 * i + 1] * f[2 * i + 1];
+        }
+        nrm = sqrt(nrm);
+        for (int i = 0; i < 2 * n; ++i) f[i] /= nrm;
+    }
+}
+
+}  // namespace pq

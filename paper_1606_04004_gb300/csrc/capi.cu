@@ -1,0 +1,555 @@
+// C ABI of the library (declared in include/prunedq.h): object lifetime,
+// argument checking, host <-> device marshalling.  The compute steps live in
+// lattice.cu, apply_h.cu and krylov.cu.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "device_util.cuh"
+
+namespace pq {
+
+std::atomic<int64_t> g_launches{0};
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+static void free_state(State* s) {
+    if (!s) return;
+    void* ptrs[] = {s->keys,   s->psi,     s->psi_alt, s->bits,  s->bits_alt, s->off,
+                    s->off_alt, s->rows,   s->planes,  s->leaders, s->cnt,    s->scan_tmp,
+                    s->red_tmp, s->ks,     s->V,       s->T64,   s->T32,     s->pot64,
+                    s->pot32,  s->fac64,   s->fac32,   s->io_in, s->io_out};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (s->h_cnt) cudaFreeHost(s->h_cnt);
+    delete s;
+}
+
+template <typename T>
+static pq_status dalloc(T** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error("cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        return PQ_ENOMEM;
+    }
+    return PQ_OK;
+}
+
+// Device Hamiltonian tables from the basis' SoP.
+static pq_status upload_hamiltonian(State& s) {
+    const Basis& b = *s.basis;
+    const int D = s.lat.D, lv = s.lead_virtual;
+    const int nt = (int)b.pot_coef.size();
+    std::vector<double> T((size_t)D * kMaxN * kMaxN, 0.0);
+    for (int k = 0; k < b.D_user; ++k) {
+        const int n = b.modes[k].n;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                T[(size_t)(k + lv) * kMaxN * kMaxN + i * kMaxN + j] =
+                    b.kin_scale[k] * b.T[k][(size_t)i * n + j];
+    }
+    std::vector<double> P((size_t)std::max(nt, 1) * D * kMaxN, 0.0);
+    for (int t = 0; t < nt; ++t) {
+        for (int k = 0; k < D; ++k) {
+            const int ku = k - lv;
+            const int n = ku < 0 ? 1 : b.modes[ku].n;
+            for (int i = 0; i < n; ++i) {
+                double v = ku < 0 ? 1.0 : b.pot_values[t][(size_t)ku * kMaxN + i];
+                if (k == 0) v *= b.pot_coef[t];
+                P[((size_t)t * D + k) * kMaxN + i] = v;
+            }
+        }
+    }
+    std::vector<float> T32(T.begin(), T.end()), P32(P.begin(), P.end());
+    pq_status rc;
+    if ((rc = dalloc(&s.T64, T.size() * 8)) || (rc = dalloc(&s.T32, T.size() * 4)) ||
+        (rc = dalloc(&s.pot64, P.size() * 8)) || (rc = dalloc(&s.pot32, P.size() * 4)))
+        return rc;
+    PQ_CUDA_TRY(cudaMemcpy(s.T64, T.data(), T.size() * 8, cudaMemcpyHostToDevice));
+    PQ_CUDA_TRY(cudaMemcpy(s.T32, T32.data(), T32.size() * 4, cudaMemcpyHostToDevice));
+    PQ_CUDA_TRY(cudaMemcpy(s.pot64, P.data(), P.size() * 8, cudaMemcpyHostToDevice));
+    PQ_CUDA_TRY(cudaMemcpy(s.pot32, P32.data(), P32.size() * 4, cudaMemcpyHostToDevice));
+    s.nterms = nt;
+    return PQ_OK;
+}
+
+static pq_status create_state(const pq_basis* basis_, int precision, size_t capacity,
+                              State** out) {
+    const Basis* basis = reinterpret_cast<const Basis*>(basis_);
+    if (!basis || !out) {
+        set_error("null basis or output pointer");
+        return PQ_EINVAL;
+    }
+    if (!basis->sop_set) {
+        set_error("the basis has no Hamiltonian: call pq_set_sop first");
+        return PQ_EINVAL;
+    }
+    if (precision != PQ_FP64 && precision != PQ_FP32MIX) {
+        set_error("unknown precision %d", precision);
+        return PQ_EINVAL;
+    }
+    State* s = new State();
+    s->basis = basis;
+    s->prec = precision;
+    s->esize = precision == PQ_FP64 ? 16 : 8;
+    s->lead_virtual = basis->D_user == 1 ? 1 : 0;
+    Lattice& L = s->lat;
+    L.D = basis->D_user + s->lead_virtual;
+    for (int k = 0; k < L.D; ++k)
+        L.n[k] = k < s->lead_virtual ? 1 : basis->modes[k - s->lead_virtual].n;
+    pq_status rc = lattice_setup(*s);
+    if (rc) {
+        free_state(s);
+        return rc;
+    }
+    // lattice axes of the neighbour rule: one per DVR mode
+    L.naxes = L.D;
+    for (int k = 0; k < L.D; ++k) {
+        L.axis_n[k] = L.n[k];
+        L.axis_stride[k] = L.stride[k];
+    }
+    s->cap = capacity == 0 ? (size_t)L.nfull : std::min(capacity, (size_t)L.nfull);
+    s->rows_cap = std::min(s->cap, (size_t)L.nrows);
+    const size_t nw = L.nwords;
+    if ((rc = dalloc(&s->keys, s->cap * 4)) || (rc = dalloc(&s->psi, s->cap * s->esize)) ||
+        (rc = dalloc(&s->psi_alt, s->cap * s->esize)) || (rc = dalloc(&s->bits, nw * 8)) ||
+        (rc = dalloc(&s->bits_alt, nw * 8)) || (rc = dalloc(&s->off, (nw + 1) * 4)) ||
+        (rc = dalloc(&s->off_alt, (nw + 1) * 4)) || (rc = dalloc(&s->rows, s->rows_cap * 4)) ||
+        (rc = dalloc(&s->planes, s->rows_cap * 4)) ||
+        (rc = dalloc(&s->leaders, s->rows_cap * 4 * (size_t)std::max(1, L.D - 2))) ||
+        (rc = dalloc(&s->cnt, CNT_SIZE * 8)) || (rc = dalloc(&s->scan_tmp, 1024 * 4)) ||
+        (rc = dalloc(&s->red_tmp, (size_t)grid_size() * 4 * (2 * kMaxK + 8) * 8)) ||
+        (rc = dalloc(&s->ks, sizeof(KrylovScalars)))) {
+        free_state(s);
+        return rc;
+    }
+    if (cudaMallocHost((void**)&s->h_cnt, CNT_SIZE * 8) != cudaSuccess) {
+        set_error("cudaMallocHost failed");
+        free_state(s);
+        return PQ_ENOMEM;
+    }
+    cudaMemset(s->cnt, 0, CNT_SIZE * 8);
+    cudaMemset(s->bits, 0, nw * 8);
+    cudaMemset(s->off, 0, (nw + 1) * 4);
+    cudaMemset(s->ks, 0, sizeof(KrylovScalars));
+    if ((rc = upload_hamiltonian(*s))) {
+        free_state(s);
+        return rc;
+    }
+    *out = s;
+    return PQ_OK;
+}
+
+static pq_status check_capacity(State& s, cudaStream_t st) {
+    PQ_CUDA_TRY(cudaMemcpyAsync(s.h_cnt, s.cnt, CNT_SIZE * 8, cudaMemcpyDeviceToHost, st));
+    PQ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (s.h_cnt[CNT_ERR] & 1) {
+        set_error("active set of %lld points exceeds the capacity %zu",
+                  (long long)s.h_cnt[CNT_NA], s.cap);
+        return PQ_ECAPACITY;
+    }
+    return PQ_OK;
+}
+
+}  // namespace pq
+
+using namespace pq;
+
+#define PQ_API extern "C" __attribute__((visibility("default")))
+
+PQ_API const char* pq_last_error(void) { return g_err.c_str(); }
+PQ_API int64_t pq_launch_count(void) { return g_launches.load(); }
+
+PQ_API pq_status pq_build_basis(const pq_mode_desc* modes, int D, pq_basis** out) {
+    clear_error();
+    if (!modes || !out) {
+        set_error("null argument");
+        return PQ_EINVAL;
+    }
+    if (D < 1 || D > kMaxD - 1) {
+        set_error("D = %d outside 1..%d", D, kMaxD - 1);
+        return PQ_EINVAL;
+    }
+    Basis* b = new Basis();
+    b->D_user = D;
+    b->modes.assign(modes, modes + D);
+    b->x.resize(D);
+    b->w.resize(D);
+    b->T.resize(D);
+    double full = 1;
+    for (int k = 0; k < D; ++k) {
+        pq_status rc = build_dvr_mode(modes[k], b->x[k], b->w[k], b->T[k]);
+        if (rc) {
+            delete b;
+            return rc;
+        }
+        full *= modes[k].n;
+    }
+    if (full >= 4294967296.0) {
+        set_error("lattice of %.0f points: the limit is 2^32", full);
+        delete b;
+        return PQ_EINVAL;
+    }
+    *out = reinterpret_cast<pq_basis*>(b);
+    return PQ_OK;
+}
+
+PQ_API void pq_basis_free(pq_basis* basis) { delete reinterpret_cast<Basis*>(basis); }
+
+PQ_API pq_status pq_basis_grid(const pq_basis* basis_, int mode, double* x, double* w) {
+    clear_error();
+    const Basis* b = reinterpret_cast<const Basis*>(basis_);
+    if (!b || mode < 0 || mode >= b->D_user) {
+        set_error("bad basis or mode");
+        return PQ_EINVAL;
+    }
+    const int n = b->modes[mode].n;
+    if (x) memcpy(x, b->x[mode].data(), n * sizeof(double));
+    if (w) memcpy(w, b->w[mode].data(), n * sizeof(double));
+    return PQ_OK;
+}
+
+PQ_API pq_status pq_basis_kinetic(const pq_basis* basis_, int mode, double* T) {
+    clear_error();
+    const Basis* b = reinterpret_cast<const Basis*>(basis_);
+    if (!b || !T || mode < 0 || mode >= b->D_user) {
+        set_error("bad basis, mode or output");
+        return PQ_EINVAL;
+    }
+    const int n = b->modes[mode].n;
+    memcpy(T, b->T[mode].data(), (size_t)n * n * sizeof(double));
+    return PQ_OK;
+}
+
+PQ_API pq_status pq_set_sop(pq_basis* basis_, const pq_sop_term* terms, int nterms) {
+    clear_error();
+    Basis* b = reinterpret_cast<Basis*>(basis_);
+    if (!b || (nterms > 0 && !terms) || nterms < 0) {
+        set_error("bad basis or term list");
+        return PQ_EINVAL;
+    }
+    const int D = b->D_user;
+    std::vector<double> kin(D, 0.0), pc;
+    std::vector<std::vector<double>> pv;
+    for (int t = 0; t < nterms; ++t) {
+        const pq_sop_term& tm = terms[t];
+        if (!tm.factors) {
+            set_error("term %d has no factors", t);
+            return PQ_EINVAL;
+        }
+        int nkin = 0, kmode = -1, ndiag = 0;
+        for (int k = 0; k < D; ++k) {
+            const int kind = tm.factors[k].kind;
+            if (kind == PQ_FACTOR_KINETIC) {
+                ++nkin;
+                kmode = k;
+            } else if (kind == PQ_FACTOR_DIAG) {
+                if (!tm.factors[k].values) {
+                    set_error("term %d mode %d: diagonal factor without values", t, k);
+                    return PQ_EINVAL;
+                }
+                ++ndiag;
+            } else if (kind != PQ_FACTOR_IDENTITY) {
+                set_error("term %d mode %d: unknown factor kind %d", t, k, kind);
+                return PQ_EINVAL;
+            }
+        }
+        if (!std::isfinite(tm.coef)) {
+            set_error("term %d: non-finite coefficient", t);
+            return PQ_EINVAL;
+        }
+        if (nkin > 1 || (nkin == 1 && ndiag > 0)) {
+            set_error("term %d: a DVR term is either one kinetic factor or diagonal factors", t);
+            return PQ_ENOTSUP;
+        }
+        if (nkin == 1) {
+            kin[kmode] += tm.coef;
+            continue;
+        }
+        std::vector<double> vals((size_t)D * kMaxN, 1.0);
+        for (int k = 0; k < D; ++k)
+            if (tm.factors[k].kind == PQ_FACTOR_DIAG)
+                for (int i = 0; i < b->modes[k].n; ++i) {
+                    const double v = tm.factors[k].values[i];
+                    if (!std::isfinite(v)) {
+                        set_error("term %d mode %d: non-finite value", t, k);
+                        return PQ_EINVAL;
+                    }
+                    vals[(size_t)k * kMaxN + i] = v;
+                }
+        pc.push_back(tm.coef);
+        pv.push_back(vals);
+    }
+    if ((int)pc.size() > kMaxTerms) {
+        set_error("%zu potential terms: at most %d", pc.size(), kMaxTerms);
+        return PQ_ENOTSUP;
+    }
+    b->kin_scale = kin;
+    b->pot_coef = pc;
+    b->pot_values = pv;
+    b->sop_set = true;
+    return PQ_OK;
+}
+
+PQ_API pq_status pq_init_packet(const pq_basis* basis_, const double* q0, const double* p0,
+                                const double* width, double theta, int radius, int precision,
+                                size_t capacity, pq_state** out) {
+    clear_error();
+    if (!q0 || !p0 || !width) {
+        set_error("null packet parameter");
+        return PQ_EINVAL;
+    }
+    if (!(theta >= 0) || !std::isfinite(theta)) {
+        set_error("theta must be finite and >= 0");
+        return PQ_EINVAL;
+    }
+    if (radius != 1) {
+        set_error("neighbour radius %d not provided (radius 1 only)", radius);
+        return PQ_ENOTSUP;
+    }
+    const Basis* b = reinterpret_cast<const Basis*>(basis_);
+    if (b)
+        for (int k = 0; k < b->D_user; ++k)
+            if (!(width[k] > 0)) {
+                set_error("packet width of mode %d must be positive", k);
+                return PQ_EINVAL;
+            }
+    State* s = nullptr;
+    pq_status rc = create_state(basis_, precision, capacity, &s);
+    if (rc) return rc;
+    std::vector<double> fac;
+    packet_factors(*b, q0, p0, width, fac, s->lead_virtual);
+    std::vector<float> fac32(fac.begin(), fac.end());
+    if ((rc = dalloc(&s->fac64, fac.size() * 8)) || (rc = dalloc(&s->fac32, fac32.size() * 4))) {
+        free_state(s);
+        return rc;
+    }
+    cudaMemcpy(s->fac64, fac.data(), fac.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(s->fac32, fac32.data(), fac32.size() * 4, cudaMemcpyHostToDevice);
+    s->theta = theta;
+    s->radius = radius;
+    cudaStream_t st = 0;
+    if ((rc = init_bits_from_packet(*s, theta, st)) || (rc = check_capacity(*s, st)) ||
+        (rc = set_psi_from_packet(*s, st)) || (rc = observe_launch(*s, theta, st))) {
+        free_state(s);
+        return rc;
+    }
+    *out = reinterpret_cast<pq_state*>(s);
+    return PQ_OK;
+}
+
+PQ_API void pq_state_free(pq_state* state) { free_state(reinterpret_cast<State*>(state)); }
+
+PQ_API pq_status pq_state_load(pq_state* state, const int64_t* idx, int64_t n, const void* psi) {
+    clear_error();
+    State* s = reinterpret_cast<State*>(state);
+    if (!s || n < 0 || (n > 0 && !idx)) {
+        set_error("bad state or index list");
+        return PQ_EINVAL;
+    }
+    if ((size_t)n > s->cap) {
+        set_error("%lld points exceed the capacity %zu", (long long)n, s->cap);
+        return PQ_ECAPACITY;
+    }
+    std::vector<uint32_t> k32((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        if (idx[i] < 0 || idx[i] >= (int64_t)s->lat.nfull || (i > 0 && idx[i] <= idx[i - 1])) {
+            set_error("index %lld at position %lld is out of the lattice or not increasing",
+                      (long long)idx[i], (long long)i);
+            return PQ_EINVAL;
+        }
+        k32[i] = (uint32_t)idx[i];
+    }
+    uint32_t* dk = nullptr;
+    pq_status rc = dalloc(&dk, (size_t)n * 4);
+    if (rc) return rc;
+    cudaMemcpy(dk, k32.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
+    rc = load_set(*s, dk, n, 0);
+    cudaDeviceSynchronize();
+    cudaFree(dk);
+    if (rc) return rc;
+    if (psi)
+        PQ_CUDA_TRY(cudaMemcpy(s->psi, psi, (size_t)n * s->esize, cudaMemcpyHostToDevice));
+    else
+        PQ_CUDA_TRY(cudaMemset(s->psi, 0, (size_t)std::max<int64_t>(n, 1) * s->esize));
+    return check_capacity(*s, 0);
+}
+
+PQ_API pq_status pq_state_size(const pq_state* state, int64_t* n_active) {
+    clear_error();
+    State* s = const_cast<State*>(reinterpret_cast<const State*>(state));
+    if (!s || !n_active) {
+        set_error("null argument");
+        return PQ_EINVAL;
+    }
+    PQ_CUDA_TRY(cudaDeviceSynchronize());
+    PQ_CUDA_TRY(cudaMemcpy(s->h_cnt, s->cnt, CNT_SIZE * 8, cudaMemcpyDeviceToHost));
+    *n_active = std::min<int64_t>(s->h_cnt[CNT_NA], (int64_t)s->cap);
+    return PQ_OK;
+}
+
+PQ_API pq_status pq_state_read(const pq_state* state, int64_t* idx, void* psi) {
+    clear_error();
+    const State* s = reinterpret_cast<const State*>(state);
+    int64_t n = 0;
+    pq_status rc = pq_state_size(state, &n);
+    if (rc) return rc;
+    if (idx && n > 0) {
+        std::vector<uint32_t> k32((size_t)n);
+        PQ_CUDA_TRY(cudaMemcpy(k32.data(), s->keys, (size_t)n * 4, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n; ++i) idx[i] = k32[i];
+    }
+    if (psi && n > 0)
+        PQ_CUDA_TRY(cudaMemcpy(psi, s->psi, (size_t)n * s->esize, cudaMemcpyDeviceToHost));
+    return PQ_OK;
+}
+
+PQ_API pq_status pq_state_psi_device(const pq_state* state, void** psi) {
+    clear_error();
+    const State* s = reinterpret_cast<const State*>(state);
+    if (!s || !psi) {
+        set_error("null argument");
+        return PQ_EINVAL;
+    }
+    *psi = s->psi;
+    return PQ_OK;
+}
+
+PQ_API pq_status pq_apply_H(const pq_state* state, const void* in, void* out, int precision,
+                            void* stream) {
+    clear_error();
+    const State* s = reinterpret_cast<const State*>(state);
+    if (!s || !in || !out) {
+        set_error("null state or vector");
+        return PQ_EINVAL;
+    }
+    if (in == out) {
+        set_error("in and out must not overlap");
+        return PQ_EINVAL;
+    }
+    return apply_H_launch(*s, in, out, precision, nullptr, nullptr, 0, (cudaStream_t)stream);
+}
+
+PQ_API pq_status pq_apply_H_host(pq_state* state, const void* in, void* out, int precision,
+                                 void* stream) {
+    clear_error();
+    State* s = reinterpret_cast<State*>(state);
+    if (!s || !in || !out) {
+        set_error("null state or vector");
+        return PQ_EINVAL;
+    }
+    if (precision != PQ_FP64 && precision != PQ_FP32MIX) {
+        set_error("unknown precision %d", precision);
+        return PQ_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!s->io_in) {
+        pq_status rc;
+        if ((rc = dalloc(&s->io_in, s->cap * 16)) || (rc = dalloc(&s->io_out, s->cap * 16)))
+            return rc;
+    }
+    PQ_CUDA_TRY(cudaMemcpyAsync(s->h_cnt, s->cnt, CNT_SIZE * 8, cudaMemcpyDeviceToHost, st));
+    PQ_CUDA_TRY(cudaStreamSynchronize(st));
+    const int64_t n = std::min<int64_t>(s->h_cnt[CNT_NA], (int64_t)s->cap);
+    const size_t bytes = (size_t)n * (precision == PQ_FP64 ? 16 : 8);
+    if (n > 0) PQ_CUDA_TRY(cudaMemcpyAsync(s->io_in, in, bytes, cudaMemcpyHostToDevice, st));
+    pq_status rc = apply_H_launch(*s, s->io_in, s->io_out, precision, nullptr, nullptr, 0, st);
+    if (rc) return rc;
+    if (n > 0) PQ_CUDA_TRY(cudaMemcpyAsync(out, s->io_out, bytes, cudaMemcpyDeviceToHost, st));
+    PQ_CUDA_TRY(cudaStreamSynchronize(st));
+    return PQ_OK;
+}
+
+PQ_API pq_status pq_prune(pq_state* state, double theta, int radius, void* stream) {
+    clear_error();
+    State* s = reinterpret_cast<State*>(state);
+    if (!s || !(theta >= 0) || !std::isfinite(theta)) {
+        set_error("bad state or theta");
+        return PQ_EINVAL;
+    }
+    return prune_launch(*s, theta, radius, (cudaStream_t)stream);
+}
+
+PQ_API pq_status pq_propagate(pq_state* state, const pq_prop_desc* desc, int nsteps,
+                              void* stream) {
+    clear_error();
+    State* s = reinterpret_cast<State*>(state);
+    if (!s || !desc) {
+        set_error("null state or descriptor");
+        return PQ_EINVAL;
+    }
+    s->theta = desc->theta;
+    return propagate_impl(*s, *desc, nsteps, (cudaStream_t)stream);
+}
+
+PQ_API pq_status pq_observables_get(pq_state* state, pq_observables* out) {
+    clear_error();
+    State* s = reinterpret_cast<State*>(state);
+    if (!s || !out) {
+        set_error("null argument");
+        return PQ_EINVAL;
+    }
+    if (s->obs_energy_pending && !s->obs.empty()) {
+        double E = 0.0;
+        pq_status rc = energy_of_current(*s, &E, 0);
+        if (rc) return rc;
+        s->obs.back().energy = E;
+        s->obs_energy_pending = false;
+    }
+    const int64_t n = (int64_t)s->obs.size();
+    if (out->count) *out->count = n;
+    const int64_t m = std::min<int64_t>(n, out->capacity);
+    for (int64_t i = 0; i < m; ++i) {
+        const ObsRecord& o = s->obs[i];
+        if (out->t) out->t[i] = o.t;
+        if (out->c_re) out->c_re[i] = o.c_re;
+        if (out->c_im) out->c_im[i] = o.c_im;
+        if (out->norm2) out->norm2[i] = o.norm2;
+        if (out->energy) out->energy[i] = o.energy;
+        if (out->n_active) out->n_active[i] = o.n_active;
+        if (out->n_wasted) out->n_wasted[i] = o.n_wasted;
+    }
+    return PQ_OK;
+}
+
+PQ_API pq_status pq_set_timing(pq_state* state, int enable) {
+    clear_error();
+    State* s = reinterpret_cast<State*>(state);
+    if (!s) {
+        set_error("null state");
+        return PQ_EINVAL;
+    }
+    s->timing.enabled = enable != 0;
+    s->timing.ms = 0;
+    s->timing.n_apply = 0;
+    s->timing.coef = 0;
+    return PQ_OK;
+}
+
+PQ_API pq_status pq_timing_get(pq_state* state, double* apply_ms, int64_t* n_apply,
+                               double* coef_applied) {
+    clear_error();
+    State* s = reinterpret_cast<State*>(state);
+    if (!s) {
+        set_error("null state");
+        return PQ_EINVAL;
+    }
+    if (apply_ms) *apply_ms = s->timing.ms;
+    if (n_apply) *n_apply = s->timing.n_apply;
+    if (coef_applied) *coef_applied = s->timing.coef;
+    return PQ_OK;
+}

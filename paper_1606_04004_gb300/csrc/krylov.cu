@@ -1,0 +1,637 @@
+// Short-iterative Lanczos propagation on the device (Sec. 3.1: short
+// iterative Arnoldi; for Hermitian H its Hessenberg matrix is the Lanczos
+// tridiagonal), the adaption after every step (Sec. 2.5) and the observables
+// (Eq. acorr).  All Lanczos scalars live on the device in FP64; the host never
+// waits inside a step.
+//
+// Per step, with V_0 = psi (scale 1/beta_0) and the new Krylov vector written
+// in place into its slot:
+//   W = H V_k                               (apply_H, input scaled by sigma_k)
+//   c_i = <V_i, W> for the vectors kept      (dots, FP64 or double-float sums)
+//   W <- W - sum_i c_i V_i,  beta_k = ||W||  (update; sigma_{k+1} = 1/beta_k)
+//   psi <- beta_0 V_K exp(-i T_K dt) e_1     (exp of the K x K tridiagonal)
+// Reductions are deterministic: fixed-order per-block partials, then one
+// block sums them in block order.
+#include <math.h>
+
+#include "device_util.cuh"
+
+namespace pq {
+
+constexpr int kRedThreads = 256;
+constexpr int kMaxM = 16;   // Krylov vectors handled per dots / update launch
+
+static int red_blocks() { return grid_size() * 4; }
+
+// accumulator: FP64 for double inputs, double-float for float inputs
+template <typename R> struct Acc;
+template <> struct Acc<double> {
+    double v;
+    __device__ void init() { v = 0.0; }
+    __device__ void add(double x) { v += x; }
+    __device__ double value() const { return v; }
+};
+template <> struct Acc<float> {
+    DF v;
+    __device__ void init() { v.hi = 0.f; v.lo = 0.f; }
+    __device__ void add(float x) { df_add(v, x); }
+    __device__ double value() const { return df_value(v); }
+};
+
+// Sum `width` per-thread doubles over the block; thread 0 writes them to
+// partials[blockIdx.x * width + j].
+__device__ void block_partials(double* vals, int width, double* partials) {
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j < width; ++j) {
+        double v = warp_sum(vals[j]);
+        if (lane == 0) sh[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            double x = lane < nw ? sh[lane] : 0.0;
+            x = warp_sum(x);
+            if (lane == 0) partials[(size_t)blockIdx.x * width + j] = x;
+        }
+        __syncthreads();
+    }
+}
+
+// Column sums of partials[G][width] in block order -> out[width].
+__device__ void sum_partials(const double* partials, int G, int width, double* out) {
+    for (int j = threadIdx.x; j < width; j += blockDim.x) {
+        double acc = 0.0;
+        for (int b = 0; b < G; ++b) acc += partials[(size_t)b * width + j];
+        out[j] = acc;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ const typename Cx<R>::T* kvec(const void* psi, const void* Vb,
+                                                          size_t cap, int i) {
+    using V = typename Cx<R>::T;
+    return i == 0 ? (const V*)psi : (const V*)Vb + (size_t)(i - 1) * cap;
+}
+
+// ---------------------------------------------------------------- norm
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_norm2(const typename Cx<R>::T* __restrict__ x,
+                                                        const int64_t* na, int64_t cap,
+                                                        double* partials) {
+    const int64_t n = min(*na, cap);
+    Acc<R> acc;
+    acc.init();
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const auto v = x[p];
+        acc.add(v.x * v.x + v.y * v.y);
+    }
+    double vals[1] = {acc.value()};
+    block_partials(vals, 1, partials);
+}
+
+// beta_0 = ||psi||; sigma_0 = 1/beta_0; reset the step's scalars.
+__global__ void k_start_step(const double* partials, int G, KrylovScalars* ks, int K,
+                             int64_t* err) {
+    __shared__ double tot[1];
+    sum_partials(partials, G, 1, tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double n2 = tot[0];
+        ks->keff = K;
+        if (!(n2 > 0.0) || !isfinite(n2)) {
+            // empty or zero state: nothing to propagate
+            ks->beta0 = 0.0;
+            ks->sigma[0] = 0.0;
+            ks->keff = 0;
+            if (!isfinite(n2)) *err |= 2;
+        } else {
+            ks->beta0 = sqrt(n2);
+            ks->sigma[0] = 1.0 / ks->beta0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- dots
+// c_i = sigma_i <V_i, W> for i in [i0, i0 + m) and ||W||^2.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_dots(const void* psi, const void* Vb, size_t cap,
+                                                       const typename Cx<R>::T* __restrict__ W,
+                                                       const int64_t* na, int i0, int m,
+                                                       const KrylovScalars* ks, int k,
+                                                       double* partials) {
+    if (ks->keff <= k) return;
+    const int64_t n = min(*na, (int64_t)cap);
+    Acc<R> ar[kMaxM], ai[kMaxM], an;
+#pragma unroll
+    for (int i = 0; i < kMaxM; ++i) {
+        ar[i].init();
+        ai[i].init();
+    }
+    an.init();
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const auto w = W[p];
+        an.add(w.x * w.x + w.y * w.y);
+#pragma unroll
+        for (int i = 0; i < kMaxM; ++i) {
+            if (i < m) {
+                const auto v = kvec<R>(psi, Vb, cap, i0 + i)[p];
+                // conj(v) * w
+                ar[i].add(v.x * w.x + v.y * w.y);
+                ai[i].add(v.x * w.y - v.y * w.x);
+            }
+        }
+    }
+    double vals[2 * kMaxM + 1];
+#pragma unroll
+    for (int i = 0; i < kMaxM; ++i) {
+        vals[2 * i] = ar[i].value();
+        vals[2 * i + 1] = ai[i].value();
+    }
+    vals[2 * m] = an.value();
+    block_partials(vals, 2 * m + 1, partials);
+}
+
+// Finalise the dots of step k: scale by sigma_i, store, record alpha_k.
+// obs_prev (nullable): E of the previous record = alpha_0.
+__global__ void k_dots_done(const double* partials, int G, int i0, int m, KrylovScalars* ks,
+                            int k, double* obs_prev_E, int64_t* err) {
+    __shared__ double tot[2 * kMaxM + 1];
+    if (ks->keff <= k) return;
+    sum_partials(partials, G, 2 * m + 1, tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < m; ++i) {
+            const double sg = ks->sigma[i0 + i];
+            ks->dots[2 * (i0 + i)] = tot[2 * i] * sg;
+            ks->dots[2 * (i0 + i) + 1] = tot[2 * i + 1] * sg;
+        }
+        if (i0 + m - 1 == k) {
+            ks->alpha[k] = ks->dots[2 * k];
+            ks->hnorm2 = tot[2 * m];
+            if (!isfinite(ks->alpha[k])) *err |= 2;
+            if (k == 0 && obs_prev_E) *obs_prev_E = ks->alpha[0];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- update
+// W <- W - sum_{i in [i0, i0+m)} c_i sigma_i V_i ; optional ||W||^2 partials.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_update(const void* psi, const void* Vb, size_t cap,
+                                                         typename Cx<R>::T* __restrict__ W,
+                                                         const int64_t* na, int i0, int m,
+                                                         const KrylovScalars* ks, int k,
+                                                         int want_norm, double* partials) {
+    if (ks->keff <= k) return;
+    const int64_t n = min(*na, (int64_t)cap);
+    R cr[kMaxM], ci[kMaxM];
+#pragma unroll
+    for (int i = 0; i < kMaxM; ++i) {
+        if (i < m) {
+            const double sg = ks->sigma[i0 + i];
+            cr[i] = (R)(ks->dots[2 * (i0 + i)] * sg);
+            ci[i] = (R)(ks->dots[2 * (i0 + i) + 1] * sg);
+        } else {
+            cr[i] = 0;
+            ci[i] = 0;
+        }
+    }
+    Acc<R> an;
+    an.init();
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        auto w = W[p];
+#pragma unroll
+        for (int i = 0; i < kMaxM; ++i) {
+            if (i < m) {
+                const auto v = kvec<R>(psi, Vb, cap, i0 + i)[p];
+                // w -= c * v  (c complex)
+                w.x -= cr[i] * v.x - ci[i] * v.y;
+                w.y -= cr[i] * v.y + ci[i] * v.x;
+            }
+        }
+        W[p] = w;
+        if (want_norm) an.add(w.x * w.x + w.y * w.y);
+    }
+    if (want_norm) {
+        double vals[1] = {an.value()};
+        block_partials(vals, 1, partials);
+    }
+}
+
+// beta_k = ||W||; breakdown test; sigma_{k+1} = 1/beta_k.
+__global__ void k_update_done(const double* partials, int G, KrylovScalars* ks, int k,
+                              int64_t* err) {
+    __shared__ double tot[1];
+    if (ks->keff <= k) return;
+    sum_partials(partials, G, 1, tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double b = sqrt(tot[0]);
+        if (!isfinite(b)) {
+            *err |= 2;
+            ks->keff = k + 1;
+            return;
+        }
+        if (b <= 1e-12 * sqrt(ks->hnorm2)) {   // invariant subspace: stop here
+            ks->keff = k + 1;
+            ks->beta[k] = 0.0;
+            return;
+        }
+        ks->beta[k] = b;
+        ks->sigma[k + 1] = 1.0 / b;
+    }
+}
+
+// ------------------------------------------------ small exponential
+// exp(-i T dt) e_1 of the keff x keff tridiagonal (cyclic Jacobi, FP64,
+// one thread); coef_j = beta_0 sigma_j [Z exp(-i L dt) Z^T e_1]_j.
+__global__ void k_tridiag_exp(KrylovScalars* ks, double dt) {
+    if (threadIdx.x != 0) return;
+    const int n = ks->keff;
+    if (n <= 0) return;
+    double A[kMaxK * kMaxK], Z[kMaxK * kMaxK];
+    for (int i = 0; i < n * n; ++i) {
+        A[i] = 0.0;
+        Z[i] = 0.0;
+    }
+    for (int i = 0; i < n; ++i) {
+        A[i * n + i] = ks->alpha[i];
+        Z[i * n + i] = 1.0;
+        if (i + 1 < n) A[i * n + i + 1] = A[(i + 1) * n + i] = ks->beta[i];
+    }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, dg = 0.0;
+        for (int i = 0; i < n; ++i) {
+            dg += A[i * n + i] * A[i * n + i];
+            for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+        }
+        if (off <= 1e-32 * (dg + 1e-300)) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                const double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int r = 0; r < n; ++r) {
+                    const double arp = A[r * n + p], arq = A[r * n + q];
+                    A[r * n + p] = c * arp - s * arq;
+                    A[r * n + q] = s * arp + c * arq;
+                }
+                for (int r = 0; r < n; ++r) {
+                    const double apr = A[p * n + r], aqr = A[q * n + r];
+                    A[p * n + r] = c * apr - s * aqr;
+                    A[q * n + r] = s * apr + c * aqr;
+                }
+                for (int r = 0; r < n; ++r) {
+                    const double zrp = Z[r * n + p], zrq = Z[r * n + q];
+                    Z[r * n + p] = c * zrp - s * zrq;
+                    Z[r * n + q] = s * zrp + c * zrq;
+                }
+            }
+    }
+    for (int j = 0; j < n; ++j) {
+        double re = 0.0, im = 0.0;
+        for (int l = 0; l < n; ++l) {
+            double sn, cs;
+            sincos(A[l * n + l] * dt, &sn, &cs);
+            const double wgt = Z[j * n + l] * Z[0 * n + l];
+            re += wgt * cs;
+            im -= wgt * sn;
+        }
+        const double f = ks->beta0 * ks->sigma[j];
+        ks->coef[2 * j] = re * f;
+        ks->coef[2 * j + 1] = im * f;
+    }
+}
+
+// psi <- sum_{j < keff} coef_j V_j  (V_0 is psi itself: read before write).
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_combine(void* psi, const void* Vb, size_t cap,
+                                                          const int64_t* na,
+                                                          const KrylovScalars* ks) {
+    using V = typename Cx<R>::T;
+    const int n_k = ks->keff;
+    if (n_k <= 0) return;
+    const int64_t n = min(*na, (int64_t)cap);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        R ax = 0, ay = 0;
+        for (int j = 0; j < n_k; ++j) {
+            const V v = kvec<R>(psi, Vb, cap, j)[p];
+            const R cr = (R)ks->coef[2 * j], ci = (R)ks->coef[2 * j + 1];
+            ax += cr * v.x - ci * v.y;
+            ay += cr * v.y + ci * v.x;
+        }
+        ((V*)psi)[p] = cmake<R>(ax, ay);
+    }
+}
+
+// ---------------------------------------------------------- observables
+// C = sum conj(a0_I) psi_I with a0_I = prod_k f_k(i_k); ||psi||^2; the number
+// of active points with |a| < theta.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_observe(const uint32_t* __restrict__ keys,
+                                                          const typename Cx<R>::T* __restrict__ psi,
+                                                          const int64_t* na, int64_t cap,
+                                                          Lattice L, const typename Cx<R>::T* fac,
+                                                          double theta2, float lo, float hi,
+                                                          double* partials) {
+    const int64_t n = min(*na, cap);
+    Acc<R> cr, ci, nn;
+    cr.init();
+    ci.init();
+    nn.init();
+    double wasted = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = keys[p];
+        R ar = 1, ai = 0;
+        for (int k = 0; k < L.D; ++k) {
+            const int d = (int)((key / L.stride[k]) % (uint32_t)L.n[k]);
+            const auto f = fac[k * kMaxN + d];
+            const R nr = ar * f.x - ai * f.y;
+            const R ni = ar * f.y + ai * f.x;
+            ar = nr;
+            ai = ni;
+        }
+        const auto v = psi[p];
+        cr.add(ar * v.x + ai * v.y);
+        ci.add(ar * v.y - ai * v.x);
+        nn.add(v.x * v.x + v.y * v.y);
+        bool sig;
+        if (sizeof(R) == 8)
+            sig = significant64((double)v.x, (double)v.y, theta2);
+        else
+            sig = significant32((float)v.x, (float)v.y, theta2, lo, hi);
+        if (!sig) wasted += 1.0;
+    }
+    double vals[4] = {cr.value(), ci.value(), nn.value(), wasted};
+    block_partials(vals, 4, partials);
+}
+
+// rec = [t, C re, C im, norm2, E (filled later), n_active, n_wasted, keff]
+__global__ void k_observe_done(const double* partials, int G, const int64_t* cnt,
+                               const KrylovScalars* ks, double t, double* rec) {
+    __shared__ double tot[4];
+    sum_partials(partials, G, 4, tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        rec[0] = t;
+        rec[1] = tot[0];
+        rec[2] = tot[1];
+        rec[3] = tot[2];
+        rec[4] = 0.0;
+        rec[5] = (double)cnt[CNT_NA];
+        rec[6] = tot[3];
+        rec[7] = ks ? (double)ks->keff : 0.0;
+    }
+}
+
+// ------------------------------------------------------------- drivers
+static void guard(double theta2, float* lo, float* hi) {
+    if (theta2 < 1e-30) {
+        *lo = -1.0f;
+        *hi = 3.0e38f;
+    } else {
+        *lo = (float)(theta2 * (1.0 - 1e-5));
+        *hi = (float)(theta2 * (1.0 + 1e-5));
+    }
+}
+
+template <typename R>
+static pq_status observe_t(State& s, double theta, double* rec, cudaStream_t st) {
+    const int G = red_blocks();
+    float lo, hi;
+    guard(theta * theta, &lo, &hi);
+    const void* fac = sizeof(R) == 8 ? (const void*)s.fac64 : (const void*)s.fac32;
+    k_observe<R><<<G, kRedThreads, 0, st>>>(s.keys, (const typename Cx<R>::T*)s.psi,
+                                            s.cnt + CNT_NA, (int64_t)s.cap, s.lat,
+                                            (const typename Cx<R>::T*)fac, theta * theta, lo, hi,
+                                            s.red_tmp);
+    PQ_CHECK_LAUNCH();
+    k_observe_done<<<1, 64, 0, st>>>(s.red_tmp, G, s.cnt, s.ks, s.t, rec);
+    PQ_CHECK_LAUNCH();
+    return PQ_OK;
+}
+
+static pq_status observe_rec(State& s, double theta, double* rec, cudaStream_t st) {
+    return s.prec == PQ_FP64 ? observe_t<double>(s, theta, rec, st)
+                             : observe_t<float>(s, theta, rec, st);
+}
+
+template <typename R>
+static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaStream_t st) {
+    using V = typename Cx<R>::T;
+    const int G = red_blocks();
+    const size_t cap = s.cap;
+    const int K = d.K;
+    k_norm2<R><<<G, kRedThreads, 0, st>>>((const V*)s.psi, s.cnt + CNT_NA, (int64_t)cap, s.red_tmp);
+    PQ_CHECK_LAUNCH();
+    k_start_step<<<1, 64, 0, st>>>(s.red_tmp, G, s.ks, K, s.cnt + CNT_ERR);
+    PQ_CHECK_LAUNCH();
+    pq_status rc;
+    for (int k = 0; k < K; ++k) {
+        const void* in = k == 0 ? s.psi : (const void*)((V*)s.V + (size_t)(k - 1) * cap);
+        V* W = (V*)s.V + (size_t)k * cap;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (s.timing.enabled) {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, st);
+        }
+        rc = apply_H_launch(s, in, W, s.prec, &s.ks->sigma[k], &s.ks->keff, k, st);
+        if (rc) return rc;
+        if (s.timing.enabled) {
+            cudaEventRecord(e1, st);
+            s.timing.ev_start.push_back(e0);
+            s.timing.ev_stop.push_back(e1);
+        }
+        // which previous vectors to orthogonalise against
+        int i0 = 0;
+        if (k == K - 1) i0 = k;                   // only alpha_k needed
+        else if (!d.reorth) i0 = k > 0 ? k - 1 : 0;
+        for (int c0 = i0; c0 <= k; c0 += kMaxM) {
+            const int m = min(kMaxM, k - c0 + 1);
+            k_dots<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, cap, W, s.cnt + CNT_NA, c0, m, s.ks,
+                                                 k, s.red_tmp);
+            PQ_CHECK_LAUNCH();
+            k_dots_done<<<1, 64, 0, st>>>(s.red_tmp, G, c0, m, s.ks, k, prev_E, s.cnt + CNT_ERR);
+            PQ_CHECK_LAUNCH();
+        }
+        if (k == K - 1) break;
+        for (int c0 = i0; c0 <= k; c0 += kMaxM) {
+            const int m = min(kMaxM, k - c0 + 1);
+            const bool last = c0 + m > k;
+            k_update<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, cap, W, s.cnt + CNT_NA, c0, m, s.ks,
+                                                   k, last ? 1 : 0, s.red_tmp);
+            PQ_CHECK_LAUNCH();
+        }
+        k_update_done<<<1, 64, 0, st>>>(s.red_tmp, G, s.ks, k, s.cnt + CNT_ERR);
+        PQ_CHECK_LAUNCH();
+    }
+    k_tridiag_exp<<<1, 32, 0, st>>>(s.ks, d.dt);
+    PQ_CHECK_LAUNCH();
+    k_combine<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, cap, s.cnt + CNT_NA, s.ks);
+    PQ_CHECK_LAUNCH();
+    return PQ_OK;
+}
+
+pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream_t st) {
+    if (d.K < 1 || d.K > kMaxK) {
+        set_error("Krylov dimension %d outside 1..%d", d.K, kMaxK);
+        return PQ_EINVAL;
+    }
+    if (!(d.dt > 0) || !(d.theta >= 0) || nsteps < 0) {
+        set_error("need dt > 0, theta >= 0, nsteps >= 0");
+        return PQ_EINVAL;
+    }
+    if (d.radius != 1) {
+        set_error("neighbour radius %d not provided (radius 1 only)", d.radius);
+        return PQ_ENOTSUP;
+    }
+    if (s.V_K < d.K) {
+        if (s.V) cudaFree(s.V);
+        s.V = nullptr;
+        s.V_K = 0;
+        cudaError_t e = cudaMalloc(&s.V, (size_t)d.K * s.cap * s.esize);
+        if (e != cudaSuccess) {
+            set_error("cannot allocate the Krylov space (%zu bytes): %s",
+                      (size_t)d.K * s.cap * s.esize, cudaGetErrorString(e));
+            return PQ_ENOMEM;
+        }
+        s.V_K = d.K;
+    }
+    if (nsteps == 0) return PQ_OK;
+    double* recs = nullptr;
+    PQ_CUDA_TRY(cudaMallocAsync((void**)&recs, (size_t)(nsteps + 1) * 8 * sizeof(double), st));
+    PQ_CUDA_TRY(cudaMemsetAsync(recs, 0, (size_t)(nsteps + 1) * 8 * sizeof(double), st));
+    // Slot 0 receives E of the record already on the host (alpha_0 of step 1).
+    pq_status rc = PQ_OK;
+    for (int n = 0; n < nsteps && rc == PQ_OK; ++n) {
+        double* prevE = recs + (size_t)n * 8 + 4;
+        rc = s.prec == PQ_FP64 ? sil_step<double>(s, d, prevE, st) : sil_step<float>(s, d, prevE, st);
+        if (rc) break;
+        rc = prune_launch(s, d.theta, d.radius, st);
+        if (rc) break;
+        s.t += d.dt;
+        rc = observe_rec(s, d.theta, recs + (size_t)(n + 1) * 8, st);
+    }
+    std::vector<double> h((size_t)(nsteps + 1) * 8);
+    cudaError_t e1 = cudaMemcpyAsync(h.data(), recs, h.size() * sizeof(double),
+                                     cudaMemcpyDeviceToHost, st);
+    cudaError_t e2 = cudaMemcpyAsync(s.h_cnt, s.cnt, CNT_SIZE * sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, st);
+    cudaError_t e3 = cudaStreamSynchronize(st);
+    cudaFreeAsync(recs, st);
+    if (rc) return rc;
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        set_error("propagate: %s", cudaGetErrorString(e3 != cudaSuccess ? e3 : (e1 ? e1 : e2)));
+        return PQ_ECUDA;
+    }
+    // E of the previous newest host record
+    if (!s.obs.empty() && s.obs_energy_pending) {
+        s.obs.back().energy = h[4];
+        s.obs_energy_pending = false;
+    }
+    for (int n = 1; n <= nsteps; ++n) {
+        const double* r = &h[(size_t)n * 8];
+        // E of record n is alpha_0 of step n+1, stored in slot n
+        ObsRecord o{r[0], r[1], r[2], r[3], n < nsteps ? r[4] : 0.0, (int64_t)r[5],
+                    (int64_t)r[6]};
+        s.obs.push_back(o);
+    }
+    s.obs_energy_pending = true;
+    if (s.timing.enabled) {
+        for (size_t i = 0; i < s.timing.ev_start.size(); ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, s.timing.ev_start[i], s.timing.ev_stop[i]);
+            s.timing.ms += ms;
+            cudaEventDestroy(s.timing.ev_start[i]);
+            cudaEventDestroy(s.timing.ev_stop[i]);
+        }
+        s.timing.n_apply += (int64_t)s.timing.ev_start.size();
+        // active points per H.psi: the set before each step (record n-1)
+        const size_t base = s.obs.size() - nsteps;
+        for (int n = 0; n < nsteps; ++n) {
+            const double na_before = (double)s.obs[base + n - 1].n_active;
+            s.timing.coef += na_before * d.K;
+        }
+        s.timing.ev_start.clear();
+        s.timing.ev_stop.clear();
+    }
+    const int64_t errw = s.h_cnt[CNT_ERR];
+    if (errw & 1) {
+        set_error("active set outgrew the capacity (%lld > %zu)", (long long)s.h_cnt[CNT_NA], s.cap);
+        return PQ_ECAPACITY;
+    }
+    if (errw & 2) {
+        set_error("non-finite norm or Lanczos coefficient");
+        return PQ_ENUMERIC;
+    }
+    return PQ_OK;
+}
+
+pq_status observe_launch(State& s, double theta, cudaStream_t st) {
+    double* rec = nullptr;
+    PQ_CUDA_TRY(cudaMallocAsync((void**)&rec, 8 * sizeof(double), st));
+    pq_status rc = observe_rec(s, theta, rec, st);
+    double h[8] = {0};
+    cudaMemcpyAsync(h, rec, sizeof(h), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFreeAsync(rec, st);
+    if (rc) return rc;
+    if (e != cudaSuccess) {
+        set_error("observe: %s", cudaGetErrorString(e));
+        return PQ_ECUDA;
+    }
+    s.obs.push_back(ObsRecord{h[0], h[1], h[2], h[3], 0.0, (int64_t)h[5], (int64_t)h[6]});
+    s.obs_energy_pending = true;
+    return PQ_OK;
+}
+
+// E = Re<psi|H psi> / ||psi||^2 of the current state (one extra H.psi).
+template <typename R>
+static pq_status energy_t(State& s, double* E, cudaStream_t st) {
+    using V = typename Cx<R>::T;
+    const int G = red_blocks();
+    void* W = nullptr;
+    PQ_CUDA_TRY(cudaMallocAsync(&W, s.cap * s.esize > 0 ? s.cap * s.esize : 16, st));
+    k_norm2<R><<<G, kRedThreads, 0, st>>>((const V*)s.psi, s.cnt + CNT_NA, (int64_t)s.cap, s.red_tmp);
+    PQ_CHECK_LAUNCH();
+    k_start_step<<<1, 64, 0, st>>>(s.red_tmp, G, s.ks, 1, s.cnt + CNT_ERR);
+    PQ_CHECK_LAUNCH();
+    // W = H (psi / ||psi||); <psi/||psi||, W> is then E
+    pq_status rc = apply_H_launch(s, s.psi, W, s.prec, &s.ks->sigma[0], nullptr, 0, st);
+    if (rc) {
+        cudaFreeAsync(W, st);
+        return rc;
+    }
+    k_dots<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, s.cap, (const V*)W, s.cnt + CNT_NA, 0, 1,
+                                         s.ks, 0, s.red_tmp);
+    PQ_CHECK_LAUNCH();
+    double* dE = nullptr;
+    PQ_CUDA_TRY(cudaMallocAsync((void**)&dE, sizeof(double), st));
+    PQ_CUDA_TRY(cudaMemsetAsync(dE, 0, sizeof(double), st));
+    k_dots_done<<<1, 64, 0, st>>>(s.red_tmp, G, 0, 1, s.ks, 0, dE, s.cnt + CNT_ERR);
+    PQ_CHECK_LAUNCH();
+    double h = 0.0;
+    cudaMemcpyAsync(&h, dE, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFreeAsync(dE, st);
+    cudaFreeAsync(W, st);
+    if (e != cudaSuccess) {
+        set_error("energy: %s", cudaGetErrorString(e));
+        return PQ_ECUDA;
+    }
+    *E = h;
+    return PQ_OK;
+}
+
+pq_status energy_of_current(State& s, double* E, cudaStream_t st) {
+    return s.prec == PQ_FP64 ? energy_t<double>(s, E, st) : energy_t<float>(s, E, st);
+}
+
+}  // namespace pq

@@ -1,0 +1,195 @@
+// Internal declarations shared by the host and device translation units of
+// the pruned-dynamics library.  Not part of the public ABI (see prunedq.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/prunedq.h"
+
+namespace pq {
+
+constexpr int kMaxD = 8;        // modes (a virtual size-1 mode is added for D = 1)
+constexpr int kMaxN = 64;       // points per mode
+constexpr int kMaxTerms = 64;   // potential terms
+constexpr int kMaxK = 32;       // Krylov dimension
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+void clear_error();
+extern std::atomic<int64_t> g_launches;
+
+#define PQ_CUDA_TRY(expr)                                                       \
+    do {                                                                        \
+        cudaError_t e_ = (expr);                                                \
+        if (e_ != cudaSuccess) {                                                \
+            ::pq::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr,          \
+                            cudaGetErrorString(e_));                            \
+            return PQ_ECUDA;                                                    \
+        }                                                                       \
+    } while (0)
+
+#define PQ_LAUNCHED() ::pq::g_launches.fetch_add(1, std::memory_order_relaxed)
+
+#define PQ_CHECK_LAUNCH()                                                       \
+    do {                                                                        \
+        PQ_LAUNCHED();                                                          \
+        cudaError_t e_ = cudaGetLastError();                                    \
+        if (e_ != cudaSuccess) {                                                \
+            ::pq::set_error("%s:%d launch: %s", __FILE__, __LINE__,             \
+                            cudaGetErrorString(e_));                            \
+            return PQ_ECUDA;                                                    \
+        }                                                                       \
+    } while (0)
+
+// ------------------------------------------------------------- lattice
+// Row-major direct-product lattice.  A "row" is a run along the last mode
+// (all digits but the last fixed); a "plane" fixes all digits but the last
+// two.  Bits of the active-set bitmap are in linear-index order, so row r
+// occupies bits [r*nlast, (r+1)*nlast).
+struct Lattice {
+    int D;                      // modes (>= 2 after the virtual leading mode)
+    int n[kMaxD];               // points per mode
+    uint32_t stride[kMaxD];     // linear-index strides
+    uint32_t rstride[kMaxD];    // row-index strides (stride / nlast), modes < D-1
+    uint32_t pstride[kMaxD];    // plane-index strides (stride / (n[D-2] nlast)), modes < D-2
+    uint32_t nfull;             // lattice size
+    uint32_t nrows;             // nfull / nlast
+    uint32_t nplanes;           // nfull / (n[D-2] * nlast)
+    uint32_t nwords;            // 64-bit bitmap words
+    int nlast;                  // n[D-1]
+    // lattice axes used by the neighbour rule of the adaption
+    int naxes;
+    int axis_n[2 * kMaxD];
+    uint32_t axis_stride[2 * kMaxD];
+};
+
+// ------------------------------------------------------------- basis
+struct Basis {
+    int D_user = 0;                       // modes the caller declared
+    std::vector<pq_mode_desc> modes;      // caller's modes
+    std::vector<std::vector<double>> x, w, T;  // per caller mode
+    // SoP Hamiltonian (DVR form): per-mode kinetic scale and potential terms
+    bool sop_set = false;
+    std::vector<double> kin_scale;                 // per caller mode
+    std::vector<double> pot_coef;                  // per potential term
+    std::vector<std::vector<double>> pot_values;   // [term][mode*n_mode + i] (1 for identity)
+};
+
+pq_status build_dvr_mode(const pq_mode_desc& m, std::vector<double>& x,
+                         std::vector<double>& w, std::vector<double>& T);
+// Normalised packet factors f_k(i) = sqrt(w_i) g_k(x_i) / ||.||, complex interleaved.
+void packet_factors(const Basis& b, const double* q0, const double* p0, const double* width,
+                    std::vector<double>& out /* D_int * kMaxN * 2 */, int lead_virtual);
+int jacobi_eigh(int n, std::vector<double>& A, std::vector<double>& evals,
+                std::vector<double>& evecs);
+
+// ------------------------------------------------------------- state
+struct Timing {
+    bool enabled = false;
+    double ms = 0;
+    int64_t n_apply = 0;
+    double coef = 0;
+    std::vector<cudaEvent_t> ev_start, ev_stop;   // pairs per recorded apply
+    std::vector<int64_t> ev_coef_slot;            // unused placeholder
+};
+
+struct ObsRecord {
+    double t, c_re, c_im, norm2, energy;
+    int64_t n_active, n_wasted;
+};
+
+// Device-side per-state counters (one int64 array).
+enum Counter : int {
+    CNT_NA = 0,        // active points
+    CNT_ROWS = 1,      // active rows
+    CNT_PLANES = 2,    // active planes
+    CNT_ERR = 3,       // error bits (1: capacity overflow, 2: numeric)
+    CNT_NA_OLD = 4,    // active points before the last rebuild
+    CNT_LEAD0 = 8,     // fibre leaders of outer mode k at CNT_LEAD0 + k
+    CNT_SIZE = 16
+};
+
+// Device scalars of the Krylov step (FP64).
+struct KrylovScalars {
+    double beta0;                 // ||psi||
+    double sigma[kMaxK + 1];      // scale of stored Krylov vector k
+    double alpha[kMaxK];
+    double beta[kMaxK];
+    double dots[2 * (kMaxK + 1)]; // <V_i, W> (re, im) of the current step
+    double hnorm2;                // ||W||^2 before orthogonalisation
+    double coef[2 * kMaxK];       // final combination coefficients (re, im)
+    int keff;                     // Krylov dimension reached (breakdown)
+    int pad;
+    double obs[8];                // C re, C im, norm2, wasted (as double)
+};
+
+struct State {
+    const Basis* basis = nullptr;
+    Lattice lat{};
+    int prec = PQ_FP64;
+    int lead_virtual = 0;          // 1 if a virtual size-1 leading mode was added
+    size_t cap = 0;                // capacity (active points)
+    size_t esize = 16;             // bytes per coefficient
+    // device buffers
+    uint32_t* keys = nullptr;      // sorted active linear indices
+    void* psi = nullptr;           // coefficients
+    void* psi_alt = nullptr;       // prune target / apply scratch
+    uint64_t* bits = nullptr;      // active-set bitmap
+    uint64_t* bits_alt = nullptr;
+    uint32_t* off = nullptr;       // rank offsets (exclusive popcount prefix), nwords+1
+    uint32_t* off_alt = nullptr;
+    uint32_t* rows = nullptr;      // active row ids
+    uint32_t* planes = nullptr;    // active plane ids
+    uint32_t* leaders = nullptr;   // fibre leaders, (D-2) lists of nrows_cap entries
+    size_t rows_cap = 0;
+    int64_t* cnt = nullptr;        // counters (CNT_*)
+    uint32_t* scan_tmp = nullptr;  // block sums of the scans
+    double* red_tmp = nullptr;     // block partials of the reductions
+    KrylovScalars* ks = nullptr;   // device Krylov scalars
+    void* V = nullptr;             // Krylov vectors, (K+1) * cap
+    int V_K = 0;
+    // Hamiltonian tables (device), both precisions
+    double* T64 = nullptr;  float* T32 = nullptr;      // [D][kMaxN][kMaxN]
+    double* pot64 = nullptr; float* pot32 = nullptr;   // [nterms][D][kMaxN]
+    int nterms = 0;
+    double* fac64 = nullptr; float* fac32 = nullptr;   // packet factors [D][kMaxN] complex
+    // host side
+    double t = 0;
+    std::vector<ObsRecord> obs;
+    bool obs_energy_pending = false;
+    double theta = 0;
+    int radius = 1;
+    Timing timing;
+    int64_t* h_cnt = nullptr;      // pinned mirror of cnt
+    void* io_in = nullptr;         // staging buffers of pq_apply_H_host
+    void* io_out = nullptr;
+    cudaStream_t last_stream = nullptr;
+};
+
+// lattice.cu
+pq_status lattice_setup(State& s);
+pq_status rebuild_from_bits(State& s, bool remap, cudaStream_t st);
+pq_status prune_launch(State& s, double theta, int radius, cudaStream_t st);
+pq_status init_bits_from_packet(State& s, double theta, cudaStream_t st);
+pq_status set_psi_from_packet(State& s, cudaStream_t st);
+pq_status load_set(State& s, const uint32_t* d_keys, int64_t n, cudaStream_t st);
+int grid_size();
+
+// apply_h.cu
+// in_scale (device, nullable): the input is multiplied by *in_scale on load.
+// skip (device, nullable): the launch does nothing when *skip <= skip_k.
+pq_status apply_H_launch(const State& s, const void* in, void* out, int prec,
+                         const double* in_scale, const int* skip, int skip_k,
+                         cudaStream_t st);
+
+// krylov.cu
+pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream_t st);
+pq_status observe_launch(State& s, double theta, cudaStream_t st);
+pq_status energy_of_current(State& s, double* E, cudaStream_t st);
+
+}  // namespace pq

@@ -1,0 +1,77 @@
+"""CPU checks of the C ABI: the library loads, exports every function that
+include/prunedq.h declares, and its host-side basis construction (no GPU
+needed) agrees with the oracle's independent construction."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    try:
+        import paper_1606_04004_gb300 as pq
+    except ImportError as e:   # the library must be built first
+        pytest.fail(f"library not built: {e}")
+    return pq
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "prunedq.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pq_[A-Za-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_symbols_exported():
+    import ctypes
+    pq = _lib()
+    lib = ctypes.CDLL(pq.lib_path())
+    names = declared_functions()
+    assert "pq_apply_H" in names and "pq_propagate" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(pq.EXPORTS)
+
+
+def test_host_bases_match_oracle():
+    from oracle import bases
+    pq = _lib()
+    b = pq.Basis(pq.modes_of(W.HH4D))
+    x, w, T = bases.ho_dvr(24)
+    xl, wl = b.grid(0)
+    np.testing.assert_allclose(xl, x, atol=1e-13)
+    np.testing.assert_allclose(wl, w, rtol=1e-12)
+    np.testing.assert_allclose(b.kinetic(0), T, atol=1e-12)
+    b = pq.Basis(pq.modes_of(W.MORSE2D))
+    x, w, T = bases.sine_dvr(32, 0.5, 6.0, 1836.0)
+    xl, wl = b.grid(1)
+    np.testing.assert_allclose(xl, x, atol=1e-14)
+    np.testing.assert_allclose(wl, w, rtol=1e-14)
+    np.testing.assert_allclose(b.kinetic(1), T, atol=1e-14 * abs(T).max())
+
+
+def test_argument_errors():
+    pq = _lib()
+    with pytest.raises(pq.PQError) as e:
+        pq.Basis([dict(kind=pq.SINE_DVR, n=1, xmin=0, xmax=1, mass=1)])
+    assert e.value.status == pq.EINVAL
+    with pytest.raises(pq.PQError) as e:
+        pq.Basis([dict(kind=pq.HO_DVR, n=65)])
+    assert e.value.status == pq.EINVAL
+    with pytest.raises(pq.PQError) as e:   # 64^6 > 2^32
+        pq.Basis([dict(kind=pq.HO_DVR, n=64)] * 6)
+    assert e.value.status == pq.EINVAL
+    with pytest.raises(pq.PQError) as e:
+        pq.Basis([dict(kind=pq.PW, n=16)])
+    assert e.value.status == pq.ENOTSUP
+    b = pq.Basis(pq.modes_of(W.scaled(W.HH4D, D=2)))
+    with pytest.raises(pq.PQError) as e:   # kinetic times a diagonal factor
+        b.set_sop([(1.0, ["T", np.ones(24)])])
+    assert e.value.status == pq.ENOTSUP
+    with pytest.raises(pq.PQError) as e:
+        b.set_sop([(float("nan"), [None, None])])
+    assert e.value.status == pq.EINVAL

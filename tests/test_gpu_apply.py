@@ -1,0 +1,115 @@
+"""GPU parity of the pruned H.psi (Sec. 2.2.2 / Appendix) against the FP64
+oracle, element by element, through the C ABI.
+
+Tolerances: FP64 |y_gpu - y| <= 1e-13 * s_I, FP32 |y_gpu - y| <= 4e-6 * s_I,
+where s_I is the same sum taken with |T|, |V| and |psi| (a rounding bound:
+at most ~130 terms of unit roundoff 1.1e-16 resp. 6e-8)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import ho_problem, lib, rel_bound, state_with, vdiag_of
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-13, 1: 4e-6}
+
+
+def _run(dims, A, seed, prec, nterms=3):
+    import torch
+    from oracle import pruned
+    pq = lib()
+    b, Ts, pot = ho_problem(dims, seed, nterms)
+    psi = W.random_psi(len(A), seed + 1)
+    dt = np.complex128 if prec == pq.FP64 else np.complex64
+    psi = psi.astype(dt)
+    s = state_with(b, A, psi, prec)
+    assert s.size() == len(A)
+    idx, p2 = s.read()
+    np.testing.assert_array_equal(idx, A)
+    np.testing.assert_array_equal(p2, psi)
+    tdt = torch.complex128 if prec == pq.FP64 else torch.complex64
+    x = torch.from_numpy(psi).to("cuda")
+    y = torch.empty_like(x)
+    s.apply_H(x, y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.complex128)
+    vd = vdiag_of(pot, A, dims)
+    ref = pruned.apply_H(A, psi.astype(np.complex128), dims, Ts, vd)
+    bound = rel_bound(Ts, A, psi, dims, vd)
+    err = np.abs(got - ref)
+    assert np.all(err <= TOL[prec] * bound + 1e-300), (err / np.maximum(bound, 1e-300)).max()
+    # host-buffer entry point gives the same numbers
+    got_h = s.apply_H_host(psi)
+    np.testing.assert_array_equal(got_h, y.cpu().numpy())
+    return s
+
+
+CASES = [
+    ((8, 9), 0.6),            # 2D: one plane
+    ((6, 7, 5), 0.5),         # 3D: one outer mode
+    ((5, 4, 6, 7), 0.4),      # 4D, ragged, two outer modes
+    ((3, 4, 2, 3, 5), 0.7),   # 5D
+    ((5, 64), 0.5),           # last mode 64 wide (two lanes per warp column)
+    ((64, 3, 5), 0.3),        # an outer mode 64 long
+    ((17,), 0.8),             # 1D (virtual leading mode)
+    ((33, 40), 1.0),          # full lattice (unpruned)
+]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dims,frac", CASES)
+def test_apply_random_sets(dims, frac, prec):
+    A = W.random_active_set(dims, frac, seed=len(dims) * 7 + int(frac * 10))
+    _run(dims, A, 5, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_ellipsoid_4d(prec):
+    dims = (24, 24, 24, 24)
+    A = W.ellipsoid_active_set(dims, (9, 8, 10, 7))
+    _run(dims, A, 9, prec, nterms=6)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_empty_and_single(prec):
+    import torch
+    pq = lib()
+    dims = (6, 5, 4)
+    b, Ts, pot = ho_problem(dims, 3)
+    s = state_with(b, np.zeros(0, np.int64), None, prec)
+    assert s.size() == 0
+    tdt = torch.complex128 if prec == pq.FP64 else torch.complex64
+    x = torch.zeros(1, dtype=tdt, device="cuda")
+    y = torch.zeros(1, dtype=tdt, device="cuda")
+    s.apply_H(x, y)
+    torch.cuda.synchronize()
+    _run(dims, np.array([37]), 4, prec)
+
+
+def test_apply_hh6d_initial_state_sampled():
+    """Full-size 6D Henon-Heiles workload (24^6 lattice), FP32 H.psi in the
+    launch configuration the benchmark times, checked on a sample of outputs
+    the oracle computes one by one."""
+    import torch
+    from oracle import pruned, propagate
+    pq = lib()
+    cfg = W.HH6D
+    b = pq.build_model(cfg)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP32MIX)
+    A, psi = s.read()
+    assert len(A) > 1_000_000
+    x = torch.from_numpy(psi).to("cuda")
+    y = torch.empty_like(x)
+    s.apply_H(x, y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.complex128)
+    prob = propagate.problem_from_config(cfg)
+    rng = np.random.default_rng(0)
+    pos = np.unique(np.concatenate([rng.integers(0, len(A), 4000), [0, len(A) - 1]]))
+    vd = prob.vdiag(A[pos])
+    ref = pruned.apply_H_at(A, psi.astype(np.complex128), prob.dims, prob.Ts, vd, pos)
+    scale = pruned.apply_H_at(A, np.abs(psi).astype(np.complex128), prob.dims,
+                              [np.abs(T) for T in prob.Ts], np.abs(vd), pos).real
+    err = np.abs(got[pos] - ref)
+    assert np.all(err <= 4e-6 * scale + 1e-30), (err / scale).max()

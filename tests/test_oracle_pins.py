@@ -123,6 +123,19 @@ def test_pruned_apply_equals_PHP(dims, frac, seed):
     np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-12)
 
 
+def test_pruned_apply_at_sample_equals_full():
+    dims = (5, 4, 6)
+    rng = np.random.default_rng(11)
+    Ts = [rng.standard_normal((d, d)) for d in dims]
+    A = W.random_active_set(dims, 0.5, 11)
+    psi = W.random_psi(len(A), 12)
+    v = rng.standard_normal(len(A))
+    y = pruned.apply_H(A, psi, dims, Ts, v)
+    pos = np.array([0, 3, len(A) - 1, len(A) // 2])
+    np.testing.assert_allclose(pruned.apply_H_at(A, psi, dims, Ts, v[pos], pos), y[pos],
+                               rtol=1e-13, atol=1e-13)
+
+
 def test_pruned_apply_empty():
     y = pruned.apply_H(np.zeros(0, np.int64), np.zeros(0, complex), (3, 4),
                        [np.eye(3), np.eye(4)], np.zeros(0))
