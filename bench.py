@@ -1,0 +1,379 @@
+"""Throughput of the pruned H.psi inside full propagation steps on one GB300.
+
+Workload (default): 6D Henon-Heiles chain, lambda = 0.111803, HO-DVR 24 points
+per mode (24^6 = 1.91e8 lattice points), coherent packet at q_k = 2, threshold
+1e-6, SIL order 10, dt = 0.1, complex64 H.psi with FP64 Lanczos scalars.  A
+step is one SIL step (10 H.psi) + adaption + observables.
+
+value     active-coefficient H.psi applications per second (Gcoef/s) over the
+          timed steps, inputs resident in HBM.
+e2e       the same metric through the host-buffer C-ABI call pq_apply_H_host
+          (copies from pinned host memory and back inside the timed region).
+roofline  the pruned H.psi (all its passes) against the measured HBM copy
+          bandwidth, with 20 algorithmic bytes per active coefficient
+          (psi read 8 B, H.psi write 8 B, index 4 B).
+cpu_baseline / --impl reference: the FP64 oracle's H.psi on a bounded sample
+          of output points of the same state, on the host cores.
+
+Replicas only: under torchrun every rank runs its own independent replica of
+the workload on its own GPU; value = all ranks' coefficients / the slowest
+rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+BYTES_PER_COEF = {"fp32mix": 20, "fp64": 36}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _traffic_record():
+    """DRAM bytes per active coefficient of the H.psi kernels from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "apply_h_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    src = os.path.join(ROOT, "paper_1606_04004_gb300", "csrc", "apply_h.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if rec.get("apply_h_sha256") != h:
+        return None
+    return rec
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample_rate(cfg, A, psi, n_sample, seed=0):
+    """The FP64 oracle's pruned H.psi on n_sample output points of (A, psi):
+    returns (coefficients per second, seconds, sample size)."""
+    from oracle import propagate, pruned
+    prob = propagate.problem_from_config(cfg)
+    rng = np.random.default_rng(seed)
+    pos = np.sort(rng.choice(len(A), size=min(n_sample, len(A)), replace=False))
+    t0 = time.perf_counter()
+    vd = prob.vdiag(A[pos])
+    pruned.apply_H_at(A, psi.astype(np.complex128), prob.dims, prob.Ts, vd, pos)
+    dt = time.perf_counter() - t0
+    return len(pos) / dt, dt, len(pos)
+
+
+def run_reference(args, cfg):
+    """--impl reference: the oracle, as it stands, on the host cores."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    from oracle import propagate
+    prob = propagate.problem_from_config(cfg)
+    A, a, _ = propagate.initial_state(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"])
+    n_sample = max(1000, args.ref_sample // 4)
+    rates, secs = [], []
+    for i in range(args.warmup + args.steps):
+        r, dt, n = oracle_sample_rate(cfg, A, a, n_sample, seed=i)
+        if i >= args.warmup:
+            rates.append(r)
+            secs.append(dt)
+    v = len(rates) * n_sample / sum(secs) / 1e9
+    line = {
+        "impl": "reference", "metric": "pruned H.psi active-coefficient applications per second",
+        "value": v, "unit": "Gcoef/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "lattice": f"{cfg['n']}^{cfg['D']}",
+                   "theta": cfg["theta"], "n_active": int(len(A))},
+        "cpu_baseline": {"value": v, "unit": "Gcoef/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n_sample} output points of the initial {cfg['name']} "
+                                   f"state per step (numpy, FP64)"},
+        "e2e": {"value": v, "unit": "Gcoef/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, cfg):
+    import torch
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1606_04004_gb300 as pq
+
+    prec = pq.FP32MIX if args.precision == "fp32mix" else pq.FP64
+    b = pq.build_model(cfg)
+    cap = args.capacity
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=prec, capacity=cap)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    K, dt, th = cfg["K"], cfg["dt"], cfg["theta"]
+    # warm-up steps (untimed)
+    s.propagate(K, dt, th, args.warmup, stream=sptr)
+    n_before = len(s.observables()["n_active"])
+    s.set_timing(True)
+    launches0 = pq.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        s.propagate(K, dt, th, args.steps, stream=sptr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = pq.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    obs = s.observables()
+    na = obs["n_active"]
+    coef = float(np.sum(na[n_before - 1:n_before - 1 + args.steps])) * K
+    tm = s.timing()
+    if dist:
+        t = torch.tensor([ms, coef], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, coef_all = float(tmax[0]), float(t[1])
+    else:
+        ms_max, coef_all = ms, coef
+    value = coef_all / (ms_max * 1e-3) / 1e9
+
+    # roofline of the pruned H.psi (all passes), timed with CUDA events on
+    # the propagation stream inside the timed region
+    peak, peak_kind = _peaks()
+    bpc = BYTES_PER_COEF[args.precision]
+    apply_s = tm["apply_ms"] * 1e-3
+    achieved = tm["coef_applied"] * bpc / apply_s / 1e9 if apply_s > 0 else 0.0
+    trec = _traffic_record()
+    traffic = None
+    if trec and args.precision == "fp32mix" and cfg["name"] == trec.get("workload"):
+        traffic = trec["dram_bytes_per_coef"] * tm["coef_applied"] / max(tm["n_apply"], 1)
+
+    # e2e: the host-buffer C-ABI call on the final state
+    A_n = s.size()
+    hdt = torch.complex64 if prec == pq.FP32MIX else torch.complex128
+    xh = torch.randn(A_n, dtype=hdt).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    import ctypes
+    lib = pq._lib
+    for _ in range(2):
+        lib.pq_apply_H_host(s._h, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(yh.data_ptr()),
+                            prec, ctypes.c_void_p(sptr))
+    reps = max(3, args.steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        rc = lib.pq_apply_H_host(s._h, ctypes.c_void_p(xh.data_ptr()),
+                                 ctypes.c_void_p(yh.data_ptr()), prec, ctypes.c_void_p(sptr))
+        if rc:
+            raise RuntimeError(lib.pq_last_error().decode())
+    e2e_s = (time.perf_counter() - t0) / reps
+    esz = 8 if prec == pq.FP32MIX else 16
+    e2e = {"value": A_n / e2e_s / 1e9 * ws, "unit": "Gcoef/s",
+           "h2d_bytes_per_step": A_n * esz, "d2h_bytes_per_step": A_n * esz}
+
+    line = {
+        "metric": "pruned H.psi active-coefficient applications per second",
+        "value": value, "unit": "Gcoef/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64" if prec == pq.FP32MIX else "c128",
+        "data": "synthetic",
+        "config": {"workload": f"{cfg['name']}: {cfg['D']}D Henon-Heiles chain, HO-DVR "
+                               f"{cfg['n']}^{cfg['D']}, theta {cfg['theta']}, SIL K={K}, dt={dt}",
+                   "precision": args.precision, "n_active_first": int(na[n_before - 1]),
+                   "n_active_last": int(na[-1]), "parallelism": f"replicas{ws}",
+                   "l2": "working set larger than L2 (Krylov space of 10 vectors)"},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "pruned H.psi (inner + outer fibre passes)",
+                     "bytes_per_coef": bpc, "peak_kind": peak_kind,
+                     "apply_gcoef_s": tm["coef_applied"] / apply_s / 1e9 if apply_s else None},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+
+    if rank == 0 and ws == 1 and not args.no_fp64_compare and prec == pq.FP32MIX:
+        # the same steps on the plain FP64 GPU path, from the same initial state
+        s64 = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP64,
+                       capacity=cap)
+        s64.propagate(K, dt, th, args.warmup, stream=sptr)
+        s64.set_timing(True)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.propagate(K, dt, th, args.steps, stream=sptr)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        o64 = s64.observables()
+        ms64 = f0.elapsed_time(f1)
+        coef64 = float(np.sum(o64["n_active"][n_before - 1:n_before - 1 + args.steps])) * K
+        v64 = coef64 / (ms64 * 1e-3) / 1e9
+        n = min(len(o64["C"]), len(obs["C"]))
+        line["fp64_gpu"] = {"value": v64, "unit": "Gcoef/s", "speedup_fp32mix": value / v64,
+                            "max_abs_dC": float(np.max(np.abs(o64["C"][:n] - obs["C"][:n]))),
+                            "max_abs_dnorm2": float(np.max(np.abs(o64["norm2"][:n] - obs["norm2"][:n])))}
+        s64.free()
+
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        A, psi = s.read()
+        r, secs, nsamp = oracle_sample_rate(cfg, A, psi, args.ref_sample)
+        line["cpu_baseline"] = {"value": r / 1e9, "unit": "Gcoef/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{nsamp} output points of the final state "
+                                          f"({len(A)} active), FP64 numpy, {secs:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_apply(args, cfg):
+    """H.psi microbenchmark: the workload's Hamiltonian on a synthetic 6D
+    ellipsoid active set (realistic ragged fibres), random complex psi, an L2
+    flush between launches, CUDA events on the launching stream."""
+    import torch
+    import paper_1606_04004_gb300 as pq
+    prec = pq.FP32MIX if args.precision == "fp32mix" else pq.FP64
+    b = pq.build_model(cfg)
+    r = args.radius
+    A = W.ellipsoid_active_set((cfg["n"],) * cfg["D"], (r,) * cfg["D"])
+    s = pq.State(b, [0.0] * cfg["D"], [0.0] * cfg["D"], [1.0] * cfg["D"], 1e30, precision=prec,
+                 capacity=len(A))
+    s.load(A)
+    tdt = torch.complex64 if prec == pq.FP32MIX else torch.complex128
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(len(A), dtype=tdt, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        s.apply_H(x, y)
+    times = []
+    for _ in range(args.reps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.apply_H(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    med = statistics.median(times) * 1e-3
+    peak, kind = _peaks()
+    bpc = BYTES_PER_COEF[args.precision]
+    print(json.dumps({"mode": "apply", "workload": cfg["name"], "precision": args.precision,
+                      "n_active": int(len(A)), "radius": r, "median_us": med * 1e6,
+                      "gcoef_s": len(A) / med / 1e9, "achieved_gbs": len(A) * bpc / med / 1e9,
+                      "frac_hbm": len(A) * bpc / med / 1e9 / peak, "peak": peak,
+                      "peak_kind": kind, "reps": args.reps}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="hh6d")
+    ap.add_argument("--precision", default="fp32mix", choices=["fp32mix", "fp64"])
+    ap.add_argument("--capacity", type=int, default=40_000_000)
+    ap.add_argument("--ref-sample", type=int, default=200_000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--mode", default="step", choices=["step", "apply"])
+    ap.add_argument("--radius", type=float, default=11.2)
+    ap.add_argument("--reps", type=int, default=20)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("need at least 3 warm-up steps")
+    cfg = W.CONFIGS[args.config]
+    if args.mode == "apply":
+        run_apply(args, cfg)
+    elif args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

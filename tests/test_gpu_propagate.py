@@ -104,7 +104,7 @@ def test_theta0_full_krylov_is_exact():
 
 def test_energy_and_norm_conserved_unpruned():
     pq = lib()
-    cfg = W.scaled(W.HH4D, D=2)
+    cfg = W.scaled(W.HH4D, D=2, q0=(2.0, 2.0), p0=(0.0, 0.0), width=(0.5 ** 0.5,) * 2)
     s, o = _gpu(cfg, 30, pq.FP64, theta=0.0)
     assert np.max(np.abs(o["norm2"] - o["norm2"][0])) < 1e-12
     assert np.max(np.abs(o["energy"] - o["energy"][0])) < 1e-11 * abs(o["energy"][0])

@@ -88,14 +88,22 @@ def random_active_set(dims, frac: float, seed: int) -> np.ndarray:
 def ellipsoid_active_set(dims, radii, centre=None) -> np.ndarray:
     """Sorted int64 linear indices of the lattice points inside the ellipsoid
     sum_k ((i_k - c_k) / r_k)^2 <= 1 (the shape a Gaussian packet's active set
-    takes); ``centre`` defaults to the lattice centre."""
+    takes); ``centre`` defaults to the lattice centre.  Built one value of the
+    first digit at a time so that 6D lattices fit in host memory."""
     dims = tuple(int(d) for d in dims)
     if centre is None:
         centre = [(d - 1) / 2.0 for d in dims]
-    acc = np.zeros(dims, dtype=np.float64)
-    for k, d in enumerate(dims):
-        shape = [1] * len(dims)
-        shape[k] = d
-        g = ((np.arange(d) - centre[k]) / radii[k]) ** 2
-        acc = acc + g.reshape(shape)
-    return np.flatnonzero(acc.ravel() <= 1.0).astype(np.int64)
+    rest = np.zeros(dims[1:], dtype=np.float64) if len(dims) > 1 else np.zeros(())
+    for k, d in enumerate(dims[1:], start=1):
+        shape = [1] * (len(dims) - 1)
+        shape[k - 1] = d
+        rest = rest + (((np.arange(d) - centre[k]) / radii[k]) ** 2).reshape(shape)
+    rest = rest.ravel()
+    stride0 = rest.size
+    out = []
+    for i0 in range(dims[0]):
+        lim = 1.0 - ((i0 - centre[0]) / radii[0]) ** 2
+        if lim < 0:
+            continue
+        out.append(np.flatnonzero(rest <= lim).astype(np.int64) + i0 * stride0)
+    return np.concatenate(out) if out else np.zeros(0, np.int64)
