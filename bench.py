@@ -356,7 +356,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="hh6d")
     ap.add_argument("--precision", default="fp32mix", choices=["fp32mix", "fp64"])
-    ap.add_argument("--capacity", type=int, default=40_000_000)
+    ap.add_argument("--capacity", type=int, default=0)   # 0 = the full lattice
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")

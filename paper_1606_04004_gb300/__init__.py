@@ -15,7 +15,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libprunedq.so")
+# PQ_LIBRARY selects another build of the same library (e.g. the
+# self-checking libprunedq_checked.so).
+_LIB_PATH = os.environ.get("PQ_LIBRARY") or os.path.join(_HERE, "libprunedq.so")
 
 if not os.path.exists(_LIB_PATH):
     raise ImportError(

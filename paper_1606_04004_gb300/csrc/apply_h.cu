@@ -42,6 +42,8 @@ struct ApplyArgs {
     int nterms;
     int mode;                   // outer mode k (outer pass only)
     int wpb;                    // warps per block
+    int64_t* cnt;               // state counters (bounds-check build)
+    uint64_t units_cap;         // entries of the units array (bounds-check build)
 };
 
 __device__ __forceinline__ uint64_t low_mask(int s) {
@@ -52,6 +54,9 @@ template <typename R>
 __global__ void __launch_bounds__(kApplyThreads) k_apply_inner(ApplyArgs<R> a) {
     using V = typename Cx<R>::T;
     if (a.skip && *a.skip <= a.skip_k) return;
+    // an active set that outgrew the capacity leaves positions beyond the
+    // buffers: do nothing until the host sees the error
+    if (a.cnt[CNT_ERR] & 1) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const Lattice& L = a.L;
     const int D = L.D, n2 = L.n[D - 2], nl = L.nlast, nt = a.nterms;
@@ -85,10 +90,16 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_inner(ApplyArgs<R> a) {
     R* pref = pref_all + (size_t)kMaxTerms * w;
     const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
     const int64_t nunits = *a.nunits;
+#ifdef PQ_BOUNDS_CHECK
+    const uint64_t na = (uint64_t)a.cnt[CNT_NA];
+#else
+    const uint64_t na = 0;
+#endif
 
     for (int64_t u = (int64_t)blockIdx.x * a.wpb + w; u < nunits;
          u += (int64_t)gridDim.x * a.wpb) {
         const uint32_t P = a.units[u];
+        if (!pq_in_bounds(P, L.nplanes, 1, a.cnt)) continue;
         for (int j = lane; j < n2; j += 32) {
             const uint32_t r = P * (uint32_t)n2 + (uint32_t)j;
             const uint64_t b = row_bits(a.bits, r, nl);
@@ -114,7 +125,9 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_inner(ApplyArgs<R> a) {
             const uint32_t st = rstart[j];
             for (int s = lane; s < nl; s += 32)
                 if ((b >> s) & 1ull) {
-                    V v = a.in[st + __popcll(b & low_mask(s))];
+                    const uint32_t pos = st + __popcll(b & low_mask(s));
+                    if (!pq_in_bounds(pos, na, 2, a.cnt)) continue;
+                    V v = a.in[pos];
                     v.x *= scale;
                     v.y *= scale;
                     tile[j * nl + s] = v;
@@ -148,7 +161,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_inner(ApplyArgs<R> a) {
                 const V c = trow[s];
                 ax += vv * c.x;
                 ay += vv * c.y;
-                a.out[st + __popcll(b & low_mask(s))] = cmake<R>(ax, ay);
+                const uint32_t pos = st + __popcll(b & low_mask(s));
+                if (pq_in_bounds(pos, na, 3, a.cnt)) a.out[pos] = cmake<R>(ax, ay);
             }
         }
         __syncwarp();
@@ -159,6 +173,9 @@ template <typename R>
 __global__ void __launch_bounds__(kApplyThreads) k_apply_outer(ApplyArgs<R> a) {
     using V = typename Cx<R>::T;
     if (a.skip && *a.skip <= a.skip_k) return;
+    // an active set that outgrew the capacity leaves positions beyond the
+    // buffers: do nothing until the host sees the error
+    if (a.cnt[CNT_ERR] & 1) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const Lattice& L = a.L;
     const int k = a.mode, nk = L.n[k], nl = L.nlast;
@@ -179,16 +196,25 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_outer(ApplyArgs<R> a) {
     uint32_t* rstart = rstart_all + (size_t)kMaxN * w;
     const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
     const int64_t nunits = *a.nunits;
+#ifdef PQ_BOUNDS_CHECK
+    const uint64_t na = (uint64_t)a.cnt[CNT_NA];
+#else
+    const uint64_t na = 0;
+#endif
 
     for (int64_t u = (int64_t)blockIdx.x * a.wpb + w; u < nunits;
          u += (int64_t)gridDim.x * a.wpb) {
+        if (!pq_in_bounds((uint64_t)u, a.units_cap, 11, a.cnt)) continue;
         const uint32_t r0 = a.units[u];
+        if (!pq_in_bounds(r0, L.nrows, 4, a.cnt)) continue;
         const int i0 = (int)((r0 / rs) % (uint32_t)nk);
         for (int j = lane; j < nk; j += 32) {
             uint64_t b = 0;
             uint32_t st = 0;
             if (j >= i0) {
                 const uint32_t r = r0 + (uint32_t)(j - i0) * rs;
+                if (!pq_in_bounds(r, L.nrows, 12, a.cnt)) continue;
+                if (!pq_in_bounds(((uint64_t)r * nl + nl - 1) >> 6, L.nwords, 13, a.cnt)) continue;
                 b = row_bits(a.bits, r, nl);
                 if (b) st = rank_of(a.bits, a.off, (uint64_t)r * nl);
             }
@@ -205,7 +231,10 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_outer(ApplyArgs<R> a) {
             const uint32_t st = rstart[j];
             for (int s = lane; s < nl; s += 32)
                 if ((b >> s) & 1ull) {
-                    V v = a.in[st + __popcll(b & low_mask(s))];
+                    const uint32_t pos = st + __popcll(b & low_mask(s));
+                    if (!pq_in_bounds(pos, na, 5, a.cnt)) continue;
+                    if (!pq_in_bounds((uint64_t)(j * nl + s), tile_elems, 14, a.cnt)) continue;
+                    V v = a.in[pos];
                     v.x *= scale;
                     v.y *= scale;
                     tile[j * nl + s] = v;
@@ -220,13 +249,17 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_outer(ApplyArgs<R> a) {
             for (int s = lane; s < nl; s += 32) {
                 if (!((b >> s) & 1ull)) continue;
                 R ax = 0, ay = 0;
+                if (!pq_in_bounds((uint64_t)(jhi * nl + s), tile_elems, 15, a.cnt)) continue;
+                if (!pq_in_bounds((uint64_t)(j * nk + jhi), (uint64_t)nk * nk, 16, a.cnt)) continue;
                 for (int jj = i0; jj <= jhi; ++jj) {
                     const R t = tk[jj];
                     const V c = tile[jj * nl + s];
                     ax += t * c.x;
                     ay += t * c.y;
                 }
-                V* o = a.out + st + __popcll(b & low_mask(s));
+                const uint32_t pos = st + __popcll(b & low_mask(s));
+                if (!pq_in_bounds(pos, na, 6, a.cnt)) continue;
+                V* o = a.out + pos;
                 V ov = *o;
                 ov.x += ax;
                 ov.y += ay;
@@ -268,6 +301,7 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
     a.T = sizeof(R) == 8 ? (const R*)s.T64 : (const R*)s.T32;
     a.pot = sizeof(R) == 8 ? (const R*)s.pot64 : (const R*)s.pot32;
     a.nterms = s.nterms;
+    a.cnt = s.cnt;
     static bool attr_set[2][2] = {{false, false}, {false, false}};
     const int pi = sizeof(R) == 8 ? 1 : 0;
     if (!attr_set[pi][0]) {
@@ -285,6 +319,7 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         const size_t sm = smem_inner(L, s.nterms, wpb, esz);
         a.wpb = wpb;
         a.units = s.planes;
+        a.units_cap = s.rows_cap;
         a.nunits = s.cnt + CNT_PLANES;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_inner<R>, kApplyThreads, sm);
@@ -298,6 +333,7 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         a.wpb = wpb;
         a.mode = k;
         a.units = s.leaders + (size_t)k * s.rows_cap;
+        a.units_cap = s.rows_cap;
         a.nunits = s.cnt + CNT_LEAD0 + k;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_outer<R>, kApplyThreads, sm);

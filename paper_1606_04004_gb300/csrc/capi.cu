@@ -157,6 +157,12 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
 static pq_status check_capacity(State& s, cudaStream_t st) {
     PQ_CUDA_TRY(cudaMemcpyAsync(s.h_cnt, s.cnt, CNT_SIZE * 8, cudaMemcpyDeviceToHost, st));
     PQ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (s.h_cnt[CNT_FAULT]) {
+        set_error("bounds check failed: site %lld, index %lld, bound %lld",
+                  (long long)s.h_cnt[CNT_FAULT], (long long)s.h_cnt[CNT_FAULT + 1],
+                  (long long)s.h_cnt[CNT_FAULT + 2]);
+        return PQ_EINVAL;
+    }
     if (s.h_cnt[CNT_ERR] & 1) {
         set_error("active set of %lld points exceeds the capacity %zu",
                   (long long)s.h_cnt[CNT_NA], s.cap);

@@ -53,6 +53,25 @@ __device__ __forceinline__ void bit_set(uint64_t* bits, uint32_t b) {
     atomicOr(reinterpret_cast<unsigned long long*>(bits + (b >> 6)), 1ull << (b & 63));
 }
 
+// Bounds checks of the self-checking build (-DPQ_BOUNDS_CHECK): the first
+// out-of-range index is recorded in cnt[CNT_FAULT..+2] and the access is
+// skipped.  In the normal build the check compiles to `true`.
+__device__ __forceinline__ bool pq_in_bounds(uint64_t idx, uint64_t bound, int site,
+                                             int64_t* cnt) {
+#ifdef PQ_BOUNDS_CHECK
+    if (idx < bound) return true;
+    if (cnt && atomicCAS(reinterpret_cast<unsigned long long*>(cnt + CNT_FAULT), 0ull,
+                         (unsigned long long)site) == 0ull) {
+        cnt[CNT_FAULT + 1] = (int64_t)idx;
+        cnt[CNT_FAULT + 2] = (int64_t)bound;
+    }
+    return false;
+#else
+    (void)idx; (void)bound; (void)site; (void)cnt;
+    return true;
+#endif
+}
+
 // |a|^2 >= theta^2 evaluated as fl(fl(re*re) + fl(im*im)) >= fl(theta*theta)
 // in FP64 without contraction (the adaption test of Sec. 2.5).
 __device__ __forceinline__ bool significant64(double re, double im, double theta2) {

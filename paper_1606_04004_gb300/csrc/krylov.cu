@@ -562,6 +562,12 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
         s.timing.ev_start.clear();
         s.timing.ev_stop.clear();
     }
+    if (s.h_cnt[CNT_FAULT]) {
+        set_error("bounds check failed: site %lld, index %lld, bound %lld",
+                  (long long)s.h_cnt[CNT_FAULT], (long long)s.h_cnt[CNT_FAULT + 1],
+                  (long long)s.h_cnt[CNT_FAULT + 2]);
+        return PQ_EINVAL;
+    }
     const int64_t errw = s.h_cnt[CNT_ERR];
     if (errw & 1) {
         set_error("active set outgrew the capacity (%lld > %zu)", (long long)s.h_cnt[CNT_NA], s.cap);

@@ -126,12 +126,14 @@ struct OpRows {
     uint32_t* rows;
     int nlast;
     int64_t cap;
+    uint64_t rows_cap;
+    int64_t* cnt;
     __device__ int64_t size() const { return min(*na, cap); }
     __device__ uint32_t count(int64_t p) const {
         return p == 0 || keys[p] / nlast != keys[p - 1] / nlast;
     }
     __device__ void emit(int64_t p, uint32_t pos, uint32_t c) const {
-        if (c) rows[pos] = keys[p] / nlast;
+        if (c && pq_in_bounds(pos, rows_cap, 8, cnt)) rows[pos] = keys[p] / nlast;
     }
 };
 
@@ -141,12 +143,14 @@ struct OpPlanes {
     const int64_t* nr;
     uint32_t* planes;
     int n2;
+    uint64_t rows_cap;
+    int64_t* cnt;
     __device__ int64_t size() const { return *nr; }
     __device__ uint32_t count(int64_t u) const {
         return u == 0 || rows[u] / n2 != rows[u - 1] / n2;
     }
     __device__ void emit(int64_t u, uint32_t pos, uint32_t c) const {
-        if (c) planes[pos] = rows[u] / n2;
+        if (c && pq_in_bounds(pos, rows_cap, 9, cnt)) planes[pos] = rows[u] / n2;
     }
 };
 
@@ -159,6 +163,8 @@ struct OpLeaders {
     uint32_t* out;
     uint32_t rstride;
     int nk, nlast;
+    uint64_t rows_cap;
+    int64_t* cnt;
     __device__ int64_t size() const { return *nr; }
     __device__ uint32_t count(int64_t u) const {
         const uint32_t r = rows[u];
@@ -168,7 +174,7 @@ struct OpLeaders {
         return 1;
     }
     __device__ void emit(int64_t u, uint32_t pos, uint32_t c) const {
-        if (c) out[pos] = rows[u];
+        if (c && pq_in_bounds(pos, rows_cap, 10, cnt)) out[pos] = rows[u];
     }
 };
 
@@ -176,15 +182,24 @@ struct OpLeaders {
 template <typename V>
 __global__ void k_remap(const uint32_t* __restrict__ keys, const int64_t* na, int64_t cap,
                         const uint64_t* __restrict__ obits, const uint32_t* __restrict__ ooff,
-                        const V* __restrict__ opsi, V* __restrict__ npsi) {
+                        const V* __restrict__ opsi, V* __restrict__ npsi, int64_t* cnt) {
+    if (cnt[CNT_ERR] & 1) return;   // capacity overflow: positions are not valid
     const int64_t n = min(*na, cap);
+#ifdef PQ_BOUNDS_CHECK
+    const uint64_t nold = (uint64_t)cnt[CNT_NA_OLD];
+#else
+    const uint64_t nold = 0;
+#endif
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = keys[p];
         V v;
         v.x = 0;
         v.y = 0;
-        if (bit_test(obits, k)) v = opsi[rank_of(obits, ooff, k)];
+        if (bit_test(obits, k)) {
+            const uint32_t r = rank_of(obits, ooff, k);
+            if (pq_in_bounds(r, nold, 7, cnt)) v = opsi[r];
+        }
         npsi[p] = v;
     }
 }
@@ -192,13 +207,13 @@ __global__ void k_remap(const uint32_t* __restrict__ keys, const int64_t* na, in
 pq_status rebuild_tables(State& s, cudaStream_t st) {
     const Lattice& L = s.lat;
     pq_status rc;
-    OpRows orow{s.keys, s.cnt + CNT_NA, s.rows, L.nlast, (int64_t)s.cap};
+    OpRows orow{s.keys, s.cnt + CNT_NA, s.rows, L.nlast, (int64_t)s.cap, s.rows_cap, s.cnt};
     if ((rc = run_scan(orow, s.scan_tmp, s.cnt + CNT_ROWS, -1, nullptr, 0, st))) return rc;
-    OpPlanes opl{s.rows, s.cnt + CNT_ROWS, s.planes, L.n[L.D - 2]};
+    OpPlanes opl{s.rows, s.cnt + CNT_ROWS, s.planes, L.n[L.D - 2], s.rows_cap, s.cnt};
     if ((rc = run_scan(opl, s.scan_tmp, s.cnt + CNT_PLANES, -1, nullptr, 0, st))) return rc;
     for (int k = 0; k + 2 < L.D; ++k) {
         OpLeaders ol{s.rows, s.cnt + CNT_ROWS, s.bits, s.leaders + (size_t)k * s.rows_cap,
-                     L.rstride[k], L.n[k], L.nlast};
+                     L.rstride[k], L.n[k], L.nlast, s.rows_cap, s.cnt};
         if ((rc = run_scan(ol, s.scan_tmp, s.cnt + CNT_LEAD0 + k, -1, nullptr, 0, st))) return rc;
     }
     return PQ_OK;
@@ -219,10 +234,10 @@ pq_status rebuild_from_bits(State& s, bool remap, cudaStream_t st) {
         const int G = grid_size() * 8;
         if (s.prec == PQ_FP64)
             k_remap<double2><<<G, 256, 0, st>>>(s.keys, s.cnt + CNT_NA, (int64_t)s.cap, s.bits,
-                                                s.off, (const double2*)s.psi, (double2*)s.psi_alt);
+                                                s.off, (const double2*)s.psi, (double2*)s.psi_alt, s.cnt);
         else
             k_remap<float2><<<G, 256, 0, st>>>(s.keys, s.cnt + CNT_NA, (int64_t)s.cap, s.bits,
-                                               s.off, (const float2*)s.psi, (float2*)s.psi_alt);
+                                               s.off, (const float2*)s.psi, (float2*)s.psi_alt, s.cnt);
         PQ_CHECK_LAUNCH();
         void* t = s.psi;
         s.psi = s.psi_alt;
@@ -252,7 +267,9 @@ __device__ __forceinline__ void mark_with_neighbours(uint64_t* bits, uint32_t ke
 template <typename R>
 __global__ void k_prune_mark(const uint32_t* __restrict__ keys, const int64_t* na, int64_t cap,
                              const typename Cx<R>::T* __restrict__ psi, double theta2,
-                             float lo, float hi, Lattice L, uint64_t* bits) {
+                             float lo, float hi, Lattice L, uint64_t* bits,
+                             const int64_t* cnt) {
+    if (cnt[CNT_ERR] & 1) return;
     const int64_t n = min(*na, cap);
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -292,11 +309,11 @@ pq_status prune_launch(State& s, double theta, int radius, cudaStream_t st) {
     if (s.prec == PQ_FP64)
         k_prune_mark<double><<<G, 256, 0, st>>>(s.keys, s.cnt + CNT_NA, (int64_t)s.cap,
                                                 (const double2*)s.psi, theta2, lo, hi, L,
-                                                s.bits_alt);
+                                                s.bits_alt, s.cnt);
     else
         k_prune_mark<float><<<G, 256, 0, st>>>(s.keys, s.cnt + CNT_NA, (int64_t)s.cap,
                                                (const float2*)s.psi, theta2, lo, hi, L,
-                                               s.bits_alt);
+                                               s.bits_alt, s.cnt);
     PQ_CHECK_LAUNCH();
     return rebuild_from_bits(s, true, st);
 }
@@ -379,6 +396,7 @@ __global__ void k_set_bits(const uint32_t* __restrict__ keys, int64_t n, uint64_
 // (d_keys may alias nothing of the state).
 pq_status load_set(State& s, const uint32_t* d_keys, int64_t n, cudaStream_t st) {
     const Lattice& L = s.lat;
+    PQ_CUDA_TRY(cudaMemsetAsync(s.cnt + CNT_ERR, 0, sizeof(int64_t), st));
     PQ_CUDA_TRY(cudaMemsetAsync(s.bits_alt, 0, (size_t)L.nwords * 8, st));
     if (n > 0) {
         k_set_bits<<<grid_size() * 8, 256, 0, st>>>(d_keys, n, s.bits_alt);

@@ -35,10 +35,19 @@ extern std::atomic<int64_t> g_launches;
 
 #define PQ_LAUNCHED() ::pq::g_launches.fetch_add(1, std::memory_order_relaxed)
 
+#ifdef PQ_BOUNDS_CHECK
+// self-checking build: every launch is followed by a synchronisation so that
+// an execution error names the launch that caused it
+#define PQ_LAUNCH_SYNC() cudaDeviceSynchronize()
+#else
+#define PQ_LAUNCH_SYNC() cudaSuccess
+#endif
+
 #define PQ_CHECK_LAUNCH()                                                       \
     do {                                                                        \
         PQ_LAUNCHED();                                                          \
         cudaError_t e_ = cudaGetLastError();                                    \
+        if (e_ == cudaSuccess) e_ = PQ_LAUNCH_SYNC();                           \
         if (e_ != cudaSuccess) {                                                \
             ::pq::set_error("%s:%d launch: %s", __FILE__, __LINE__,             \
                             cudaGetErrorString(e_));                            \
@@ -111,7 +120,8 @@ enum Counter : int {
     CNT_ERR = 3,       // error bits (1: capacity overflow, 2: numeric)
     CNT_NA_OLD = 4,    // active points before the last rebuild
     CNT_LEAD0 = 8,     // fibre leaders of outer mode k at CNT_LEAD0 + k
-    CNT_SIZE = 16
+    CNT_FAULT = 24,    // bounds-check build: site, index, bound of the first bad access
+    CNT_SIZE = 32
 };
 
 // Device scalars of the Krylov step (FP64).
