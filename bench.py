@@ -52,7 +52,7 @@ def _peaks():
 def _traffic_record():
     """DRAM bytes per active coefficient of the H.psi kernels from the committed
     ncu summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "apply_h_traffic.json")
+    p = os.path.join(ROOT, "profiles", "apply_h_hh6d_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -357,7 +357,7 @@ def main():
     ap.add_argument("--config", default="hh6d")
     ap.add_argument("--precision", default="fp32mix", choices=["fp32mix", "fp64"])
     ap.add_argument("--capacity", type=int, default=0)   # 0 = the full lattice
-    ap.add_argument("--ref-sample", type=int, default=200_000)
+    ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--mode", default="step", choices=["step", "apply"])
