@@ -225,6 +225,27 @@ pq_status pq_set_timing(pq_state* state, int enable);
 pq_status pq_timing_get(pq_state* state, double* apply_ms, int64_t* n_apply,
                         double* coef_applied);
 
+/* Observables of the state's current coefficients without any device
+ * allocation.  The paper has no counterpart: this entry point exists for
+ * callers that must not let a library call cudaMalloc / cudaFree, e.g. code
+ * running under a framework allocator that owns the whole device-memory
+ * budget, or step loops that must not pay the device-wide synchronisation an
+ * allocation or free implies.
+ *   out[0], out[1]  C = <Psi(0)|psi> (re, im), as in pq_observables_get;
+ *   out[2]          ||psi||^2;
+ *   out[3]          number of active points with |a| < theta (as a double).
+ * `out` is a host array of 4 doubles; the call synchronises `stream`.
+ * Scratch: a fixed 1 MiB file-scope device array (32768 blocks x 4 partial
+ * sums), held by every GPU that loads the library until exit.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture.
+ * The array is shared by all calls and keeps the last call's contents: calls
+ * that overlap on the GPU (other streams, other host threads) race on it.
+ * Errors: PQ_EINVAL for a null state or output, theta < 0, or more than
+ * 268,435,456 active points (the scratch's limit); PQ_ECAPACITY if the
+ * state's active set outgrew its capacity. */
+pq_status pq_observe_noalloc(const pq_state* state, double theta, double* out, void* stream);
+
 /* Number of kernels the library has launched since load (all states). */
 int64_t pq_launch_count(void);
 

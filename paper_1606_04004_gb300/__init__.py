@@ -88,6 +88,7 @@ _SIGS = {
     "pq_observables_get": [_vp, C.POINTER(Observables)],
     "pq_set_timing": [_vp, C.c_int],
     "pq_timing_get": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+    "pq_observe_noalloc": [_vp, C.c_double, _vp, _vp],
     "pq_launch_count": [],
     "pq_last_error": [],
 }
@@ -275,6 +276,13 @@ class State:
         out.update(ia)
         out["C"] = arrs["c_re"] + 1j * arrs["c_im"]
         return out
+
+    def observe_noalloc(self, theta, stream=None):
+        """C(t), ||psi||^2 and the small-coefficient count of the current state
+        through pq_observe_noalloc (no device allocation; fixed scratch)."""
+        out = np.zeros(4)
+        _check(_lib.pq_observe_noalloc(self._h, float(theta), _dptr(out), _vp(stream or 0)))
+        return dict(C=complex(out[0], out[1]), norm2=float(out[2]), n_wasted=int(round(out[3])))
 
     def set_timing(self, enable=True):
         _check(_lib.pq_set_timing(self._h, int(enable)))
