@@ -38,12 +38,15 @@ struct ApplyArgs {
     const int* skip;
     int skip_k;
     const R* T;                 // [D][kMaxN][kMaxN]
-    const R* pot;               // [nterms][D][kMaxN]
+    const R* pot;               // [nterms][D][kMaxN] factor values (1 for identity)
+    const R* potc;              // [nterms] term coefficients
     int nterms;
     int mode;                   // outer mode k (outer pass only)
     int wpb;                    // warps per block
     int64_t* cnt;               // state counters (bounds-check build)
     uint64_t units_cap;         // entries of the units array (bounds-check build)
+    int ngroup[4];              // potential terms by tile modes touched (neither, D-2, D-1, both)
+    const uint2* rowinfo;       // per-row (start, pattern) table, or null
 };
 
 __device__ __forceinline__ uint64_t low_mask(int s) {
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_inner(ApplyArgs<R> a) {
             rstart[j] = b ? rank_of(a.bits, a.off, (uint64_t)r * nl) : 0u;
         }
         for (int t = lane; t < nt; t += 32) {
-            R p = (R)1;
+            R p = a.potc[t];
             for (int k = 0; k < D - 2; ++k) {
                 const int d = (int)((P / L.pstride[k]) % (uint32_t)L.n[k]);
                 p *= a.pot[((size_t)t * D + k) * kMaxN + d];
@@ -270,6 +273,505 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_outer(ApplyArgs<R> a) {
     }
 }
 
+
+// ------------------------------------------------------------------------
+// Register-blocked fibre kernels for compile-time fibre lengths (the common
+// 16/24/32-point modes).  A warp still owns one plane / one fibre, but lane s
+// keeps the whole column s of the fibre tile in registers, and each output
+// row j is a dot product of that column with row j of the 1D operator, read
+// as vectorised shared-memory broadcasts (4 entries per load).  This removes
+// the per-FMA shared-memory traffic of the generic kernels above.
+// Requires n[D-1] <= 32 (one lane per last-mode point).
+
+// four consecutive values from 16-byte aligned shared memory
+__device__ __forceinline__ void ld4(const float* p, float& a, float& b, float& c, float& d) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double& a, double& b, double& c, double& d) {
+    const double2 u = *reinterpret_cast<const double2*>(p);
+    const double2 v = *reinterpret_cast<const double2*>(p + 2);
+    a = u.x; b = u.y; c = v.x; d = v.y;
+}
+
+// acc += sum_jj t[jj] * (cx[jj], cy[jj]) over jj in [0, N), with whole
+// 8-entry chunks outside [jlo, jhi] skipped (warp-uniform branch).
+template <typename R, int N>
+__device__ __forceinline__ void row_dot(const R* __restrict__ t, const R (&cx)[N],
+                                        const R (&cy)[N], int jlo, int jhi, R& ax, R& ay) {
+#pragma unroll
+    for (int c = 0; c < N; c += 8) {
+        if (c + 8 <= jlo || c > jhi) continue;
+#pragma unroll
+        for (int q = 0; q < 8 && c + q < N; q += 4) {
+            R t0, t1, t2, t3;
+            ld4(t + c + q, t0, t1, t2, t3);
+            ax += t0 * cx[c + q] + t1 * cx[c + q + 1] + t2 * cx[c + q + 2] + t3 * cx[c + q + 3];
+            ay += t0 * cy[c + q] + t1 * cy[c + q + 1] + t2 * cy[c + q + 2] + t3 * cy[c + q + 3];
+        }
+    }
+}
+
+template <typename R, int NK>
+__global__ void __launch_bounds__(kApplyThreads) k_apply_outer_reg(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lattice& L = a.L;
+    const int k = a.mode, nl = L.nlast;
+    const uint32_t rs = L.rstride[k];
+    R* Tk = reinterpret_cast<R*>(smem);                              // [NK][NK]
+    uint64_t* rbits_all = reinterpret_cast<uint64_t*>(Tk + NK * NK);
+    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + NK * a.wpb);
+    for (int i = threadIdx.x; i < NK * NK; i += blockDim.x)
+        Tk[i] = a.T[(size_t)k * kMaxN * kMaxN + (i / NK) * kMaxN + (i % NK)];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= a.wpb) return;
+    uint64_t* rbits = rbits_all + NK * w;
+    uint32_t* rstart = rstart_all + NK * w;
+    const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
+    const int64_t nunits = *a.nunits;
+    const uint64_t lmask = (1ull << lane) - 1ull;
+    const bool lane_ok = lane < nl;
+    for (int64_t u = (int64_t)blockIdx.x * a.wpb + w; u < nunits;
+         u += (int64_t)gridDim.x * a.wpb) {
+        const uint32_t r0 = a.units[u];
+        const int i0 = (int)((r0 / rs) % (uint32_t)NK);
+        for (int j = lane; j < NK; j += 32) {
+            uint64_t b = 0;
+            uint32_t st = 0;
+            if (j >= i0) {
+                const uint32_t r = r0 + (uint32_t)(j - i0) * rs;
+                if (a.rowinfo) {
+                    const uint2 ri = a.rowinfo[r];
+                    st = ri.x;
+                    b = ri.y;
+                } else {
+                    b = row_bits(a.bits, r, nl);
+                    if (b) st = rank_of(a.bits, a.off, (uint64_t)r * nl);
+                }
+            }
+            rbits[j] = b;
+            rstart[j] = st;
+        }
+        __syncwarp();
+        R cx[NK], cy[NK];
+        int jhi = i0;
+#pragma unroll
+        for (int jj = 0; jj < NK; ++jj) {
+            const uint64_t b = rbits[jj];
+            if (b) jhi = jj;
+            R x = 0, y = 0;
+            if (lane_ok && ((b >> lane) & 1ull)) {
+                const V v = a.in[rstart[jj] + __popcll(b & lmask)];
+                x = v.x * scale;
+                y = v.y * scale;
+            }
+            cx[jj] = x;
+            cy[jj] = y;
+        }
+        for (int j = i0; j <= jhi; ++j) {
+            const uint64_t b = rbits[j];
+            if (!b) continue;
+            R ax = 0, ay = 0;
+            row_dot<R, NK>(Tk + j * NK, cx, cy, i0, jhi, ax, ay);
+            if (lane_ok && ((b >> lane) & 1ull)) {
+                V* o = a.out + rstart[j] + __popcll(b & lmask);
+                V ov = *o;
+                ov.x += ax;
+                ov.y += ay;
+                *o = ov;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Inner pass, register-blocked: modes D-2 (column dot products, as above) and
+// D-1 (row dot products: lane s keeps row s of T^(D-1) in registers and reads
+// the tile row as broadcasts), plus the potential split by the tile modes each
+// term touches: V(j,s) = f(j) + g(s) + sum_{both} A_t(j) B_t(s), where f holds
+// the terms constant in s (including plane constants), g those constant in j.
+template <typename R, int N2, int NL>
+__global__ void __launch_bounds__(kApplyThreads) k_apply_inner_reg(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lattice& L = a.L;
+    const int D = L.D, nt = a.nterms;
+    const int g1 = a.ngroup[0], g2 = g1 + a.ngroup[1], g3 = g2 + a.ngroup[2];   // group starts
+    // shared: Tq [N2][N2], then per warp: tile [N2][NL] (V), rbits [N2], rstart [N2],
+    // pref [kMaxTerms], f [N2]
+    R* Tq = reinterpret_cast<R*>(smem);
+    V* tiles = reinterpret_cast<V*>(Tq + N2 * N2);
+    uint64_t* rbits_all = reinterpret_cast<uint64_t*>(tiles + N2 * NL * a.wpb);
+    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + N2 * a.wpb);
+    R* pref_all = reinterpret_cast<R*>(rstart_all + N2 * a.wpb);
+    R* f_all = pref_all + kMaxTerms * a.wpb;
+    for (int i = threadIdx.x; i < N2 * N2; i += blockDim.x)
+        Tq[i] = a.T[(size_t)(D - 2) * kMaxN * kMaxN + (i / N2) * kMaxN + (i % N2)];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= a.wpb) return;
+    const int ls = lane < NL ? lane : NL - 1;
+    // row ls of T^(D-1) and the mode-(D-1) potential factors in registers
+    R tl[NL];
+#pragma unroll
+    for (int ss = 0; ss < NL; ++ss) tl[ss] = a.T[(size_t)(D - 1) * kMaxN * kMaxN + ls * kMaxN + ss];
+    V* tile = tiles + N2 * NL * w;
+    uint64_t* rbits = rbits_all + N2 * w;
+    uint32_t* rstart = rstart_all + N2 * w;
+    R* pref = pref_all + kMaxTerms * w;
+    R* fj = f_all + N2 * w;
+    const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
+    const int64_t nunits = *a.nunits;
+    const uint64_t lmask = (1ull << lane) - 1ull;
+    const bool lane_ok = lane < NL;
+    for (int64_t u = (int64_t)blockIdx.x * a.wpb + w; u < nunits;
+         u += (int64_t)gridDim.x * a.wpb) {
+        const uint32_t P = a.units[u];
+        for (int j = lane; j < N2; j += 32) {
+            const uint32_t r = P * (uint32_t)N2 + (uint32_t)j;
+            if (a.rowinfo) {
+                const uint2 ri = a.rowinfo[r];
+                rbits[j] = ri.y;
+                rstart[j] = ri.x;
+            } else {
+                const uint64_t b = row_bits(a.bits, r, NL);
+                rbits[j] = b;
+                rstart[j] = b ? rank_of(a.bits, a.off, (uint64_t)r * NL) : 0u;
+            }
+        }
+        for (int t = lane; t < nt; t += 32) {
+            R p = a.potc[t];
+            for (int k = 0; k < D - 2; ++k) {
+                const int d = (int)((P / L.pstride[k]) % (uint32_t)L.n[k]);
+                p *= a.pot[((size_t)t * D + k) * kMaxN + d];
+            }
+            pref[t] = p;
+        }
+        __syncwarp();
+        // f(j): terms constant along the last mode
+        for (int j = lane; j < N2; j += 32) {
+            R f = 0;
+            for (int t = 0; t < g1; ++t) f += pref[t];
+            for (int t = g1; t < g2; ++t) f += pref[t] * a.pot[((size_t)t * D + D - 2) * kMaxN + j];
+            fj[j] = f;
+        }
+        // g(s): terms constant along mode D-2
+        R gs = 0;
+        for (int t = g2; t < g3; ++t) gs += pref[t] * a.pot[((size_t)t * D + D - 1) * kMaxN + ls];
+        // column s of the plane in registers, and the plane in shared memory
+        R cx[N2], cy[N2];
+        int jlo = N2, jhi = -1;
+#pragma unroll
+        for (int jj = 0; jj < N2; ++jj) {
+            const uint64_t b = rbits[jj];
+            if (b) {
+                jlo = min(jlo, jj);
+                jhi = jj;
+            }
+            R x = 0, y = 0;
+            if (lane_ok && ((b >> lane) & 1ull)) {
+                const V v = a.in[rstart[jj] + __popcll(b & lmask)];
+                x = v.x * scale;
+                y = v.y * scale;
+            }
+            cx[jj] = x;
+            cy[jj] = y;
+            if (lane_ok) tile[jj * NL + lane] = cmake<R>(x, y);
+        }
+        __syncwarp();
+        for (int j = jlo; j <= jhi; ++j) {
+            const uint64_t b = rbits[j];
+            if (!b) continue;
+            R ax = 0, ay = 0;
+            row_dot<R, N2>(Tq + j * N2, cx, cy, jlo, jhi, ax, ay);   // mode D-2
+            const V* trow = tile + j * NL;                            // mode D-1
+            const int slo = (__ffsll((long long)b) - 1) & ~1;
+            const int shi = 63 - __clzll((long long)b);
+#pragma unroll
+            for (int ss = 0; ss < NL; ss += 2) {
+                if (ss + 1 < slo || ss > shi) continue;
+                R x0, y0, x1, y1;
+                ld4(reinterpret_cast<const R*>(trow + ss), x0, y0, x1, y1);
+                ax += tl[ss] * x0 + tl[ss + 1] * x1;
+                ay += tl[ss] * y0 + tl[ss + 1] * y1;
+            }
+            if (lane_ok && ((b >> lane) & 1ull)) {
+                R vv = fj[j] + gs;
+                for (int t = g3; t < nt; ++t)
+                    vv += pref[t] * a.pot[((size_t)t * D + D - 2) * kMaxN + j] *
+                          a.pot[((size_t)t * D + D - 1) * kMaxN + lane];
+                const V c = trow[lane];
+                ax += vv * c.x;
+                ay += vv * c.y;
+                a.out[rstart[j] + __popcll(b & lmask)] = cmake<R>(ax, ay);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------------
+// Compact fibre kernels (used whenever n[D-1] <= 32).  The fibre tiles of a
+// pruned set are sparse (for a 6D ellipsoid about 15-20 % of the n[k] x
+// n[D-1] tile is active), so each warp first compacts the fibre's active rows
+// (ballot), gathers only those rows into shared memory, and runs the dot
+// products over active rows only: the work per output is the number of active
+// partners, not the fibre length.  Lane s owns last-mode point s.
+
+template <typename R>
+__global__ void __launch_bounds__(kApplyThreads) k_apply_outer_cmp(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lattice& L = a.L;
+    const int k = a.mode, nk = L.n[k], nl = L.nlast;
+    const uint32_t rs = L.rstride[k];
+    // per warp: xin [nk][32] V, rbits [64], rstart [64], rowj [64], trow [64] R
+    V* tiles = reinterpret_cast<V*>(smem);
+    uint64_t* rbits_all = reinterpret_cast<uint64_t*>(tiles + (size_t)nk * 32 * a.wpb);
+    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + kMaxN * a.wpb);
+    int* rowj_all = reinterpret_cast<int*>(rstart_all + kMaxN * a.wpb);
+    R* trow_all = reinterpret_cast<R*>(rowj_all + kMaxN * a.wpb);
+    R* Tk = trow_all + kMaxN * a.wpb;                       // [nk][nk]
+    for (int i = threadIdx.x; i < nk * nk; i += blockDim.x)
+        Tk[i] = a.T[(size_t)k * kMaxN * kMaxN + (i / nk) * kMaxN + (i % nk)];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= a.wpb) return;
+    V* xin = tiles + (size_t)nk * 32 * w;
+    uint64_t* rbits = rbits_all + kMaxN * w;
+    uint32_t* rstart = rstart_all + kMaxN * w;
+    int* rowj = rowj_all + kMaxN * w;
+    R* trow = trow_all + kMaxN * w;
+    const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
+    const int64_t nunits = *a.nunits;
+    const uint64_t lmask = (1ull << lane) - 1ull;
+    const int64_t ustep = (int64_t)gridDim.x * a.wpb;
+    int64_t u = (int64_t)blockIdx.x * a.wpb + w;
+    uint32_t r0n = u < nunits ? a.units[u] : 0u;
+    for (; u < nunits; u += ustep) {
+        const uint32_t r0 = r0n;
+        if (u + ustep < nunits) r0n = a.units[u + ustep];   // next fibre, in flight
+        const int i0 = (int)((r0 / rs) % (uint32_t)nk);
+        // active rows of the fibre, compacted in order of j
+        int na = 0;
+        for (int jb = 0; jb < nk; jb += 32) {
+            const int j = jb + lane;
+            uint64_t b = 0;
+            uint32_t st = 0;
+            if (j < nk && j >= i0) {
+                const uint32_t r = r0 + (uint32_t)(j - i0) * rs;
+                if (a.rowinfo) {
+                    const uint2 ri = a.rowinfo[r];
+                    st = ri.x;
+                    b = ri.y;
+                } else {
+                    b = row_bits(a.bits, r, nl);
+                    if (b) st = rank_of(a.bits, a.off, (uint64_t)r * nl);
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, b != 0);
+            if (b) {
+                const int slot = na + __popc(m & (unsigned)lmask);
+                rbits[slot] = b;
+                rstart[slot] = st;
+                rowj[slot] = j;
+            }
+            na += __popc(m);
+        }
+        __syncwarp();
+        // inputs and the outputs accumulated so far, all loads in flight at once
+#pragma unroll 4
+        for (int v = 0; v < na; ++v) {
+            const uint64_t b = rbits[v];
+            V x = cmake<R>(0, 0);
+            if ((b >> lane) & 1ull) {
+                x = a.in[rstart[v] + __popcll(b & lmask)];
+                x.x *= scale;
+                x.y *= scale;
+            }
+            xin[v * 32 + lane] = x;
+        }
+        __syncwarp();
+        for (int uo = 0; uo < na; ++uo) {
+            const int j = rowj[uo];
+            const R* tj = Tk + j * nk;
+            for (int v = lane; v < na; v += 32) trow[v] = tj[rowj[v]];
+            __syncwarp();
+            const uint64_t b = rbits[uo];
+            if ((b >> lane) & 1ull) {
+                V* o = a.out + rstart[uo] + __popcll(b & lmask);
+                V ov = *o;                                // in flight during the dot product
+                R ax = 0, ay = 0;
+                for (int v = 0; v < na; ++v) {
+                    const R t = trow[v];
+                    const V c = xin[v * 32 + lane];
+                    ax += t * c.x;
+                    ay += t * c.y;
+                }
+                ov.x += ax;
+                ov.y += ay;
+                *o = ov;
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kApplyThreads) k_apply_inner_cmp(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lattice& L = a.L;
+    const int D = L.D, n2 = L.n[D - 2], nl = L.nlast, nt = a.nterms;
+    const int g1 = a.ngroup[0], g2 = g1 + a.ngroup[1], g3 = g2 + a.ngroup[2];
+    // per warp: tile [n2][32] V, rbits [64], rstart [64], rowj [64], trow [64] R,
+    // pref [kMaxTerms] R, fj [64] R; shared: Tq [n2][n2], Tlt [nl][32]
+    V* tiles = reinterpret_cast<V*>(smem);
+    uint64_t* rbits_all = reinterpret_cast<uint64_t*>(tiles + (size_t)n2 * 32 * a.wpb);
+    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + kMaxN * a.wpb);
+    int* rowj_all = reinterpret_cast<int*>(rstart_all + kMaxN * a.wpb);
+    R* trow_all = reinterpret_cast<R*>(rowj_all + kMaxN * a.wpb);
+    R* pref_all = trow_all + kMaxN * a.wpb;
+    R* fj_all = pref_all + kMaxTerms * a.wpb;
+    R* Tq = fj_all + kMaxN * a.wpb;                         // [n2][n2]
+    R* Tlt = Tq + n2 * n2;                                  // [nl][32]: Tlt[ss][s] = T[s][ss]
+    for (int i = threadIdx.x; i < n2 * n2; i += blockDim.x)
+        Tq[i] = a.T[(size_t)(D - 2) * kMaxN * kMaxN + (i / n2) * kMaxN + (i % n2)];
+    for (int i = threadIdx.x; i < nl * 32; i += blockDim.x) {
+        const int ss = i / 32, sl = i % 32;
+        Tlt[i] = sl < nl ? a.T[(size_t)(D - 1) * kMaxN * kMaxN + sl * kMaxN + ss] : (R)0;
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= a.wpb) return;
+    V* tile = tiles + (size_t)n2 * 32 * w;
+    uint64_t* rbits = rbits_all + kMaxN * w;
+    uint32_t* rstart = rstart_all + kMaxN * w;
+    int* rowj = rowj_all + kMaxN * w;
+    R* trow = trow_all + kMaxN * w;
+    R* pref = pref_all + kMaxTerms * w;
+    R* fj = fj_all + kMaxN * w;
+    const int ls = lane < nl ? lane : nl - 1;
+    const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
+    const int64_t nunits = *a.nunits;
+    const uint64_t lmask = (1ull << lane) - 1ull;
+    for (int64_t u = (int64_t)blockIdx.x * a.wpb + w; u < nunits;
+         u += (int64_t)gridDim.x * a.wpb) {
+        const uint32_t P = a.units[u];
+        int na = 0;
+        for (int jb = 0; jb < n2; jb += 32) {
+            const int j = jb + lane;
+            uint64_t b = 0;
+            uint32_t st = 0;
+            if (j < n2) {
+                const uint32_t r = P * (uint32_t)n2 + (uint32_t)j;
+                if (a.rowinfo) {
+                    const uint2 ri = a.rowinfo[r];
+                    st = ri.x;
+                    b = ri.y;
+                } else {
+                    b = row_bits(a.bits, r, nl);
+                    if (b) st = rank_of(a.bits, a.off, (uint64_t)r * nl);
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, b != 0);
+            if (b) {
+                const int slot = na + __popc(m & (unsigned)lmask);
+                rbits[slot] = b;
+                rstart[slot] = st;
+                rowj[slot] = j;
+            }
+            na += __popc(m);
+        }
+        for (int t = lane; t < nt; t += 32) {
+            R p = a.potc[t];
+            for (int k = 0; k < D - 2; ++k) {
+                const int d = (int)((P / L.pstride[k]) % (uint32_t)L.n[k]);
+                p *= a.pot[((size_t)t * D + k) * kMaxN + d];
+            }
+            pref[t] = p;
+        }
+        __syncwarp();
+        for (int v = lane; v < na; v += 32) {   // f(j): terms constant along the last mode
+            const int j = rowj[v];
+            R f = 0;
+            for (int t = 0; t < g1; ++t) f += pref[t];
+            for (int t = g1; t < g2; ++t) f += pref[t] * a.pot[((size_t)t * D + D - 2) * kMaxN + j];
+            fj[v] = f;
+        }
+        R gs = 0;                                 // g(s): terms constant along mode D-2
+        for (int t = g2; t < g3; ++t) gs += pref[t] * a.pot[((size_t)t * D + D - 1) * kMaxN + ls];
+#pragma unroll 4
+        for (int v = 0; v < na; ++v) {
+            const uint64_t b = rbits[v];
+            V x = cmake<R>(0, 0);
+            if ((b >> lane) & 1ull) {
+                x = a.in[rstart[v] + __popcll(b & lmask)];
+                x.x *= scale;
+                x.y *= scale;
+            }
+            tile[v * 32 + lane] = x;
+        }
+        __syncwarp();
+        for (int uo = 0; uo < na; ++uo) {
+            const int j = rowj[uo];
+            const R* tj = Tq + j * n2;
+            for (int v = lane; v < na; v += 32) trow[v] = tj[rowj[v]];
+            __syncwarp();
+            const uint64_t b = rbits[uo];
+            if ((b >> lane) & 1ull) {
+                R ax = 0, ay = 0;
+                for (int v = 0; v < na; ++v) {            // mode D-2
+                    const R t = trow[v];
+                    const V c = tile[v * 32 + lane];
+                    ax += t * c.x;
+                    ay += t * c.y;
+                }
+                const V* rowv = tile + uo * 32;           // mode D-1
+                const int slo = __ffsll((long long)b) - 1, shi = 63 - __clzll((long long)b);
+                for (int ss = slo; ss <= shi; ++ss) {
+                    const R t = Tlt[ss * 32 + lane];
+                    const V c = rowv[ss];
+                    ax += t * c.x;
+                    ay += t * c.y;
+                }
+                R vv = fj[uo] + gs;
+                for (int t = g3; t < nt; ++t)
+                    vv += pref[t] * a.pot[((size_t)t * D + D - 2) * kMaxN + j] *
+                          a.pot[((size_t)t * D + D - 1) * kMaxN + lane];
+                const V c = rowv[lane];
+                ax += vv * c.x;
+                ay += vv * c.y;
+                a.out[rstart[uo] + __popcll(b & lmask)] = cmake<R>(ax, ay);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <typename R>
+static size_t smem_outer_cmp(int nk, int wpb) {
+    const size_t esz = sizeof(R);
+    return (size_t)wpb * ((size_t)nk * 32 * 2 * esz + kMaxN * (8 + 4 + 4 + esz)) + (size_t)nk * nk * esz;
+}
+template <typename R>
+static size_t smem_inner_cmp(int n2, int nl, int wpb) {
+    const size_t esz = sizeof(R);
+    return (size_t)wpb * ((size_t)n2 * 32 * 2 * esz + kMaxN * (8 + 4 + 4 + esz) + kMaxTerms * esz +
+                          kMaxN * esz) +
+           ((size_t)n2 * n2 + (size_t)nl * 32) * esz;
+}
+
 static size_t smem_inner(const Lattice& L, int nterms, int wpb, size_t esz) {
     const int n2 = L.n[L.D - 2], nl = L.nlast;
     const size_t per_warp = (size_t)n2 * nl * 2 * esz + kMaxN * 8 + kMaxN * 4 + kMaxTerms * esz;
@@ -283,6 +785,41 @@ static size_t smem_outer(const Lattice& L, int k, int wpb, size_t esz) {
 }
 
 constexpr size_t kSmemBudget = 200 * 1024;
+
+template <typename R, int N2, int NL>
+static pq_status launch_inner_reg(ApplyArgs<R> a, int G, cudaStream_t st) {
+    const size_t esz = sizeof(R);
+    const int wpb = kApplyThreads / 32;
+    const size_t sm = (size_t)N2 * N2 * esz +
+                      (size_t)wpb * ((size_t)N2 * NL * 2 * esz + N2 * 8 + N2 * 4 + kMaxTerms * esz + N2 * esz);
+    static bool attr = false;
+    if (!attr) {
+        PQ_CUDA_TRY(cudaFuncSetAttribute(k_apply_inner_reg<R, N2, NL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    a.wpb = wpb;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_inner_reg<R, N2, NL>, kApplyThreads, sm);
+    k_apply_inner_reg<R, N2, NL><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+    PQ_CHECK_LAUNCH();
+    return PQ_OK;
+}
+
+template <typename R, int NK>
+static pq_status launch_outer_reg(ApplyArgs<R> a, int G, cudaStream_t st) {
+    const size_t esz = sizeof(R);
+    const int wpb = kApplyThreads / 32;
+    const size_t sm = (size_t)NK * NK * esz + (size_t)wpb * (NK * 8 + NK * 4);
+    a.wpb = wpb;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_outer_reg<R, NK>, kApplyThreads, sm);
+    k_apply_outer_reg<R, NK><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+    PQ_CHECK_LAUNCH();
+    return PQ_OK;
+}
+
+
 
 template <typename R>
 static pq_status launch_all(const State& s, const void* in, void* out, const double* in_scale,
@@ -300,6 +837,9 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
     a.skip_k = skip_k;
     a.T = sizeof(R) == 8 ? (const R*)s.T64 : (const R*)s.T32;
     a.pot = sizeof(R) == 8 ? (const R*)s.pot64 : (const R*)s.pot32;
+    a.potc = a.pot + (size_t)std::max(s.nterms, 1) * L.D * kMaxN;
+    a.rowinfo = s.rowinfo;
+    for (int g = 0; g < 4; ++g) a.ngroup[g] = s.ngroup[g];
     a.nterms = s.nterms;
     a.cnt = s.cnt;
     static bool attr_set[2][2] = {{false, false}, {false, false}};
@@ -312,29 +852,72 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         attr_set[pi][0] = true;
     }
     const int G = grid_size();
+    static bool cmp_attr[2] = {false, false};
+    if (!cmp_attr[pi]) {
+        PQ_CUDA_TRY(cudaFuncSetAttribute(k_apply_inner_cmp<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024));
+        PQ_CUDA_TRY(cudaFuncSetAttribute(k_apply_outer_cmp<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024));
+        cmp_attr[pi] = true;
+    }
+    const bool compact = L.nlast <= 32;
     // inner pass
     {
-        int wpb = kApplyThreads / 32;
-        while (wpb > 1 && smem_inner(L, s.nterms, wpb, esz) > kSmemBudget) --wpb;
-        const size_t sm = smem_inner(L, s.nterms, wpb, esz);
-        a.wpb = wpb;
         a.units = s.planes;
         a.units_cap = s.rows_cap;
         a.nunits = s.cnt + CNT_PLANES;
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_inner<R>, kApplyThreads, sm);
-        k_apply_inner<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
-        PQ_CHECK_LAUNCH();
+        int wpb = kApplyThreads / 32;
+        const int n2 = L.n[L.D - 2], nl = L.nlast;
+        if (n2 == nl && (nl == 16 || nl == 24 || nl == 32)) {
+            pq_status rc = nl == 16 ? launch_inner_reg<R, 16, 16>(a, G, st)
+                         : nl == 24 ? launch_inner_reg<R, 24, 24>(a, G, st)
+                                    : launch_inner_reg<R, 32, 32>(a, G, st);
+            if (rc) return rc;
+        } else if (compact) {
+            while (wpb > 1 && smem_inner_cmp<R>(n2, L.nlast, wpb) > kSmemBudget) --wpb;
+            const size_t sm = smem_inner_cmp<R>(n2, L.nlast, wpb);
+            a.wpb = wpb;
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_inner_cmp<R>, kApplyThreads, sm);
+            k_apply_inner_cmp<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+            PQ_CHECK_LAUNCH();
+        } else {
+            while (wpb > 1 && smem_inner(L, s.nterms, wpb, esz) > kSmemBudget) --wpb;
+            const size_t sm = smem_inner(L, s.nterms, wpb, esz);
+            a.wpb = wpb;
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_inner<R>, kApplyThreads, sm);
+            k_apply_inner<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+            PQ_CHECK_LAUNCH();
+        }
     }
     for (int k = L.D - 3; k >= 0; --k) {
-        int wpb = kApplyThreads / 32;
-        while (wpb > 1 && smem_outer(L, k, wpb, esz) > kSmemBudget) --wpb;
-        const size_t sm = smem_outer(L, k, wpb, esz);
-        a.wpb = wpb;
         a.mode = k;
         a.units = s.leaders + (size_t)k * s.rows_cap;
         a.units_cap = s.rows_cap;
         a.nunits = s.cnt + CNT_LEAD0 + k;
+        int wpb = kApplyThreads / 32;
+        const int nk = L.n[k];
+        if (L.nlast <= 32 && (nk == 16 || nk == 24 || nk == 32)) {
+            pq_status rc = nk == 16 ? launch_outer_reg<R, 16>(a, G, st)
+                         : nk == 24 ? launch_outer_reg<R, 24>(a, G, st)
+                                    : launch_outer_reg<R, 32>(a, G, st);
+            if (rc) return rc;
+            continue;
+        }
+        if (compact) {
+            while (wpb > 1 && smem_outer_cmp<R>(L.n[k], wpb) > kSmemBudget) --wpb;
+            const size_t sm = smem_outer_cmp<R>(L.n[k], wpb);
+            a.wpb = wpb;
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_outer_cmp<R>, kApplyThreads, sm);
+            k_apply_outer_cmp<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+            PQ_CHECK_LAUNCH();
+            continue;
+        }
+        while (wpb > 1 && smem_outer(L, k, wpb, esz) > kSmemBudget) --wpb;
+        const size_t sm = smem_outer(L, k, wpb, esz);
+        a.wpb = wpb;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_outer<R>, kApplyThreads, sm);
         k_apply_outer<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);

@@ -27,6 +27,7 @@ void clear_error() { g_err.clear(); }
 
 static void free_state(State* s) {
     if (!s) return;
+    if (s->rowinfo) cudaFree(s->rowinfo);
     void* ptrs[] = {s->keys,   s->psi,     s->psi_alt, s->bits,  s->bits_alt, s->off,
                     s->off_alt, s->rows,   s->planes,  s->leaders, s->cnt,    s->scan_tmp,
                     s->red_tmp, s->ks,     s->V,       s->T64,   s->T32,     s->pot64,
@@ -62,15 +63,32 @@ static pq_status upload_hamiltonian(State& s) {
                 T[(size_t)(k + lv) * kMaxN * kMaxN + i * kMaxN + j] =
                     b.kin_scale[k] * b.T[k][(size_t)i * n + j];
     }
-    std::vector<double> P((size_t)std::max(nt, 1) * D * kMaxN, 0.0);
-    for (int t = 0; t < nt; ++t) {
+    // Order the potential terms by which of the two last (tile) modes they
+    // touch: neither, mode D-2 only, mode D-1 only, both.  The inner fibre pass
+    // adds each group with the least work (see apply_h.cu).
+    std::vector<int> order;
+    for (int g = 0; g < 4; ++g) s.ngroup[g] = 0;
+    for (int g = 0; g < 4; ++g)
+        for (int t = 0; t < nt; ++t) {
+            const uint32_t m = lv ? (b.pot_mask[t] << 1) : b.pot_mask[t];
+            const int gt = ((m >> (D - 2)) & 1) + 2 * ((m >> (D - 1)) & 1);
+            if (gt == g) {
+                order.push_back(t);
+                ++s.ngroup[g];
+            }
+        }
+    // factor tables [term][mode][point] (identity factors hold 1), followed by
+    // the term coefficients
+    std::vector<double> P((size_t)std::max(nt, 1) * D * kMaxN + kMaxTerms, 0.0);
+    for (int o = 0; o < nt; ++o) {
+        P[(size_t)std::max(nt, 1) * D * kMaxN + o] = b.pot_coef[order[o]];
+        const int t = order[o];
         for (int k = 0; k < D; ++k) {
             const int ku = k - lv;
             const int n = ku < 0 ? 1 : b.modes[ku].n;
             for (int i = 0; i < n; ++i) {
-                double v = ku < 0 ? 1.0 : b.pot_values[t][(size_t)ku * kMaxN + i];
-                if (k == 0) v *= b.pot_coef[t];
-                P[((size_t)t * D + k) * kMaxN + i] = v;
+                P[((size_t)o * D + k) * kMaxN + i] =
+                    ku < 0 ? 1.0 : b.pot_values[t][(size_t)ku * kMaxN + i];
             }
         }
     }
@@ -136,6 +154,13 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
         (rc = dalloc(&s->ks, sizeof(KrylovScalars)))) {
         free_state(s);
         return rc;
+    }
+    if (L.nlast <= 32 && L.nrows <= (1u << 28)) {
+        if ((rc = dalloc(&s->rowinfo, (size_t)L.nrows * sizeof(uint2)))) {
+            free_state(s);
+            return rc;
+        }
+        cudaMemset(s->rowinfo, 0, (size_t)L.nrows * sizeof(uint2));
     }
     if (cudaMallocHost((void**)&s->h_cnt, CNT_SIZE * 8) != cudaSuccess) {
         set_error("cudaMallocHost failed");
@@ -251,6 +276,7 @@ PQ_API pq_status pq_set_sop(pq_basis* basis_, const pq_sop_term* terms, int nter
     const int D = b->D_user;
     std::vector<double> kin(D, 0.0), pc;
     std::vector<std::vector<double>> pv;
+    std::vector<uint32_t> pm;
     for (int t = 0; t < nterms; ++t) {
         const pq_sop_term& tm = terms[t];
         if (!tm.factors) {
@@ -287,6 +313,9 @@ PQ_API pq_status pq_set_sop(pq_basis* basis_, const pq_sop_term* terms, int nter
             continue;
         }
         std::vector<double> vals((size_t)D * kMaxN, 1.0);
+        uint32_t mask = 0;
+        for (int k = 0; k < D; ++k)
+            if (tm.factors[k].kind == PQ_FACTOR_DIAG) mask |= 1u << k;
         for (int k = 0; k < D; ++k)
             if (tm.factors[k].kind == PQ_FACTOR_DIAG)
                 for (int i = 0; i < b->modes[k].n; ++i) {
@@ -299,6 +328,7 @@ PQ_API pq_status pq_set_sop(pq_basis* basis_, const pq_sop_term* terms, int nter
                 }
         pc.push_back(tm.coef);
         pv.push_back(vals);
+        pm.push_back(mask);
     }
     if ((int)pc.size() > kMaxTerms) {
         set_error("%zu potential terms: at most %d", pc.size(), kMaxTerms);
@@ -307,6 +337,7 @@ PQ_API pq_status pq_set_sop(pq_basis* basis_, const pq_sop_term* terms, int nter
     b->kin_scale = kin;
     b->pot_coef = pc;
     b->pot_values = pv;
+    b->pot_mask = pm;
     b->sop_set = true;
     return PQ_OK;
 }

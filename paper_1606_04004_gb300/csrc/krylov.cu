@@ -56,12 +56,15 @@ __device__ void block_partials(double* vals, int width, double* partials) {
     }
 }
 
-// Column sums of partials[G][width] in block order -> out[width].
+// Column sums of partials[G][width] -> out[width]: warp j sums column j
+// with a fixed lane-strided order and a fixed butterfly (deterministic).
 __device__ void sum_partials(const double* partials, int G, int width, double* out) {
-    for (int j = threadIdx.x; j < width; j += blockDim.x) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = wid; j < width; j += nw) {
         double acc = 0.0;
-        for (int b = 0; b < G; ++b) acc += partials[(size_t)b * width + j];
-        out[j] = acc;
+        for (int b = lane; b < G; b += 32) acc += partials[(size_t)b * width + j];
+        acc = warp_sum(acc);
+        if (lane == 0) out[j] = acc;
     }
 }
 
@@ -245,65 +248,105 @@ __global__ void k_update_done(const double* partials, int G, KrylovScalars* ks, 
 }
 
 // ------------------------------------------------ small exponential
-// exp(-i T dt) e_1 of the keff x keff tridiagonal (cyclic Jacobi, FP64,
-// one thread); coef_j = beta_0 sigma_j [Z exp(-i L dt) Z^T e_1]_j.
-__global__ void k_tridiag_exp(KrylovScalars* ks, double dt) {
-    if (threadIdx.x != 0) return;
+// exp(-i T dt) e_1 of the keff x keff tridiagonal: cyclic Jacobi with the
+// round-robin (parallel) ordering, one warp, matrices in shared memory.  In
+// every round the m/2 disjoint rotations are applied at once (lane r updates
+// row r for A J and Z J, then column r for J^T A).
+// coef_j = beta_0 sigma_j [Z exp(-i Lambda dt) Z^T e_1]_j.
+__global__ void __launch_bounds__(32) k_tridiag_exp(KrylovScalars* ks, double dt) {
+    __shared__ double A[kMaxK][kMaxK + 1], Z[kMaxK][kMaxK + 1];
+    __shared__ double rc[kMaxK / 2], rs[kMaxK / 2];
+    __shared__ int rp[kMaxK / 2], rq[kMaxK / 2];
+    __shared__ double ph_re[kMaxK], ph_im[kMaxK];
     const int n = ks->keff;
+    const int r = threadIdx.x;
     if (n <= 0) return;
-    double A[kMaxK * kMaxK], Z[kMaxK * kMaxK];
-    for (int i = 0; i < n * n; ++i) {
-        A[i] = 0.0;
-        Z[i] = 0.0;
-    }
-    for (int i = 0; i < n; ++i) {
-        A[i * n + i] = ks->alpha[i];
-        Z[i * n + i] = 1.0;
-        if (i + 1 < n) A[i * n + i + 1] = A[(i + 1) * n + i] = ks->beta[i];
-    }
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0, dg = 0.0;
-        for (int i = 0; i < n; ++i) {
-            dg += A[i * n + i] * A[i * n + i];
-            for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+    if (r < n) {
+        for (int c = 0; c < n; ++c) {
+            double v = 0.0;
+            if (c == r) v = ks->alpha[r];
+            else if (c == r + 1) v = ks->beta[r];
+            else if (c + 1 == r) v = ks->beta[c];
+            A[r][c] = v;
+            Z[r][c] = c == r ? 1.0 : 0.0;
         }
-        if (off <= 1e-32 * (dg + 1e-300)) break;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const double apq = A[p * n + q];
-                if (apq == 0.0) continue;
-                const double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-                const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-                for (int r = 0; r < n; ++r) {
-                    const double arp = A[r * n + p], arq = A[r * n + q];
-                    A[r * n + p] = c * arp - s * arq;
-                    A[r * n + q] = s * arp + c * arq;
-                }
-                for (int r = 0; r < n; ++r) {
-                    const double apr = A[p * n + r], aqr = A[q * n + r];
-                    A[p * n + r] = c * apr - s * aqr;
-                    A[q * n + r] = s * apr + c * aqr;
-                }
-                for (int r = 0; r < n; ++r) {
-                    const double zrp = Z[r * n + p], zrq = Z[r * n + q];
-                    Z[r * n + p] = c * zrp - s * zrq;
-                    Z[r * n + q] = s * zrp + c * zrq;
-                }
-            }
     }
-    for (int j = 0; j < n; ++j) {
+    __syncwarp();
+    const int m = (n + 1) & ~1;   // even number of indices (index n is a dummy when n is odd)
+    for (int sweep = 0; sweep < 40 && n > 1; ++sweep) {
+        double off = 0.0, dg = 0.0;
+        if (r < n)
+            for (int c = 0; c < n; ++c) {
+                const double v = A[r][c] * A[r][c];
+                if (c == r) dg += v;
+                else off += v;
+            }
+        off = warp_sum(off);
+        dg = warp_sum(dg);
+        if (off <= 1e-32 * (dg + 1e-300)) break;
+        for (int t = 0; t + 1 < m; ++t) {
+            if (r < m / 2) {   // pair r of round t (circle method)
+                const int a = r == 0 ? 0 : ((r - 1 + t) % (m - 1)) + 1;
+                const int bpos = m - 1 - r;
+                const int b = bpos == 0 ? 0 : ((bpos - 1 + t) % (m - 1)) + 1;
+                const int p = min(a, b), q = max(a, b);
+                double c = 1.0, sn = 0.0;
+                if (q < n) {
+                    const double apq = A[p][q];
+                    if (apq != 0.0) {
+                        const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
+                        const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + tt * tt);
+                        sn = tt * c;
+                    }
+                }
+                rp[r] = p;
+                rq[r] = q;
+                rc[r] = c;
+                rs[r] = sn;
+            }
+            __syncwarp();
+            if (r < n)
+                for (int i = 0; i < m / 2; ++i) {
+                    const int p = rp[i], q = rq[i];
+                    if (q >= n) continue;
+                    const double c = rc[i], sn = rs[i];
+                    const double ap = A[r][p], aq = A[r][q];
+                    A[r][p] = c * ap - sn * aq;
+                    A[r][q] = sn * ap + c * aq;
+                    const double zp = Z[r][p], zq = Z[r][q];
+                    Z[r][p] = c * zp - sn * zq;
+                    Z[r][q] = sn * zp + c * zq;
+                }
+            __syncwarp();
+            if (r < n)
+                for (int i = 0; i < m / 2; ++i) {
+                    const int p = rp[i], q = rq[i];
+                    if (q >= n) continue;
+                    const double c = rc[i], sn = rs[i];
+                    const double ap = A[p][r], aq = A[q][r];
+                    A[p][r] = c * ap - sn * aq;
+                    A[q][r] = sn * ap + c * aq;
+                }
+            __syncwarp();
+        }
+    }
+    if (r < n) {
+        double sn, cs;
+        sincos(A[r][r] * dt, &sn, &cs);
+        ph_re[r] = cs * Z[0][r];
+        ph_im[r] = -sn * Z[0][r];
+    }
+    __syncwarp();
+    if (r < n) {
         double re = 0.0, im = 0.0;
         for (int l = 0; l < n; ++l) {
-            double sn, cs;
-            sincos(A[l * n + l] * dt, &sn, &cs);
-            const double wgt = Z[j * n + l] * Z[0 * n + l];
-            re += wgt * cs;
-            im -= wgt * sn;
+            re += Z[r][l] * ph_re[l];
+            im += Z[r][l] * ph_im[l];
         }
-        const double f = ks->beta0 * ks->sigma[j];
-        ks->coef[2 * j] = re * f;
-        ks->coef[2 * j + 1] = im * f;
+        const double f = ks->beta0 * ks->sigma[r];
+        ks->coef[2 * r] = re * f;
+        ks->coef[2 * r + 1] = im * f;
     }
 }
 
@@ -412,7 +455,7 @@ static pq_status observe_t(State& s, double theta, double* rec, cudaStream_t st)
                                             (const typename Cx<R>::T*)fac, theta * theta, lo, hi,
                                             s.red_tmp);
     PQ_CHECK_LAUNCH();
-    k_observe_done<<<1, 64, 0, st>>>(s.red_tmp, G, s.cnt, s.ks, s.t, rec);
+    k_observe_done<<<1, 256, 0, st>>>(s.red_tmp, G, s.cnt, s.ks, s.t, rec);
     PQ_CHECK_LAUNCH();
     return PQ_OK;
 }
@@ -430,7 +473,7 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
     const int K = d.K;
     k_norm2<R><<<G, kRedThreads, 0, st>>>((const V*)s.psi, s.cnt + CNT_NA, (int64_t)cap, s.red_tmp);
     PQ_CHECK_LAUNCH();
-    k_start_step<<<1, 64, 0, st>>>(s.red_tmp, G, s.ks, K, s.cnt + CNT_ERR);
+    k_start_step<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks, K, s.cnt + CNT_ERR);
     PQ_CHECK_LAUNCH();
     pq_status rc;
     for (int k = 0; k < K; ++k) {
@@ -458,7 +501,7 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
             k_dots<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, cap, W, s.cnt + CNT_NA, c0, m, s.ks,
                                                  k, s.red_tmp);
             PQ_CHECK_LAUNCH();
-            k_dots_done<<<1, 64, 0, st>>>(s.red_tmp, G, c0, m, s.ks, k, prev_E, s.cnt + CNT_ERR);
+            k_dots_done<<<1, 256, 0, st>>>(s.red_tmp, G, c0, m, s.ks, k, prev_E, s.cnt + CNT_ERR);
             PQ_CHECK_LAUNCH();
         }
         if (k == K - 1) break;
@@ -469,7 +512,7 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
                                                    k, last ? 1 : 0, s.red_tmp);
             PQ_CHECK_LAUNCH();
         }
-        k_update_done<<<1, 64, 0, st>>>(s.red_tmp, G, s.ks, k, s.cnt + CNT_ERR);
+        k_update_done<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks, k, s.cnt + CNT_ERR);
         PQ_CHECK_LAUNCH();
     }
     k_tridiag_exp<<<1, 32, 0, st>>>(s.ks, d.dt);
@@ -607,7 +650,7 @@ static pq_status energy_t(State& s, double* E, cudaStream_t st) {
     PQ_CUDA_TRY(cudaMallocAsync(&W, s.cap * s.esize > 0 ? s.cap * s.esize : 16, st));
     k_norm2<R><<<G, kRedThreads, 0, st>>>((const V*)s.psi, s.cnt + CNT_NA, (int64_t)s.cap, s.red_tmp);
     PQ_CHECK_LAUNCH();
-    k_start_step<<<1, 64, 0, st>>>(s.red_tmp, G, s.ks, 1, s.cnt + CNT_ERR);
+    k_start_step<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks, 1, s.cnt + CNT_ERR);
     PQ_CHECK_LAUNCH();
     // W = H (psi / ||psi||); <psi/||psi||, W> is then E
     pq_status rc = apply_H_launch(s, s.psi, W, s.prec, &s.ks->sigma[0], nullptr, 0, st);
@@ -621,7 +664,7 @@ static pq_status energy_t(State& s, double* E, cudaStream_t st) {
     double* dE = nullptr;
     PQ_CUDA_TRY(cudaMallocAsync((void**)&dE, sizeof(double), st));
     PQ_CUDA_TRY(cudaMemsetAsync(dE, 0, sizeof(double), st));
-    k_dots_done<<<1, 64, 0, st>>>(s.red_tmp, G, 0, 1, s.ks, 0, dE, s.cnt + CNT_ERR);
+    k_dots_done<<<1, 256, 0, st>>>(s.red_tmp, G, 0, 1, s.ks, 0, dE, s.cnt + CNT_ERR);
     PQ_CHECK_LAUNCH();
     double h = 0.0;
     cudaMemcpyAsync(&h, dE, sizeof(double), cudaMemcpyDeviceToHost, st);

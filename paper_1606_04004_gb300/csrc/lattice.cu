@@ -204,11 +204,31 @@ __global__ void k_remap(const uint32_t* __restrict__ keys, const int64_t* na, in
     }
 }
 
+// rowinfo[r] = (rank of the row's first bit, the row's active pattern) for
+// every active row r (empty rows were cleared to (0, 0)).
+__global__ void k_fill_rowinfo(const uint32_t* __restrict__ rows, const int64_t* nr,
+                               const uint64_t* __restrict__ bits, const uint32_t* __restrict__ off,
+                               int nlast, uint2* rowinfo) {
+    const int64_t n = *nr;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = rows[u];
+        const uint64_t b = row_bits(bits, r, nlast);
+        rowinfo[r] = make_uint2(rank_of(bits, off, (uint64_t)r * nlast), (uint32_t)b);
+    }
+}
+
 pq_status rebuild_tables(State& s, cudaStream_t st) {
     const Lattice& L = s.lat;
     pq_status rc;
     OpRows orow{s.keys, s.cnt + CNT_NA, s.rows, L.nlast, (int64_t)s.cap, s.rows_cap, s.cnt};
     if ((rc = run_scan(orow, s.scan_tmp, s.cnt + CNT_ROWS, -1, nullptr, 0, st))) return rc;
+    if (s.rowinfo) {
+        PQ_CUDA_TRY(cudaMemsetAsync(s.rowinfo, 0, (size_t)L.nrows * sizeof(uint2), st));
+        k_fill_rowinfo<<<grid_size() * 8, 256, 0, st>>>(s.rows, s.cnt + CNT_ROWS, s.bits, s.off,
+                                                       L.nlast, s.rowinfo);
+        PQ_CHECK_LAUNCH();
+    }
     OpPlanes opl{s.rows, s.cnt + CNT_ROWS, s.planes, L.n[L.D - 2], s.rows_cap, s.cnt};
     if ((rc = run_scan(opl, s.scan_tmp, s.cnt + CNT_PLANES, -1, nullptr, 0, st))) return rc;
     for (int k = 0; k + 2 < L.D; ++k) {

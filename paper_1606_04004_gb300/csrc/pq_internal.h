@@ -87,6 +87,7 @@ struct Basis {
     std::vector<double> kin_scale;                 // per caller mode
     std::vector<double> pot_coef;                  // per potential term
     std::vector<std::vector<double>> pot_values;   // [term][mode*n_mode + i] (1 for identity)
+    std::vector<uint32_t> pot_mask;                // [term] bit k set: mode k not identity
 };
 
 pq_status build_dvr_mode(const pq_mode_desc& m, std::vector<double>& x,
@@ -156,6 +157,9 @@ struct State {
     uint32_t* rows = nullptr;      // active row ids
     uint32_t* planes = nullptr;    // active plane ids
     uint32_t* leaders = nullptr;   // fibre leaders, (D-2) lists of nrows_cap entries
+    uint2* rowinfo = nullptr;      // per lattice row: (position of its first active point,
+                                   // active pattern); (0, 0) for empty rows.  Only when
+                                   // n[D-1] <= 32 and the lattice has at most 2^28 rows.
     size_t rows_cap = 0;
     int64_t* cnt = nullptr;        // counters (CNT_*)
     uint32_t* scan_tmp = nullptr;  // block sums of the scans
@@ -167,6 +171,7 @@ struct State {
     double* T64 = nullptr;  float* T32 = nullptr;      // [D][kMaxN][kMaxN]
     double* pot64 = nullptr; float* pot32 = nullptr;   // [nterms][D][kMaxN]
     int nterms = 0;
+    int ngroup[4] = {0, 0, 0, 0};  // potential terms by the tile modes they touch (see apply_h.cu)
     double* fac64 = nullptr; float* fac32 = nullptr;   // packet factors [D][kMaxN] complex
     // host side
     double t = 0;

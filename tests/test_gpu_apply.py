@@ -54,6 +54,18 @@ CASES = [
     ((64, 3, 5), 0.3),        # an outer mode 64 long
     ((17,), 0.8),             # 1D (virtual leading mode)
     ((33, 40), 1.0),          # full lattice (unpruned)
+    # register-blocked kernels (fibre lengths 16 / 24 / 32)
+    ((24, 24), 0.5),
+    ((32, 32), 0.6),
+    ((16, 16, 16), 0.4),
+    ((24, 24, 24), 0.3),
+    ((16, 24, 16, 16), 0.5),
+    ((32, 7, 32), 0.5),       # generic inner tile, register outer pass
+    ((24, 24), 1.0),
+    # compact fibre kernels (other fibre lengths, last mode <= 32)
+    ((9, 12, 20), 0.4),
+    ((40, 6, 28, 11), 0.3),
+    ((5, 30), 0.7),
 ]
 
 
