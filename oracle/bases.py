@@ -60,3 +60,68 @@ def ho_dvr(n: int, mass: float = 1.0, omega: float = 1.0):
     phi0 = (mass * omega / np.pi) ** 0.25 * np.exp(-0.5 * mass * omega * x * x)
     w = (U[0, :] / phi0) ** 2
     return x, w, T
+
+
+def pw_basis(n, xmin, xmax, mass, nx, np_):
+    """Projected Weylets on a sine DVR (Sec. 2.4).
+
+    Momentum-symmetrised Gaussians (Eq. sG_def) on a doubly dense phase-space
+    lattice (Delta x Delta p = pi, p_l > 0): x_a = xmin + (a + 1/2) Dx with
+    Dx = L / nx, p_b = (b + 1/2) Dp with Dp = pi / Dx, alpha = Dp / (2 Dx),
+        phi_ab(x) = (8 alpha / pi)^(1/4) exp(-alpha (x - x_a)^2)
+                    sin(p_b (x - x_a - sqrt(pi / (8 alpha)))).
+    Projected on the DVR, Phi_ji = sqrt(w_j) phi_i(x_j) with i = a np + b
+    (x index slow, p index fast), and orthogonalised symmetrically (Loewdin):
+    W = Phi S^(-1/2), S = Phi^T Phi.  Needs n = nx np.
+    Returns (x, w, T, W) where x, w, T are the underlying DVR's."""
+    if nx * np_ != n:
+        raise ValueError("the phase-space lattice must have as many functions as DVR points")
+    x, w, T = sine_dvr(n, xmin, xmax, mass)
+    L = xmax - xmin
+    dx = L / nx
+    dp = np.pi / dx
+    alpha = dp / (2.0 * dx)
+    xa = xmin + (np.arange(nx) + 0.5) * dx
+    pb = (np.arange(np_) + 0.5) * dp
+    shift = np.sqrt(np.pi / (8.0 * alpha))
+    Phi = np.zeros((n, n))
+    for a in range(nx):
+        for b in range(np_):
+            g = (8.0 * alpha / np.pi) ** 0.25 * np.exp(-alpha * (x - xa[a]) ** 2) \
+                * np.sin(pb[b] * (x - xa[a] - shift))
+            Phi[:, a * np_ + b] = np.sqrt(w) * g
+    S = Phi.T @ Phi
+    lam, U = np.linalg.eigh(S)
+    W = Phi @ (U @ np.diag(lam ** -0.5) @ U.T)
+    return x, w, T, W
+
+
+def pvb_basis(n, xmin, xmax, mass, nx, np_):
+    """Biorthogonal projected von Neumann basis on a sine DVR (Sec. 2.2).
+
+    von Neumann Gaussians on a lattice with Delta x Delta p = 2 pi:
+    x_a = xmin + (a + 1/2) Dx, Dx = L / nx, Dp = 2 pi / Dx, momenta
+    p_b = -p_max + (b + 1/2) Dp with p_max = np Dp / 2, alpha = Dp / (2 Dx),
+        g_ab(x) = (2 alpha / pi)^(1/4) exp(-alpha (x - x_a)^2 + i p_b (x - x_a)).
+    Projection (Eq. pvN_def): G_jm = sqrt(w_j) g_m(x_j), m = a np + b.  The
+    biorthogonal functions (Eq. pvb_def) have B = G^{-dagger}, so that
+    B^dagger G = 1 (<b_n|g_m> = delta).  Needs n = nx np.
+    Returns (x, w, T, G, B)."""
+    if nx * np_ != n:
+        raise ValueError("the phase-space lattice must have as many functions as DVR points")
+    x, w, T = sine_dvr(n, xmin, xmax, mass)
+    L = xmax - xmin
+    dx = L / nx
+    dp = 2.0 * np.pi / dx
+    alpha = dp / (2.0 * dx)
+    xa = xmin + (np.arange(nx) + 0.5) * dx
+    pmax = np_ * dp / 2.0
+    pb = -pmax + (np.arange(np_) + 0.5) * dp
+    G = np.zeros((n, n), dtype=np.complex128)
+    for a in range(nx):
+        for b in range(np_):
+            g = (2.0 * alpha / np.pi) ** 0.25 * np.exp(-alpha * (x - xa[a]) ** 2
+                                                      + 1j * pb[b] * (x - xa[a]))
+            G[:, a * np_ + b] = np.sqrt(w) * g
+    B = np.linalg.inv(G).conj().T
+    return x, w, T, G, B

@@ -11,7 +11,8 @@ from . import bases, models, pruned, sil
 
 class DVRProblem:
     """A DVR direct-product problem: per-mode grids, weights, kinetic
-    matrices, and the potential as a function of the coordinates."""
+    matrices, and the potential as a function of the coordinates.  The
+    adaption lattice has one axis per mode."""
 
     def __init__(self, grids, weights, Ts, vfunc):
         self.grids = [np.asarray(g, dtype=np.float64) for g in grids]
@@ -19,6 +20,7 @@ class DVRProblem:
         self.Ts = [np.asarray(T, dtype=np.float64) for T in Ts]
         self.vfunc = vfunc
         self.dims = tuple(len(g) for g in self.grids)
+        self.axes = self.dims
 
     def vdiag(self, A):
         return pruned.potential_diag(A, self.dims, self.grids, self.vfunc)
@@ -27,6 +29,67 @@ class DVRProblem:
         if vd is None:
             vd = self.vdiag(A)
         return pruned.apply_H(A, psi, self.dims, self.Ts, vd)
+
+    def factors(self, q0, p0, width):
+        return pruned.packet_factors(self.grids, self.weights, q0, p0, width,
+                                     models.gaussian_1d)
+
+
+class PWProblem:
+    """Projected-Weylet problem (Sec. 2.4): per mode a DVR and the orthogonal
+    transformation W to the pW functions; every SoP factor is transformed by
+    congruence, h^w = W^T h^chi W (Sec. 2.2, Eq. pvb_H_trafo with B -> W),
+    and applied with the pruned sequential transform.  The adaption lattice
+    has two axes per mode (x and p indices of the phase-space lattice)."""
+
+    def __init__(self, grids, weights, Ts, Ws, lattices, sop_terms):
+        self.grids = [np.asarray(g, dtype=np.float64) for g in grids]
+        self.weights = [np.asarray(w, dtype=np.float64) for w in weights]
+        self.Ws = [np.asarray(W, dtype=np.float64) for W in Ws]
+        self.dims = tuple(len(g) for g in self.grids)
+        self.axes = tuple(v for lat in lattices for v in lat)
+        self.terms = []
+        for coef, facs in sop_terms:     # factors given on the DVR: 'T' or grid values
+            tf = {}
+            for k, f in facs.items():
+                h = Ts[k] if isinstance(f, str) else np.diag(np.asarray(f, dtype=np.float64))
+                tf[k] = self.Ws[k].T @ h @ self.Ws[k]
+            self.terms.append((coef, tf))
+
+    def vdiag(self, A):
+        return None
+
+    def apply(self, A, psi, vd=None):
+        return pruned.apply_H_sop(A, psi, self.dims, self.terms)
+
+    def factors(self, q0, p0, width):
+        f = pruned.packet_factors(self.grids, self.weights, q0, p0, width, models.gaussian_1d)
+        return [self.Ws[k].T @ f[k] for k in range(len(f))]
+
+
+def morse_sop_terms(grids, De, a, qe, coupling):
+    """Coupled Morse as SoP terms on the DVR grids: kinetic per mode, Morse
+    per mode, coupling * q_i q_j per pair (used by the phase-space bases)."""
+    D = len(grids)
+    terms = [(1.0, {k: "T"}) for k in range(D)]
+    for k in range(D):
+        terms.append((1.0, {k: models.coupled_morse(grids[k][:, None], De, a, qe, 0.0)}))
+    for i in range(D):
+        for j in range(i + 1, D):
+            terms.append((coupling, {i: grids[i], j: grids[j]}))
+    return terms
+
+
+def pw_problem_from_config(cfg, n=None, nx=None, np_=None):
+    """pW problem of the 3D coupled Morse workload (or a smaller lattice)."""
+    n = cfg["n"] if n is None else n
+    nx = cfg["nx_lattice"] if nx is None else nx
+    np_ = cfg["np_lattice"] if np_ is None else np_
+    D = cfg["D"]
+    x, w, T, W = bases.pw_basis(n, cfg["xmin"], cfg["xmax"], cfg["mass"], nx, np_)
+    terms = morse_sop_terms([x] * D, cfg["morse_D"], cfg["morse_a"], cfg["morse_qe"],
+                            cfg["coupling"])
+    return PWProblem([x] * D, [w] * D, [T] * D, [W] * D, [(nx, np_)] * D, terms)
 
 
 def problem_from_config(cfg, omegas=None, lam=None):
@@ -51,15 +114,14 @@ def initial_state(prob, q0, p0, width, theta, radius=1, chunk=1 << 22):
     factors are the per-mode normalised packet vectors (the full-lattice packet
     used by C(t) is their product).  The full lattice is scanned in chunks of
     linear indices so that 6D lattices fit in host memory."""
-    f = pruned.packet_factors(prob.grids, prob.weights, q0, p0, width,
-                              models.gaussian_1d)
+    f = prob.factors(q0, p0, width)
     total = int(np.prod(prob.dims))
     S = []
     for c0 in range(0, total, chunk):
         idx = np.arange(c0, min(total, c0 + chunk), dtype=np.int64)
         a = pruned.product_on(idx, prob.dims, f)
         S.append(idx[pruned.significant(a, theta)])
-    A = pruned.adapt_set(np.concatenate(S), prob.dims, radius)
+    A = pruned.adapt_set(np.concatenate(S), prob.axes, radius)
     return A, pruned.product_on(A, prob.dims, f), f
 
 
@@ -87,7 +149,7 @@ def run(prob, q0, p0, width, theta, K, dt, nsteps, radius=1,
     for _ in range(nsteps):
         vd = prob.vdiag(A)
         a = sil.sil_step(a, lambda v: prob.apply(A, v, vd), K, dt)
-        A, a = pruned.prune(A, a, prob.dims, theta, radius)
+        A, a = pruned.prune(A, a, prob.axes, theta, radius)
         obs.append(observables(prob, A, a, f, theta))
         if record_sets:
             sets.append(A.copy())

@@ -114,6 +114,42 @@ def apply_H_at(A, psi, dims, Ts, vdiag_at, pos):
     return y
 
 
+def mode_apply(A, x, dims, kappa, h):
+    """P_A (h along mode kappa) x: y_I = sum_j h[i_kappa, j] x(I[kappa -> j])
+    over I[kappa -> j] in A, for I in A -- one step of the pruned sequential
+    transform of Sec. 2.2.2 (the sets I, J(i), K(i,j) restrict both the
+    summation and the result to the active set)."""
+    A = np.asarray(A, dtype=np.int64)
+    x = np.asarray(x, dtype=np.complex128)
+    y = np.zeros(len(A), dtype=np.complex128)
+    if len(A) == 0:
+        return y
+    dg = digits(A, dims)
+    st = strides_of(dims)
+    where = PositionMap(A, int(np.prod(dims)))
+    h = np.asarray(h)
+    ik = dg[kappa]
+    for j in range(int(dims[kappa])):
+        pos, found = where(A + (j - ik) * st[kappa])
+        y[found] += h[ik[found], j] * x[pos[found]]
+    return y
+
+
+def apply_H_sop(A, a, dims, terms):
+    """Pruned H.a for an SoP Hamiltonian with dense 1D factors (Sec. 2.2.2):
+    for every term (coef, {mode: matrix}) the factors are applied one mode at
+    a time, last mode first (the order of Eq. matvecprod_sequential), each
+    result truncated to the active set; terms with no factor are coef * a."""
+    a = np.asarray(a, dtype=np.complex128)
+    y = np.zeros(len(a), dtype=np.complex128)
+    for coef, facs in terms:
+        x = a
+        for kappa in sorted(facs, reverse=True):
+            x = mode_apply(A, x, dims, kappa, facs[kappa])
+        y += coef * x
+    return y
+
+
 def neighbour_offsets(axes, radius=1):
     """The phase-space-ball neighbour rule of Sec. 3.1 on a lattice with the
     given axes: radius 1 adds +-1 along each lattice axis (2 per axis)."""

@@ -317,3 +317,116 @@ def test_pruned_infidelity_decreases_with_theta():
         sizes.append(np.mean([o["n_active"] for o in r["obs"]]))
     assert all(np.diff(errs) < 0), errs
     assert all(np.diff(sizes) > 0), sizes
+
+
+# ------------------------------------------------------ phase-space bases
+
+def test_pw_orthonormal_and_similar():
+    # Sec. 2.4: W = Phi S^(-1/2) is orthonormal, and the pW Hamiltonian is a
+    # similarity transform of the DVR one (same eigenvalues, DVR accuracy).
+    x, w, T, W = bases.pw_basis(16, 0.5, 6.0, 1836.0, 4, 4)
+    np.testing.assert_allclose(W.T @ W, np.eye(16), atol=1e-12)
+    V = np.diag(models.coupled_morse(x[:, None], 0.1, 1.0, 2.0, 0.0))
+    H = T + V
+    np.testing.assert_allclose(np.linalg.eigvalsh(W.T @ H @ W), np.linalg.eigvalsh(H),
+                               rtol=1e-10, atol=1e-14)
+
+
+def test_pw_functions_follow_eq_sG():
+    # brute force of Eq. sG_def at the DVR points for one lattice function:
+    # Phi = W S^(1/2); its column (a, b) is sqrt(w) times the symmetrised
+    # Gaussian with phase shift sqrt(pi / (8 alpha)) on the doubly dense lattice.
+    n, lo, hi, nx, np_ = 16, 0.5, 6.0, 4, 4
+    x, w, T, W = bases.pw_basis(n, lo, hi, 1.0, nx, np_)
+    lam, U = np.linalg.eigh(W.T @ W)   # = 1; Phi = W S^(1/2) needs S:
+    dx = (hi - lo) / nx
+    dp = np.pi / dx                       # doubly dense: dx dp = pi
+    alpha = dp / (2 * dx)
+    a, b = 2, 3
+    xa = lo + (a + 0.5) * dx
+    pb = (b + 0.5) * dp
+    g = (8 * alpha / np.pi) ** 0.25 * np.exp(-alpha * (x - xa) ** 2) \
+        * np.sin(pb * (x - xa - np.sqrt(np.pi / (8 * alpha))))
+    Phi_col = np.sqrt(w) * g
+    # W spans the same space as Phi: the column lies in span(W) and
+    # W W^T Phi_col = Phi_col
+    np.testing.assert_allclose(W @ (W.T @ Phi_col), Phi_col, atol=1e-12)
+    assert pb > 0 and abs(dx * dp - np.pi) < 1e-12
+
+
+def test_pvb_biorthogonal():
+    # Eq. pvb_def: <b_n|g_m> = delta_nm, i.e. B^dagger G = 1 (brute force),
+    # and the generalised problem S_b^-1 (B^dag H B) has the DVR eigenvalues.
+    x, w, T, G, B = bases.pvb_basis(16, 0.5, 6.0, 1836.0, 4, 4)
+    np.testing.assert_allclose(B.conj().T @ G, np.eye(16), atol=1e-10)
+    H = T + np.diag(models.coupled_morse(x[:, None], 0.1, 1.0, 2.0, 0.0))
+    Hb = B.conj().T @ H @ B
+    Sb = B.conj().T @ B
+    ev = np.sort(np.linalg.eigvals(np.linalg.solve(Sb, Hb)).real)
+    np.testing.assert_allclose(ev, np.linalg.eigvalsh(H), rtol=1e-8, atol=1e-12)
+
+
+@pytest.mark.parametrize("dims,seed", [((5, 4, 6), 1), ((6, 7), 2), ((3, 4, 2, 3), 3)])
+def test_sop_sequential_equals_dense_truncated_products(dims, seed):
+    # Sec. 2.2.2: each factor is applied along its mode with the result
+    # truncated to A, last mode first.  Dense reference: P_A K_k P_A ... with
+    # K_k the Kronecker embedding of the factor (non-symmetric factors catch
+    # transposes; three-factor terms check the order).
+    rng = np.random.default_rng(seed)
+    D = len(dims)
+    A = W.random_active_set(dims, 0.5, seed)
+    a = W.random_psi(len(A), seed + 1)
+    N = int(np.prod(dims))
+    P = np.zeros((N, len(A)))
+    P[A, np.arange(len(A))] = 1.0
+
+    def K(k, h):
+        mats = [np.eye(d) for d in dims]
+        mats[k] = h
+        M = mats[0]
+        for m in mats[1:]:
+            M = np.kron(M, m)
+        return M
+
+    terms = []
+    for t in range(4):
+        modes = sorted(rng.choice(D, size=min(D, t % 3 + 1), replace=False))
+        terms.append((float(rng.uniform(-1, 1)),
+                      {int(k): rng.standard_normal((dims[k], dims[k])) for k in modes}))
+    terms.append((0.7, {}))
+    y = pruned.apply_H_sop(A, a, dims, terms)
+    ref = np.zeros(len(A), dtype=complex)
+    for c, facs in terms:
+        x = a.copy()
+        for k in sorted(facs, reverse=True):
+            x = P.T @ K(k, facs[k]) @ P @ x
+        ref += c * x
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_pw_full_basis_equals_transformed_dvr():
+    # With A = the full lattice the pruned sequential products are exact
+    # Kronecker products, so the pW H.a equals (x W^T) H^chi (x W) a.
+    cfg = W.scaled(W.MORSE3D, D=2)
+    prob = propagate.pw_problem_from_config(cfg, n=16, nx=4, np_=4)
+    dv = propagate.problem_from_config(W.scaled(W.MORSE2D, n=16))
+    full = np.arange(256)
+    a = W.random_psi(256, 5)
+    Wm = prob.Ws[0]
+    WW = np.kron(Wm, Wm)
+    ref = WW.T @ dv.apply(full, WW @ a)
+    np.testing.assert_allclose(prob.apply(full, a), ref, rtol=1e-11, atol=1e-13)
+
+
+def test_pw_theta0_matches_dvr_dynamics():
+    # Sec. 3.1: at 100 % basis the phase-space bases give the DVR result:
+    # the autocorrelation of a theta = 0 pW run equals the DVR run's.
+    cfg = W.scaled(W.MORSE3D, D=2)
+    prob = propagate.pw_problem_from_config(cfg, n=16, nx=4, np_=4)
+    dv = propagate.problem_from_config(W.scaled(W.MORSE2D, n=16))
+    q0, p0, wd = (2.2, 2.35), (0.0, 0.0), (0.2, 0.2)
+    r1 = propagate.run(prob, q0, p0, wd, 0.0, 12, 10.0, 6)
+    r2 = propagate.run(dv, q0, p0, wd, 0.0, 12, 10.0, 6)
+    for o1, o2 in zip(r1["obs"], r2["obs"]):
+        assert abs(o1["C"] - o2["C"]) < 1e-10
+        assert abs(o1["E"] - o2["E"]) < 1e-10 * abs(o2["E"])
