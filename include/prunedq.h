@@ -93,6 +93,11 @@ void pq_basis_free(pq_basis* basis);
 pq_status pq_basis_grid(const pq_basis* basis, int mode, double* x, double* w);
 pq_status pq_basis_kinetic(const pq_basis* basis, int mode, double* T);
 
+/* Mode `mode`'s transformation from basis coefficients to DVR coefficients
+ * (n*n doubles, row-major, a^chi = W a): the projected Weylets' W = Phi S^(-1/2)
+ * (Sec. 2.4); the unit matrix for a DVR mode. */
+pq_status pq_basis_transform(const pq_basis* basis, int mode, double* W);
+
 /* Sum-of-products Hamiltonian H = sum_l coef_l (x)_kappa h^(kappa,l)
  * (Sec. 2.2.2).  Each term gives one factor per mode:
  *   PQ_FACTOR_IDENTITY  the unit matrix;

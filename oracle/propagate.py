@@ -93,8 +93,10 @@ def pw_problem_from_config(cfg, n=None, nx=None, np_=None):
 
 
 def problem_from_config(cfg, omegas=None, lam=None):
-    """Build the DVR problem of a workload record (see ``workloads``)."""
+    """Build the problem of a workload record (see ``workloads``)."""
     D, n = cfg["D"], cfg["n"]
+    if cfg["basis"] == "pw":
+        return pw_problem_from_config(cfg)
     if cfg["basis"] == "sine":
         x, w, T = bases.sine_dvr(n, cfg["xmin"], cfg["xmax"], cfg["mass"])
         vf = lambda q: models.coupled_morse(q, cfg["morse_D"], cfg["morse_a"],

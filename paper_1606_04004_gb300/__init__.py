@@ -73,6 +73,7 @@ _SIGS = {
     "pq_basis_free": [_vp],
     "pq_basis_grid": [_vp, C.c_int, _vp, _vp],
     "pq_basis_kinetic": [_vp, C.c_int, _vp],
+    "pq_basis_transform": [_vp, C.c_int, _vp],
     "pq_set_sop": [_vp, C.POINTER(SopTerm), C.c_int],
     "pq_init_packet": [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.c_int, C.c_size_t,
                        C.POINTER(_vp)],
@@ -155,6 +156,13 @@ class Basis:
         T = np.zeros((n, n))
         _check(_lib.pq_basis_kinetic(self._h, mode, _dptr(T)))
         return T
+
+    def transform(self, mode):
+        """W of a phase-space mode (basis -> DVR coefficients); 1 for a DVR mode."""
+        n = self.dims[mode]
+        Wm = np.zeros((n, n))
+        _check(_lib.pq_basis_transform(self._h, mode, _dptr(Wm)))
+        return Wm
 
     def set_sop(self, terms):
         """terms: list of (coef, [factor per mode]) with factor None (identity),

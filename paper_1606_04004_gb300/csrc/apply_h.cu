@@ -24,6 +24,7 @@
 namespace pq {
 
 constexpr int kApplyThreads = 256;
+constexpr size_t kSmemBudget = 200 * 1024;   // dynamic shared memory per block
 
 template <typename R>
 struct ApplyArgs {
@@ -47,6 +48,10 @@ struct ApplyArgs {
     uint64_t units_cap;         // entries of the units array (bounds-check build)
     int ngroup[4];              // potential terms by tile modes touched (neither, D-2, D-1, both)
     const uint2* rowinfo;       // per-row (start, pattern) table, or null
+    // generic single-mode pass (phase-space bases)
+    const R* mat;               // n x n matrix of the pass (row stride kMaxN)
+    double coef;                // result scale
+    int accumulate;             // 1: out += coef * (M along mode) in;  0: out = ...
 };
 
 __device__ __forceinline__ uint64_t low_mask(int s) {
@@ -772,6 +777,256 @@ static size_t smem_inner_cmp(int n2, int nl, int wpb) {
            ((size_t)n2 * n2 + (size_t)nl * 32) * esz;
 }
 
+// ------------------------------------------------------------------------
+// Generic single-mode passes for SoP Hamiltonians with dense 1D factors
+// (projected Weylets, Sec. 2.4; pruned sequential transform, Sec. 2.2.2):
+//   out (+)= coef * P_A (M along mode k) in.
+// Last mode: one warp per active row (the row is contiguous in A).  Other
+// modes: one warp per fibre leader, the fibre staged as a dense tile.
+
+template <typename R>
+__global__ void __launch_bounds__(kApplyThreads) k_pass_row(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lattice& L = a.L;
+    const int nl = L.nlast;
+    R* Mt = reinterpret_cast<R*>(smem);                    // [nl][nl], Mt[ss][s] = M[s][ss]
+    V* xrow_all = reinterpret_cast<V*>(Mt + ((nl * nl + 1) & ~1));
+    for (int i = threadIdx.x; i < nl * nl; i += blockDim.x) {
+        const int ss = i / nl, sl = i % nl;
+        Mt[i] = a.mat[sl * kMaxN + ss];
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= a.wpb) return;
+    V* xrow = xrow_all + kMaxN * w;
+    const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
+    const R coef = (R)a.coef;
+    const int64_t nunits = *a.nunits;
+    for (int64_t u = (int64_t)blockIdx.x * a.wpb + w; u < nunits;
+         u += (int64_t)gridDim.x * a.wpb) {
+        const uint32_t r = a.units[u];
+        const uint64_t b = row_bits(a.bits, r, nl);
+        const uint32_t st = rank_of(a.bits, a.off, (uint64_t)r * nl);
+        for (int s = lane; s < nl; s += 32) {
+            V x = cmake<R>(0, 0);
+            if ((b >> s) & 1ull) {
+                x = a.in[st + __popcll(b & low_mask(s))];
+                x.x *= scale;
+                x.y *= scale;
+            }
+            xrow[s] = x;
+        }
+        __syncwarp();
+        const int slo = __ffsll((long long)b) - 1, shi = 63 - __clzll((long long)b);
+        for (int s = lane; s < nl; s += 32) {
+            if (!((b >> s) & 1ull)) continue;
+            R ax = 0, ay = 0;
+            for (int ss = slo; ss <= shi; ++ss) {
+                const R t = Mt[ss * nl + s];
+                const V c = xrow[ss];
+                ax += t * c.x;
+                ay += t * c.y;
+            }
+            V* o = a.out + st + __popcll(b & low_mask(s));
+            V y = cmake<R>(coef * ax, coef * ay);
+            if (a.accumulate) {
+                const V ov = *o;
+                y.x += ov.x;
+                y.y += ov.y;
+            }
+            *o = y;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kApplyThreads) k_pass_fibre(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lattice& L = a.L;
+    const int k = a.mode, nk = L.n[k], nl = L.nlast;
+    const uint32_t rs = L.rstride[k];
+    const size_t tile_elems = (size_t)nk * nl;
+    V* tiles = reinterpret_cast<V*>(smem);
+    uint64_t* rbits_all = reinterpret_cast<uint64_t*>(tiles + tile_elems * a.wpb);
+    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + (size_t)kMaxN * a.wpb);
+    R* Mk = reinterpret_cast<R*>(rstart_all + (size_t)kMaxN * a.wpb);   // [nk][nk]
+    for (int i = threadIdx.x; i < nk * nk; i += blockDim.x) Mk[i] = a.mat[(i / nk) * kMaxN + (i % nk)];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= a.wpb) return;
+    V* tile = tiles + tile_elems * w;
+    uint64_t* rbits = rbits_all + (size_t)kMaxN * w;
+    uint32_t* rstart = rstart_all + (size_t)kMaxN * w;
+    const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
+    const R coef = (R)a.coef;
+    const int64_t nunits = *a.nunits;
+    for (int64_t u = (int64_t)blockIdx.x * a.wpb + w; u < nunits;
+         u += (int64_t)gridDim.x * a.wpb) {
+        const uint32_t r0 = a.units[u];
+        const int i0 = (int)((r0 / rs) % (uint32_t)nk);
+        for (int j = lane; j < nk; j += 32) {
+            uint64_t b = 0;
+            uint32_t st = 0;
+            if (j >= i0) {
+                const uint32_t r = r0 + (uint32_t)(j - i0) * rs;
+                b = row_bits(a.bits, r, nl);
+                if (b) st = rank_of(a.bits, a.off, (uint64_t)r * nl);
+            }
+            rbits[j] = b;
+            rstart[j] = st;
+        }
+        for (size_t e = lane; e < tile_elems; e += 32) tile[e] = cmake<R>(0, 0);
+        __syncwarp();
+        int jhi = -1;
+        for (int j = i0; j < nk; ++j) {
+            const uint64_t b = rbits[j];
+            if (!b) continue;
+            jhi = j;
+            const uint32_t st = rstart[j];
+            for (int s = lane; s < nl; s += 32)
+                if ((b >> s) & 1ull) {
+                    V v = a.in[st + __popcll(b & low_mask(s))];
+                    v.x *= scale;
+                    v.y *= scale;
+                    tile[j * nl + s] = v;
+                }
+        }
+        __syncwarp();
+        for (int j = i0; j <= jhi; ++j) {
+            const uint64_t b = rbits[j];
+            if (!b) continue;
+            const uint32_t st = rstart[j];
+            const R* mj = Mk + j * nk;
+            for (int s = lane; s < nl; s += 32) {
+                if (!((b >> s) & 1ull)) continue;
+                R ax = 0, ay = 0;
+                for (int jj = i0; jj <= jhi; ++jj) {
+                    const R t = mj[jj];
+                    const V c = tile[jj * nl + s];
+                    ax += t * c.x;
+                    ay += t * c.y;
+                }
+                V* o = a.out + st + __popcll(b & low_mask(s));
+                V y = cmake<R>(coef * ax, coef * ay);
+                if (a.accumulate) {
+                    const V ov = *o;
+                    y.x += ov.x;
+                    y.y += ov.y;
+                }
+                *o = y;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename R>
+__global__ void k_zero(typename Cx<R>::T* out, const int64_t* na, const int* skip, int skip_k) {
+    if (skip && *skip <= skip_k) return;
+    const int64_t n = *na;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        out[p] = cmake<R>(0, 0);
+}
+
+template <typename R>
+static pq_status launch_pass(const State& s, ApplyArgs<R> a, int mode, int mat, const void* in,
+                             void* out, const double* in_scale, double coef, int accumulate,
+                             cudaStream_t st) {
+    const Lattice& L = s.lat;
+    const size_t esz = sizeof(R);
+    a.in = (const typename Cx<R>::T*)in;
+    a.out = (typename Cx<R>::T*)out;
+    a.in_scale = in_scale;
+    a.mat = (sizeof(R) == 8 ? (const R*)s.gmat64 : (const R*)s.gmat32) + (size_t)mat * kMaxN * kMaxN;
+    a.coef = coef;
+    a.accumulate = accumulate;
+    a.mode = mode;
+    const int G = grid_size();
+    int wpb = kApplyThreads / 32;
+    if (mode == L.D - 1) {
+        const int nl = L.nlast;
+        const size_t sm = (size_t)((nl * nl + 1) & ~1) * esz + (size_t)wpb * kMaxN * 2 * esz;
+        a.wpb = wpb;
+        a.units = s.rows;
+        a.units_cap = s.rows_cap;
+        a.nunits = s.cnt + CNT_ROWS;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_row<R>, kApplyThreads, sm);
+        k_pass_row<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+        PQ_CHECK_LAUNCH();
+        return PQ_OK;
+    }
+    const int nk = L.n[mode], nl = L.nlast;
+    auto smem = [&](int wp) {
+        return (size_t)wp * ((size_t)nk * nl * 2 * esz + kMaxN * 12) + (size_t)nk * nk * esz;
+    };
+    while (wpb > 1 && smem(wpb) > kSmemBudget) --wpb;
+    a.wpb = wpb;
+    a.units = s.leaders + (size_t)mode * s.rows_cap;
+    a.units_cap = s.rows_cap;
+    a.nunits = s.cnt + CNT_LEAD0 + mode;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_fibre<R>, kApplyThreads, smem(wpb));
+    k_pass_fibre<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, smem(wpb), st>>>(a);
+    PQ_CHECK_LAUNCH();
+    return PQ_OK;
+}
+
+// H.in for a generic SoP: merged single-mode matrices (one pass per mode),
+// then every multi-factor term through the scratch vectors, last mode first.
+template <typename R>
+static pq_status launch_generic(const State& s, ApplyArgs<R> a, const void* in, void* out,
+                                const double* in_scale, cudaStream_t st) {
+    const Lattice& L = s.lat;
+    static bool attr[2] = {false, false};
+    const int pi = sizeof(R) == 8 ? 1 : 0;
+    if (!attr[pi]) {
+        PQ_CUDA_TRY(cudaFuncSetAttribute(k_pass_fibre<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024));
+        PQ_CUDA_TRY(cudaFuncSetAttribute(k_pass_row<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024));
+        attr[pi] = true;
+    }
+    bool first = true;
+    pq_status rc;
+    for (int k = L.D - 1; k >= 0; --k) {
+        if (s.gsingle[k] < 0) continue;
+        if ((rc = launch_pass<R>(s, a, k, s.gsingle[k], in, out, in_scale, 1.0, first ? 0 : 1, st)))
+            return rc;
+        first = false;
+    }
+    if (first) {
+        k_zero<R><<<grid_size() * 4, 256, 0, st>>>((typename Cx<R>::T*)out, s.cnt + CNT_NA, a.skip,
+                                                   a.skip_k);
+        PQ_CHECK_LAUNCH();
+    }
+    const size_t esz = 2 * sizeof(R);
+    for (const State::GPlan& plan : s.gplan) {
+        const void* cur = in;
+        const double* sc = in_scale;
+        int tsel = 0;
+        for (size_t p = 0; p < plan.passes.size(); ++p) {
+            const bool last = p + 1 == plan.passes.size();
+            void* dst = last ? out : (void*)((char*)s.gtmp + (size_t)tsel * s.cap * esz);
+            if ((rc = launch_pass<R>(s, a, plan.passes[p].mode, plan.passes[p].mat, cur, dst, sc,
+                                     last ? plan.coef : 1.0, last ? 1 : 0, st)))
+                return rc;
+            cur = dst;
+            sc = nullptr;
+            tsel ^= 1;
+        }
+    }
+    return PQ_OK;
+}
+
 static size_t smem_inner(const Lattice& L, int nterms, int wpb, size_t esz) {
     const int n2 = L.n[L.D - 2], nl = L.nlast;
     const size_t per_warp = (size_t)n2 * nl * 2 * esz + kMaxN * 8 + kMaxN * 4 + kMaxTerms * esz;
@@ -784,7 +1039,6 @@ static size_t smem_outer(const Lattice& L, int k, int wpb, size_t esz) {
     return per_warp * wpb + (size_t)nk * nk * esz;
 }
 
-constexpr size_t kSmemBudget = 200 * 1024;
 
 template <typename R, int N2, int NL>
 static pq_status launch_inner_reg(ApplyArgs<R> a, int G, cudaStream_t st) {
@@ -842,6 +1096,7 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
     for (int g = 0; g < 4; ++g) a.ngroup[g] = s.ngroup[g];
     a.nterms = s.nterms;
     a.cnt = s.cnt;
+    if (s.generic) return launch_generic<R>(s, a, in, out, in_scale, st);
     static bool attr_set[2][2] = {{false, false}, {false, false}};
     const int pi = sizeof(R) == 8 ? 1 : 0;
     if (!attr_set[pi][0]) {

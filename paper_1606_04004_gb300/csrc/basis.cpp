@@ -162,6 +162,72 @@ static int ho_dvr(int n, double mass, double omega, std::vector<double>& x,
     return 0;
 }
 
+// Projected Weylets (Sec. 2.4) on a sine DVR: momentum-symmetrised Gaussians
+// (Eq. sG_def) on the doubly dense lattice Dx Dp = pi (x_a cell-centred,
+// p_b = (b + 1/2) Dp > 0, alpha = Dp / (2 Dx)), projected on the DVR
+// (Phi_ji = sqrt(w_j) phi_i(x_j), i = a np + b) and orthogonalised
+// symmetrically: W = Phi S^(-1/2), S = Phi^T Phi.  W (n x n, row-major) maps
+// pW coefficients to DVR coefficients.
+pq_status build_pw_mode(const pq_mode_desc& m, std::vector<double>& x, std::vector<double>& w,
+                        std::vector<double>& T, std::vector<double>& W) {
+    const int n = m.n, nx = m.nx_lattice, np_ = m.np_lattice;
+    if (nx < 1 || np_ < 1 || nx * np_ != n) {
+        set_error("projected Weylets need nx_lattice * np_lattice = n (%d x %d != %d)", nx, np_, n);
+        return PQ_EINVAL;
+    }
+    if (!(m.xmax > m.xmin) || !(m.mass > 0)) {
+        set_error("projected Weylets need xmax > xmin and mass > 0");
+        return PQ_EINVAL;
+    }
+    sine_dvr(n, m.xmin, m.xmax, m.mass, x, w, T);
+    const double L = m.xmax - m.xmin, dx = L / nx, dp = M_PI / dx, alpha = dp / (2.0 * dx);
+    const double shift = sqrt(M_PI / (8.0 * alpha)), amp = pow(8.0 * alpha / M_PI, 0.25);
+    std::vector<double> Phi((size_t)n * n);
+    for (int a = 0; a < nx; ++a) {
+        const double xa = m.xmin + (a + 0.5) * dx;
+        for (int b = 0; b < np_; ++b) {
+            const double pb = (b + 0.5) * dp;
+            for (int j = 0; j < n; ++j) {
+                const double d = x[j] - xa;
+                Phi[(size_t)j * n + a * np_ + b] =
+                    sqrt(w[j]) * (amp * exp(-alpha * d * d) * sin(pb * (d - shift)));
+            }
+        }
+    }
+    std::vector<double> S((size_t)n * n, 0.0), U, lam;
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q) {
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc += Phi[(size_t)j * n + p] * Phi[(size_t)j * n + q];
+            S[(size_t)p * n + q] = acc;
+        }
+    if (jacobi_eigh(n, S, lam, U) < 0) {
+        set_error("projected Weylets: eigensolver of the overlap did not converge");
+        return PQ_ENUMERIC;
+    }
+    for (int i = 0; i < n; ++i)
+        if (!(lam[i] > 1e-12 * lam[n - 1])) {
+            set_error("projected Weylets: overlap matrix is singular (lambda_min %.3e)", lam[0]);
+            return PQ_ENUMERIC;
+        }
+    std::vector<double> Sm((size_t)n * n, 0.0);   // S^(-1/2) = U diag(lam^-1/2) U^T
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q) {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i)
+                acc += U[(size_t)p * n + i] * U[(size_t)q * n + i] / sqrt(lam[i]);
+            Sm[(size_t)p * n + q] = acc;
+        }
+    W.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j)
+        for (int q = 0; q < n; ++q) {
+            double acc = 0.0;
+            for (int p = 0; p < n; ++p) acc += Phi[(size_t)j * n + p] * Sm[(size_t)p * n + q];
+            W[(size_t)j * n + q] = acc;
+        }
+    return PQ_OK;
+}
+
 pq_status build_dvr_mode(const pq_mode_desc& m, std::vector<double>& x, std::vector<double>& w,
                          std::vector<double>& T) {
     if (m.n < 2 || m.n > kMaxN) {
@@ -191,8 +257,8 @@ pq_status build_dvr_mode(const pq_mode_desc& m, std::vector<double>& x, std::vec
         }
         return PQ_OK;
     }
-    if (m.kind == PQ_PVB || m.kind == PQ_PW) {
-        set_error("phase-space bases (pvB, pW) are not provided by this build");
+    if (m.kind == PQ_PVB) {
+        set_error("the pvB basis is not provided by this build");
         return PQ_ENOTSUP;
     }
     set_error("unknown basis kind %d", m.kind);
@@ -222,6 +288,15 @@ void packet_factors(const Basis& b, const double* q0, const double* p0, const do
         }
         nrm = sqrt(nrm);
         for (int i = 0; i < 2 * n; ++i) f[i] /= nrm;
+        if (!b.W[k].empty()) {   // pW coefficients: W^T f
+            std::vector<double> g(2 * n, 0.0);
+            for (int q = 0; q < n; ++q)
+                for (int j = 0; j < n; ++j) {
+                    g[2 * q] += b.W[k][(size_t)j * n + q] * f[2 * j];
+                    g[2 * q + 1] += b.W[k][(size_t)j * n + q] * f[2 * j + 1];
+                }
+            for (int i = 0; i < 2 * n; ++i) f[i] = g[i];
+        }
     }
 }
 

@@ -28,6 +28,9 @@ void clear_error() { g_err.clear(); }
 static void free_state(State* s) {
     if (!s) return;
     if (s->rowinfo) cudaFree(s->rowinfo);
+    if (s->gmat64) cudaFree(s->gmat64);
+    if (s->gmat32) cudaFree(s->gmat32);
+    if (s->gtmp) cudaFree(s->gtmp);
     void* ptrs[] = {s->keys,   s->psi,     s->psi_alt, s->bits,  s->bits_alt, s->off,
                     s->off_alt, s->rows,   s->planes,  s->leaders, s->cnt,    s->scan_tmp,
                     s->red_tmp, s->ks,     s->V,       s->T64,   s->T32,     s->pot64,
@@ -105,6 +108,90 @@ static pq_status upload_hamiltonian(State& s) {
     return PQ_OK;
 }
 
+// Generic SoP (a basis with phase-space modes): every factor becomes a dense
+// 1D matrix in the basis (congruence transform h^w = W^T h^chi W, Sec. 2.2
+// Eq. pvb_H_trafo with B -> W for the orthogonal pW), single-factor terms are
+// summed per mode, and terms with several factors keep their factor list for
+// the pruned sequential transform (Sec. 2.2.2).
+static pq_status upload_generic(State& s) {
+    const Basis& b = *s.basis;
+    const int D = s.lat.D, lv = s.lead_virtual;
+    std::vector<std::vector<double>> mats;   // each kMaxN x kMaxN
+    auto factor = [&](int ku, int kind, const std::vector<double>& vals) {
+        const int n = b.modes[ku].n;
+        std::vector<double> F((size_t)n * n, 0.0);
+        if (kind == PQ_FACTOR_KINETIC) F = b.T[ku];
+        else
+            for (int i = 0; i < n; ++i) F[(size_t)i * n + i] = vals[i];
+        if (!b.W[ku].empty()) {   // W^T F W
+            const std::vector<double>& Wm = b.W[ku];
+            std::vector<double> FW((size_t)n * n, 0.0), G((size_t)n * n, 0.0);
+            for (int i = 0; i < n; ++i)
+                for (int q = 0; q < n; ++q) {
+                    double acc = 0.0;
+                    for (int j = 0; j < n; ++j) acc += F[(size_t)i * n + j] * Wm[(size_t)j * n + q];
+                    FW[(size_t)i * n + q] = acc;
+                }
+            for (int p = 0; p < n; ++p)
+                for (int q = 0; q < n; ++q) {
+                    double acc = 0.0;
+                    for (int i = 0; i < n; ++i) acc += Wm[(size_t)i * n + p] * FW[(size_t)i * n + q];
+                    G[(size_t)p * n + q] = acc;
+                }
+            F.swap(G);
+        }
+        std::vector<double> M((size_t)kMaxN * kMaxN, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) M[(size_t)i * kMaxN + j] = F[(size_t)i * n + j];
+        return M;
+    };
+    for (int k = 0; k < kMaxD; ++k) s.gsingle[k] = -1;
+    s.gplan.clear();
+    for (const Basis::GTerm& t : b.gterms) {
+        std::vector<int> fm;
+        for (int ku = 0; ku < b.D_user; ++ku)
+            if (t.kind[ku] != PQ_FACTOR_IDENTITY) fm.push_back(ku);
+        if (fm.size() <= 1) {
+            const int ku = fm.empty() ? b.D_user - 1 : fm[0];
+            const int n = b.modes[ku].n;
+            std::vector<double> M((size_t)kMaxN * kMaxN, 0.0);
+            if (fm.empty())
+                for (int i = 0; i < n; ++i) M[(size_t)i * kMaxN + i] = 1.0;
+            else
+                M = factor(ku, t.kind[ku], t.values[ku]);
+            const int k = ku + lv;
+            if (s.gsingle[k] < 0) {
+                s.gsingle[k] = (int)mats.size();
+                mats.push_back(std::vector<double>((size_t)kMaxN * kMaxN, 0.0));
+            }
+            std::vector<double>& acc = mats[s.gsingle[k]];
+            for (size_t i = 0; i < acc.size(); ++i) acc[i] += t.coef * M[i];
+            continue;
+        }
+        State::GPlan plan;
+        plan.coef = t.coef;
+        for (int f = (int)fm.size() - 1; f >= 0; --f) {   // last mode first
+            plan.passes.push_back(State::GPass{fm[f] + lv, (int)mats.size()});
+            mats.push_back(factor(fm[f], t.kind[fm[f]], t.values[fm[f]]));
+        }
+        s.gplan.push_back(plan);
+    }
+    const size_t nm = std::max<size_t>(mats.size(), 1);
+    std::vector<double> M64(nm * kMaxN * kMaxN, 0.0);
+    for (size_t m = 0; m < mats.size(); ++m)
+        std::copy(mats[m].begin(), mats[m].end(), M64.begin() + m * kMaxN * kMaxN);
+    std::vector<float> M32(M64.begin(), M64.end());
+    pq_status rc;
+    if ((rc = dalloc(&s.gmat64, M64.size() * 8)) || (rc = dalloc(&s.gmat32, M32.size() * 4)))
+        return rc;
+    PQ_CUDA_TRY(cudaMemcpy(s.gmat64, M64.data(), M64.size() * 8, cudaMemcpyHostToDevice));
+    PQ_CUDA_TRY(cudaMemcpy(s.gmat32, M32.data(), M32.size() * 4, cudaMemcpyHostToDevice));
+    if (!s.gplan.empty() && (rc = dalloc(&s.gtmp, 2 * s.cap * 16))) return rc;
+    s.generic = true;
+    (void)D;
+    return PQ_OK;
+}
+
 static pq_status create_state(const pq_basis* basis_, int precision, size_t capacity,
                               State** out) {
     const Basis* basis = reinterpret_cast<const Basis*>(basis_);
@@ -134,11 +221,21 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
         free_state(s);
         return rc;
     }
-    // lattice axes of the neighbour rule: one per DVR mode
-    L.naxes = L.D;
+    // lattice axes of the neighbour rule: one per DVR mode, two (x, p) per
+    // phase-space mode (function index a np + b: x slow, p fast)
+    L.naxes = 0;
     for (int k = 0; k < L.D; ++k) {
-        L.axis_n[k] = L.n[k];
-        L.axis_stride[k] = L.stride[k];
+        const int ku = k - s->lead_virtual;
+        if (ku >= 0 && !basis->W[ku].empty()) {
+            const int npl = basis->modes[ku].np_lattice;
+            L.axis_n[L.naxes] = basis->modes[ku].nx_lattice;
+            L.axis_stride[L.naxes++] = L.stride[k] * (uint32_t)npl;
+            L.axis_n[L.naxes] = npl;
+            L.axis_stride[L.naxes++] = L.stride[k];
+        } else {
+            L.axis_n[L.naxes] = L.n[k];
+            L.axis_stride[L.naxes++] = L.stride[k];
+        }
     }
     s->cap = capacity == 0 ? (size_t)L.nfull : std::min(capacity, (size_t)L.nfull);
     s->rows_cap = std::min(s->cap, (size_t)L.nrows);
@@ -148,7 +245,7 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
         (rc = dalloc(&s->bits_alt, nw * 8)) || (rc = dalloc(&s->off, (nw + 1) * 4)) ||
         (rc = dalloc(&s->off_alt, (nw + 1) * 4)) || (rc = dalloc(&s->rows, s->rows_cap * 4)) ||
         (rc = dalloc(&s->planes, s->rows_cap * 4)) ||
-        (rc = dalloc(&s->leaders, s->rows_cap * 4 * (size_t)std::max(1, L.D - 2))) ||
+        (rc = dalloc(&s->leaders, s->rows_cap * 4 * (size_t)std::max(1, L.D - 1))) ||
         (rc = dalloc(&s->cnt, CNT_SIZE * 8)) || (rc = dalloc(&s->scan_tmp, 1024 * 4)) ||
         (rc = dalloc(&s->red_tmp, (size_t)grid_size() * 4 * (2 * kMaxK + 8) * 8)) ||
         (rc = dalloc(&s->ks, sizeof(KrylovScalars)))) {
@@ -171,7 +268,7 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
     cudaMemset(s->bits, 0, nw * 8);
     cudaMemset(s->off, 0, (nw + 1) * 4);
     cudaMemset(s->ks, 0, sizeof(KrylovScalars));
-    if ((rc = upload_hamiltonian(*s))) {
+    if ((rc = basis->generic ? upload_generic(*s) : upload_hamiltonian(*s))) {
         free_state(s);
         return rc;
     }
@@ -221,9 +318,13 @@ PQ_API pq_status pq_build_basis(const pq_mode_desc* modes, int D, pq_basis** out
     b->x.resize(D);
     b->w.resize(D);
     b->T.resize(D);
+    b->W.resize(D);
     double full = 1;
     for (int k = 0; k < D; ++k) {
-        pq_status rc = build_dvr_mode(modes[k], b->x[k], b->w[k], b->T[k]);
+        pq_status rc = modes[k].kind == PQ_PW
+                           ? build_pw_mode(modes[k], b->x[k], b->w[k], b->T[k], b->W[k])
+                           : build_dvr_mode(modes[k], b->x[k], b->w[k], b->T[k]);
+        if (modes[k].kind == PQ_PW) b->generic = true;
         if (rc) {
             delete b;
             return rc;
@@ -266,6 +367,22 @@ PQ_API pq_status pq_basis_kinetic(const pq_basis* basis_, int mode, double* T) {
     return PQ_OK;
 }
 
+PQ_API pq_status pq_basis_transform(const pq_basis* basis_, int mode, double* Wout) {
+    clear_error();
+    const Basis* b = reinterpret_cast<const Basis*>(basis_);
+    if (!b || !Wout || mode < 0 || mode >= b->D_user) {
+        set_error("bad basis, mode or output");
+        return PQ_EINVAL;
+    }
+    const int n = b->modes[mode].n;
+    if (b->W[mode].empty())
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) Wout[(size_t)i * n + j] = i == j ? 1.0 : 0.0;
+    else
+        memcpy(Wout, b->W[mode].data(), (size_t)n * n * sizeof(double));
+    return PQ_OK;
+}
+
 PQ_API pq_status pq_set_sop(pq_basis* basis_, const pq_sop_term* terms, int nterms) {
     clear_error();
     Basis* b = reinterpret_cast<Basis*>(basis_);
@@ -274,6 +391,44 @@ PQ_API pq_status pq_set_sop(pq_basis* basis_, const pq_sop_term* terms, int nter
         return PQ_EINVAL;
     }
     const int D = b->D_user;
+    if (b->generic) {
+        std::vector<Basis::GTerm> gt;
+        for (int t = 0; t < nterms; ++t) {
+            const pq_sop_term& tm = terms[t];
+            if (!tm.factors || !std::isfinite(tm.coef)) {
+                set_error("term %d: no factors or non-finite coefficient", t);
+                return PQ_EINVAL;
+            }
+            Basis::GTerm g;
+            g.coef = tm.coef;
+            g.kind.resize(D);
+            g.values.resize(D);
+            for (int k = 0; k < D; ++k) {
+                const int kind = tm.factors[k].kind;
+                if (kind != PQ_FACTOR_IDENTITY && kind != PQ_FACTOR_KINETIC && kind != PQ_FACTOR_DIAG) {
+                    set_error("term %d mode %d: unknown factor kind %d", t, k, kind);
+                    return PQ_EINVAL;
+                }
+                g.kind[k] = kind;
+                if (kind == PQ_FACTOR_DIAG) {
+                    if (!tm.factors[k].values) {
+                        set_error("term %d mode %d: diagonal factor without values", t, k);
+                        return PQ_EINVAL;
+                    }
+                    g.values[k].assign(tm.factors[k].values, tm.factors[k].values + b->modes[k].n);
+                    for (double v : g.values[k])
+                        if (!std::isfinite(v)) {
+                            set_error("term %d mode %d: non-finite value", t, k);
+                            return PQ_EINVAL;
+                        }
+                }
+            }
+            gt.push_back(g);
+        }
+        b->gterms = gt;
+        b->sop_set = true;
+        return PQ_OK;
+    }
     std::vector<double> kin(D, 0.0), pc;
     std::vector<std::vector<double>> pv;
     std::vector<uint32_t> pm;

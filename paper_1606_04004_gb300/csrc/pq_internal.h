@@ -88,10 +88,22 @@ struct Basis {
     std::vector<double> pot_coef;                  // per potential term
     std::vector<std::vector<double>> pot_values;   // [term][mode*n_mode + i] (1 for identity)
     std::vector<uint32_t> pot_mask;                // [term] bit k set: mode k not identity
+    // phase-space modes: W (pW coefficients -> DVR coefficients), empty for DVR modes
+    std::vector<std::vector<double>> W;
+    bool generic = false;                          // some mode is a phase-space basis
+    // generic SoP: per term the factor kind and values per mode
+    struct GTerm {
+        double coef;
+        std::vector<int> kind;
+        std::vector<std::vector<double>> values;
+    };
+    std::vector<GTerm> gterms;
 };
 
 pq_status build_dvr_mode(const pq_mode_desc& m, std::vector<double>& x,
                          std::vector<double>& w, std::vector<double>& T);
+pq_status build_pw_mode(const pq_mode_desc& m, std::vector<double>& x, std::vector<double>& w,
+                        std::vector<double>& T, std::vector<double>& W);
 // Normalised packet factors f_k(i) = sqrt(w_i) g_k(x_i) / ||.||, complex interleaved.
 void packet_factors(const Basis& b, const double* q0, const double* p0, const double* width,
                     std::vector<double>& out /* D_int * kMaxN * 2 */, int lead_virtual);
@@ -172,6 +184,14 @@ struct State {
     double* pot64 = nullptr; float* pot32 = nullptr;   // [nterms][D][kMaxN]
     int nterms = 0;
     int ngroup[4] = {0, 0, 0, 0};  // potential terms by the tile modes they touch (see apply_h.cu)
+    // generic SoP (phase-space bases): dense 1D matrices and the pass plan
+    bool generic = false;
+    double* gmat64 = nullptr; float* gmat32 = nullptr;   // [nmat][kMaxN][kMaxN]
+    int gsingle[kMaxD];            // merged single-mode matrix per mode (-1: none)
+    struct GPass { int mode, mat; };
+    struct GPlan { double coef; std::vector<GPass> passes; };   // passes: descending mode
+    std::vector<GPlan> gplan;      // terms with two or more factors
+    void* gtmp = nullptr;          // two scratch vectors (capacity each) for those terms
     double* fac64 = nullptr; float* fac32 = nullptr;   // packet factors [D][kMaxN] complex
     // host side
     double t = 0;

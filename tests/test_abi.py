@@ -66,7 +66,7 @@ def test_argument_errors():
         pq.Basis([dict(kind=pq.HO_DVR, n=64)] * 6)
     assert e.value.status == pq.EINVAL
     with pytest.raises(pq.PQError) as e:
-        pq.Basis([dict(kind=pq.PW, n=16)])
+        pq.Basis([dict(kind=pq.PVB, n=16, xmin=0.5, xmax=6.0, mass=1.0, nx_lattice=4, np_lattice=4)])
     assert e.value.status == pq.ENOTSUP
     b = pq.Basis(pq.modes_of(W.scaled(W.HH4D, D=2)))
     with pytest.raises(pq.PQError) as e:   # kinetic times a diagonal factor
@@ -75,3 +75,21 @@ def test_argument_errors():
     with pytest.raises(pq.PQError) as e:
         b.set_sop([(float("nan"), [None, None])])
     assert e.value.status == pq.EINVAL
+
+
+def test_host_pw_basis_matches_oracle():
+    # the library's projected-Weylet construction (its own Jacobi solver) and
+    # the oracle's (LAPACK) agree: same W = Phi S^(-1/2), a unique matrix
+    pq = _lib()
+    from oracle import bases, propagate
+    cfg = W.scaled(W.MORSE3D, D=2, n=16, nx_lattice=4, np_lattice=4)
+    b = pq.Basis(pq.modes_of(cfg))
+    x, w, T, Wo = bases.pw_basis(16, 0.5, 6.0, 1836.0, 4, 4)
+    xl, wl = b.grid(0)
+    np.testing.assert_allclose(xl, x, atol=1e-14)
+    np.testing.assert_allclose(b.transform(0), Wo, atol=1e-12)
+    np.testing.assert_allclose(b.transform(1), Wo, atol=1e-12)
+    with pytest.raises(pq.PQError) as e:   # lattice does not match the DVR size
+        pq.Basis([dict(kind=pq.PW, n=16, xmin=0.5, xmax=6.0, mass=1.0, nx_lattice=4, np_lattice=3)])
+    assert e.value.status == pq.EINVAL
+    b.set_sop(pq.coupled_morse_terms([xl, xl], 0.1, 1.0, 2.0, 0.005))

@@ -1,0 +1,108 @@
+"""GPU parity of the projected-Weylet path (Sec. 2.4; pruned sequential
+transform of Sec. 2.2.2 with dense 1D factors; adaption on the phase-space
+lattice with two axes per mode) against the FP64 oracle.
+
+H.psi tolerances: FP64 |y - y_ref| <= 1e-12 s_I, FP32 <= 2e-5 s_I with s_I
+the same sequential products taken with |h| and |psi| (each term is up to two
+64-long passes: about 130 roundings of 1.1e-16 resp. 6e-8)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import lib
+
+pytestmark = pytest.mark.gpu
+
+
+def _pw_cfg(D, n, nx, np_):
+    return W.scaled(W.MORSE3D, D=D, n=n, nx_lattice=nx, np_lattice=np_,
+                    q0=W.morse3d_centres()[:D], p0=(0.0,) * D, width=(0.2,) * D)
+
+
+def _state_with(b, A, psi, prec):
+    pq = lib()
+    s = pq.State(b, [0.0] * b.D, [0.0] * b.D, [1.0] * b.D, 1e30, precision=prec)
+    s.load(A, psi)
+    return s
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("D,n,nx,np_,frac", [(2, 16, 4, 4, 0.5), (3, 16, 4, 4, 0.3),
+                                             (2, 64, 8, 8, 0.4), (1, 16, 4, 4, 0.8)])
+def test_pw_apply_random_sets(D, n, nx, np_, frac, prec):
+    import torch
+    from oracle import propagate, pruned
+    pq = lib()
+    cfg = _pw_cfg(D, n, nx, np_)
+    b = pq.build_model(cfg)
+    prob = propagate.problem_from_config(cfg)
+    dims = (n,) * D
+    A = W.random_active_set(dims, frac, seed=D * 10 + n)
+    psi = W.random_psi(len(A), 3).astype(np.complex128 if prec == 0 else np.complex64)
+    s = _state_with(b, A, psi, prec)
+    x = torch.from_numpy(psi).to("cuda")
+    y = torch.empty_like(x)
+    s.apply_H(x, y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.complex128)
+    ref = prob.apply(A, psi.astype(np.complex128))
+    absterms = [(abs(c), {k: np.abs(h) for k, h in f.items()}) for c, f in prob.terms]
+    bound = pruned.apply_H_sop(A, np.abs(psi).astype(np.complex128), dims, absterms).real
+    tol = 1e-12 if prec == 0 else 2e-5
+    err = np.abs(got - ref)
+    assert np.all(err <= tol * bound + 1e-300), (err / np.maximum(bound, 1e-300)).max()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pw_prune_phase_space_axes(prec):
+    from oracle import pruned
+    pq = lib()
+    cfg = _pw_cfg(2, 64, 8, 8)
+    b = pq.build_model(cfg)
+    dims = (64, 64)
+    axes = (8, 8, 8, 8)
+    rng = np.random.default_rng(4)
+    A = W.random_active_set(dims, 0.3, seed=5)
+    psi = rng.uniform(0, 0.6, len(A)) * np.exp(2j * np.pi * rng.random(len(A)))
+    psi[::9] = 0.3
+    psi = psi.astype(np.complex128 if prec == 0 else np.complex64)
+    s = _state_with(b, A, psi, prec)
+    s.prune(0.3)
+    An, pn = s.read()
+    Ar, pr = pruned.prune(A, psi, axes, 0.3)
+    np.testing.assert_array_equal(An, Ar)
+    np.testing.assert_array_equal(pn, pr.astype(pn.dtype))
+
+
+def test_pw_initial_state_morse3d():
+    """The 3D coupled Morse workload in projected Weylets (64^3 lattice)."""
+    from oracle import propagate
+    pq = lib()
+    cfg = W.scaled(W.MORSE3D, q0=W.morse3d_centres())
+    b = pq.build_model(cfg)
+    prob = propagate.problem_from_config(cfg)
+    A, a, f = propagate.initial_state(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"])
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP64)
+    Ag, ag = s.read()
+    np.testing.assert_array_equal(Ag, A)
+    np.testing.assert_allclose(ag, a, rtol=1e-12, atol=1e-12 * np.abs(a).max())
+
+
+@pytest.mark.parametrize("name,D,n,nx,np_,nsteps", [("small", 2, 16, 4, 4, 8),
+                                                   ("morse3d", 3, 64, 8, 8, 3)])
+def test_pw_propagation_fp64(name, D, n, nx, np_, nsteps):
+    from oracle import propagate
+    pq = lib()
+    cfg = _pw_cfg(D, n, nx, np_)
+    b = pq.build_model(cfg)
+    prob = propagate.problem_from_config(cfg)
+    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], cfg["K"], cfg["dt"],
+                      nsteps)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP64)
+    s.propagate(cfg["K"], cfg["dt"], cfg["theta"], nsteps)
+    o = s.observables()
+    np.testing.assert_array_equal(o["n_active"], [x["n_active"] for x in r["obs"]])
+    A, psi = s.read()
+    np.testing.assert_array_equal(A, r["A"])
+    assert np.linalg.norm(psi - r["a"]) <= 1e-10 * np.linalg.norm(r["a"])
+    assert np.max(np.abs(o["C"] - np.array([x["C"] for x in r["obs"]]))) < 1e-10

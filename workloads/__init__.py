@@ -44,7 +44,7 @@ HH6D = dict(
 )
 
 MORSE3D = dict(
-    name="morse3d", D=3, basis="sine", n=64, xmin=0.5, xmax=6.0, mass=1836.0,
+    name="morse3d", D=3, basis="pw", n=64, xmin=0.5, xmax=6.0, mass=1836.0,
     morse_D=0.1, morse_a=1.0, morse_qe=2.0, coupling=0.005,
     nx_lattice=8, np_lattice=8, width=(0.2,) * 3, p0=(0.0,) * 3,
     K=10, dt=10.0, nsteps=400, theta=1e-6, radius=1, seed=1606,
