@@ -230,6 +230,38 @@ pq_status pq_set_timing(pq_state* state, int enable);
 pq_status pq_timing_get(pq_state* state, double* apply_ms, int64_t* n_apply,
                         double* coef_applied);
 
+/* Gradient of the survival probability P = |<Psi(0)|Psi(T)>|^2 (Psi(0) the
+ * normalised full packet, as in the autocorrelation of Eq. acorr), T =
+ * nsteps * desc->dt, with respect to parameters of the Hamiltonian or of the
+ * packet.  The paper computes C(t) only; the gradient is taken of that
+ * quantity.  The run starts from the state's initial packet and adaption;
+ * the sequence of active sets of that run is recorded and then held fixed
+ * (the map is differentiable only with the sets frozen).  Backward sweep
+ * with adjoint vectors, lambda_n = exp(+i H_{A_n} dt) R_n^T lambda_{n+1},
+ * psi_n recomputed from checkpoints taken every `ckpt_every` steps; the
+ * time integral of <lambda| dH/dtheta |psi> over each step by 5-point
+ * Gauss-Legendre with SIL propagators (negative times for the adjoint).
+ * Parameters:
+ *   PQ_PARAM_POTENTIAL  dH/dtheta as diagonal SoP terms on the DVR grid
+ *                       (PQ_FACTOR_DIAG / PQ_FACTOR_IDENTITY factors);
+ *   PQ_PARAM_CENTRE     the packet centre q0 of `mode`.
+ * grad_out: nparams doubles (host); P_out (nullable): P.  DVR bases only
+ * (PQ_ENOTSUP otherwise), at most 16 parameters.  The state is left at its
+ * initial packet; its recorded observables are not changed.  Synchronises.
+ * Allocates device memory for the recorded sets and checkpoints. */
+typedef enum pq_param_kind { PQ_PARAM_POTENTIAL = 0, PQ_PARAM_CENTRE = 1 } pq_param_kind;
+
+typedef struct pq_param_desc {
+    int kind;                   /* pq_param_kind                                  */
+    int mode;                   /* PQ_PARAM_CENTRE: mode whose q0 is the parameter */
+    const pq_sop_term* dterms;  /* PQ_PARAM_POTENTIAL: dH/dtheta terms             */
+    int nterms;
+} pq_param_desc;
+
+pq_status pq_survival_grad(pq_state* state, const pq_prop_desc* desc, int nsteps,
+                           int ckpt_every, const pq_param_desc* params, int nparams,
+                           double* grad_out, double* P_out, void* stream);
+
 /* Observables of the state's current coefficients without any device
  * allocation.  The paper has no counterpart: this entry point exists for
  * callers that must not let a library call cudaMalloc / cudaFree, e.g. code

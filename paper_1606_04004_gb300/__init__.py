@@ -67,6 +67,13 @@ class Observables(C.Structure):
                 ("n_wasted", C.POINTER(C.c_int64))]
 
 
+class ParamDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("mode", C.c_int), ("dterms", C.POINTER(SopTerm)),
+                ("nterms", C.c_int)]
+
+
+PARAM_POTENTIAL, PARAM_CENTRE = 0, 1
+
 _vp = C.c_void_p
 _SIGS = {
     "pq_build_basis": [C.POINTER(ModeDesc), C.c_int, C.POINTER(_vp)],
@@ -90,6 +97,8 @@ _SIGS = {
     "pq_set_timing": [_vp, C.c_int],
     "pq_timing_get": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
     "pq_observe_noalloc": [_vp, C.c_double, _vp, _vp],
+    "pq_survival_grad": [_vp, C.POINTER(PropDesc), C.c_int, C.c_int, C.POINTER(ParamDesc), C.c_int,
+                         _vp, _vp, _vp],
     "pq_launch_count": [],
     "pq_last_error": [],
 }
@@ -168,11 +177,19 @@ class Basis:
         """terms: list of (coef, [factor per mode]) with factor None (identity),
         "T" (kinetic) or an array of n values (diagonal)."""
         keep = []
+        carr = _marshal_terms(self.dims, terms, keep)
+        _check(_lib.pq_set_sop(self._h, carr, len(terms)))
+
+
+def _marshal_terms(dims, terms, keep):
+    """SoP terms -> a ctypes pq_sop_term array (arrays kept alive in `keep`)."""
+    D = len(dims)
+    if True:
         carr = (SopTerm * max(1, len(terms)))()
         for t, (coef, facs) in enumerate(terms):
-            if len(facs) != self.D:
+            if len(facs) != D:
                 raise ValueError("one factor per mode")
-            fa = (Factor * self.D)()
+            fa = (Factor * D)()
             for k, f in enumerate(facs):
                 if f is None:
                     fa[k] = Factor(FACTOR_IDENTITY, None)
@@ -180,13 +197,13 @@ class Basis:
                     fa[k] = Factor(FACTOR_KINETIC, None)
                 else:
                     v = np.ascontiguousarray(f, dtype=np.float64)
-                    if v.shape != (self.dims[k],):
-                        raise ValueError(f"factor of mode {k} needs {self.dims[k]} values")
+                    if v.shape != (dims[k],):
+                        raise ValueError(f"factor of mode {k} needs {dims[k]} values")
                     keep.append(v)
                     fa[k] = Factor(FACTOR_DIAG, v.ctypes.data_as(C.POINTER(C.c_double)))
             keep.append(fa)
             carr[t] = SopTerm(float(coef), fa)
-        _check(_lib.pq_set_sop(self._h, carr, len(terms)))
+        return carr
 
 
 # ------------------------------------------------------------------ state
@@ -292,6 +309,29 @@ class State:
         _check(_lib.pq_observe_noalloc(self._h, float(theta), _dptr(out), _vp(stream or 0)))
         return dict(C=complex(out[0], out[1]), norm2=float(out[2]), n_wasted=int(round(out[3])))
 
+    def survival_grad(self, K, dt, theta, nsteps, ckpt_every, params, reorth=1, radius=1,
+                      stream=None):
+        """P = |<Psi(0)|Psi(T)>|^2 and dP/dtheta (pq_survival_grad).  params:
+        list of ("centre", mode) or ("potential", dH/dtheta SoP terms)."""
+        keep = []
+        parr = (ParamDesc * max(1, len(params)))()
+        dims = self.basis.dims
+        for i, (kind, arg) in enumerate(params):
+            if kind == "centre":
+                parr[i] = ParamDesc(PARAM_CENTRE, int(arg), None, 0)
+            elif kind == "potential":
+                terms = _marshal_terms(dims, arg, keep)
+                keep.append(terms)
+                parr[i] = ParamDesc(PARAM_POTENTIAL, 0, terms, len(arg))
+            else:
+                raise ValueError(kind)
+        grad = np.zeros(max(1, len(params)))
+        P = C.c_double()
+        d = PropDesc(int(K), float(dt), float(theta), int(radius), int(reorth))
+        _check(_lib.pq_survival_grad(self._h, C.byref(d), int(nsteps), int(ckpt_every), parr,
+                                     len(params), _dptr(grad), C.byref(P), _vp(stream or 0)))
+        return P.value, grad[:len(params)]
+
     def set_timing(self, enable=True):
         _check(_lib.pq_set_timing(self._h, int(enable)))
 
@@ -302,4 +342,4 @@ class State:
 
 
 from .hamiltonians import (build_model, henon_heiles_terms, coupled_morse_terms,  # noqa: E402
-                           modes_of)
+                           modes_of, henon_heiles_param_derivs)

@@ -534,6 +534,11 @@ PQ_API pq_status pq_init_packet(const pq_basis* basis_, const double* q0, const 
     cudaMemcpy(s->fac32, fac32.data(), fac32.size() * 4, cudaMemcpyHostToDevice);
     s->theta = theta;
     s->radius = radius;
+    for (int k = 0; k < b->D_user; ++k) {
+        s->q0[k] = q0[k];
+        s->p0[k] = p0[k];
+        s->width[k] = width[k];
+    }
     cudaStream_t st = 0;
     if ((rc = init_bits_from_packet(*s, theta, st)) || (rc = check_capacity(*s, st)) ||
         (rc = set_psi_from_packet(*s, st)) || (rc = observe_launch(*s, theta, st))) {

@@ -522,6 +522,27 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
     return PQ_OK;
 }
 
+pq_status ensure_krylov(State& s, int K) {
+    if (s.V_K >= K) return PQ_OK;
+    if (s.V) cudaFree(s.V);
+    s.V = nullptr;
+    s.V_K = 0;
+    cudaError_t e = cudaMalloc(&s.V, (size_t)K * s.cap * s.esize);
+    if (e != cudaSuccess) {
+        set_error("cannot allocate the Krylov space (%zu bytes): %s", (size_t)K * s.cap * s.esize,
+                  cudaGetErrorString(e));
+        return PQ_ENOMEM;
+    }
+    s.V_K = K;
+    return PQ_OK;
+}
+
+pq_status sil_only(State& s, const pq_prop_desc& d, cudaStream_t st) {
+    pq_status rc = ensure_krylov(s, d.K);
+    if (rc) return rc;
+    return s.prec == PQ_FP64 ? sil_step<double>(s, d, nullptr, st) : sil_step<float>(s, d, nullptr, st);
+}
+
 pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream_t st) {
     if (d.K < 1 || d.K > kMaxK) {
         set_error("Krylov dimension %d outside 1..%d", d.K, kMaxK);
@@ -535,18 +556,8 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
         set_error("neighbour radius %d not provided (radius 1 only)", d.radius);
         return PQ_ENOTSUP;
     }
-    if (s.V_K < d.K) {
-        if (s.V) cudaFree(s.V);
-        s.V = nullptr;
-        s.V_K = 0;
-        cudaError_t e = cudaMalloc(&s.V, (size_t)d.K * s.cap * s.esize);
-        if (e != cudaSuccess) {
-            set_error("cannot allocate the Krylov space (%zu bytes): %s",
-                      (size_t)d.K * s.cap * s.esize, cudaGetErrorString(e));
-            return PQ_ENOMEM;
-        }
-        s.V_K = d.K;
-    }
+    pq_status erc = ensure_krylov(s, d.K);
+    if (erc) return erc;
     if (nsteps == 0) return PQ_OK;
     double* recs = nullptr;
     PQ_CUDA_TRY(cudaMallocAsync((void**)&recs, (size_t)(nsteps + 1) * 8 * sizeof(double), st));

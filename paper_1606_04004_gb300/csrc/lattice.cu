@@ -414,15 +414,15 @@ __global__ void k_set_bits(const uint32_t* __restrict__ keys, int64_t n, uint64_
 
 // Replace the active set by n sorted distinct keys already on the device
 // (d_keys may alias nothing of the state).
-pq_status load_set(State& s, const uint32_t* d_keys, int64_t n, cudaStream_t st) {
+pq_status load_set(State& s, const uint32_t* d_keys, int64_t n, cudaStream_t st, bool remap) {
     const Lattice& L = s.lat;
-    PQ_CUDA_TRY(cudaMemsetAsync(s.cnt + CNT_ERR, 0, sizeof(int64_t), st));
+    if (!remap) PQ_CUDA_TRY(cudaMemsetAsync(s.cnt + CNT_ERR, 0, sizeof(int64_t), st));
     PQ_CUDA_TRY(cudaMemsetAsync(s.bits_alt, 0, (size_t)L.nwords * 8, st));
     if (n > 0) {
         k_set_bits<<<grid_size() * 8, 256, 0, st>>>(d_keys, n, s.bits_alt);
         PQ_CHECK_LAUNCH();
     }
-    return rebuild_from_bits(s, false, st);
+    return rebuild_from_bits(s, remap, st);
 }
 
 // -------------------------------------------------------------- setup

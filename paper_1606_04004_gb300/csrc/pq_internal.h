@@ -201,6 +201,7 @@ struct State {
     int radius = 1;
     Timing timing;
     int64_t* h_cnt = nullptr;      // pinned mirror of cnt
+    double q0[kMaxD] = {0}, p0[kMaxD] = {0}, width[kMaxD] = {0};   // packet (caller modes)
     void* io_in = nullptr;         // staging buffers of pq_apply_H_host
     void* io_out = nullptr;
     cudaStream_t last_stream = nullptr;
@@ -212,7 +213,11 @@ pq_status rebuild_from_bits(State& s, bool remap, cudaStream_t st);
 pq_status prune_launch(State& s, double theta, int radius, cudaStream_t st);
 pq_status init_bits_from_packet(State& s, double theta, cudaStream_t st);
 pq_status set_psi_from_packet(State& s, cudaStream_t st);
-pq_status load_set(State& s, const uint32_t* d_keys, int64_t n, cudaStream_t st);
+// Replace the active set by n sorted keys on the device; with remap the
+// current coefficients are carried over (kept where the point stays, zero
+// where it is new), else they are left undefined.
+pq_status load_set(State& s, const uint32_t* d_keys, int64_t n, cudaStream_t st,
+                   bool remap = false);
 int grid_size();
 
 // apply_h.cu
@@ -224,7 +229,16 @@ pq_status apply_H_launch(const State& s, const void* in, void* out, int prec,
 
 // krylov.cu
 pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream_t st);
+pq_status ensure_krylov(State& s, int K);
+// One SIL step of the state's coefficients on the current set (no adaption,
+// no observables); dt may be negative (backward propagation).
+pq_status sil_only(State& s, const pq_prop_desc& d, cudaStream_t st);
 pq_status observe_launch(State& s, double theta, cudaStream_t st);
 pq_status energy_of_current(State& s, double* E, cudaStream_t st);
+
+// adjoint.cu
+pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
+                        const pq_param_desc* params, int np, double* grad, double* P_out,
+                        cudaStream_t st);
 
 }  // namespace pq

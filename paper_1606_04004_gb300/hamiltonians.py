@@ -77,3 +77,28 @@ def build_model(cfg, omegas=None, lam=None):
         terms = henon_heiles_terms(grids, cfg["lam"] if lam is None else lam, omegas)
     b.set_sop(terms)
     return b
+
+
+def henon_heiles_param_derivs(grids, lam, omegas=None):
+    """Parameters of the Henon-Heiles workload for the survival gradient, in
+    the order (lambda, omega_1..omega_D, q0_1..q0_D): dH/dlambda =
+    sum_k (q_k^2 q_{k+1} - q_{k+1}^3/3), dH/domega_k = omega_k q_k^2, and the
+    packet centres."""
+    D = len(grids)
+    om = np.ones(D) if omegas is None else np.asarray(omegas, dtype=np.float64)
+    dlam = []
+    for k in range(D - 1):
+        f = [None] * D
+        f[k] = grids[k] ** 2
+        f[k + 1] = grids[k + 1]
+        dlam.append((1.0, f))
+        g = [None] * D
+        g[k + 1] = grids[k + 1] ** 3
+        dlam.append((-1.0 / 3.0, g))
+    params = [("potential", dlam)]
+    for k in range(D):
+        f = [None] * D
+        f[k] = grids[k] ** 2
+        params.append(("potential", [(float(om[k]), f)]))
+    params += [("centre", k) for k in range(D)]
+    return params

@@ -1,0 +1,87 @@
+"""Adjoint gradient of the survival probability on the GPU (pq_survival_grad)
+against central finite differences (h = 1e-4) of the FP64 oracle with the
+sets of active functions frozen, relative error <= 1e-4 (norm-wise, and per
+component against the largest component)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import lib
+
+pytestmark = pytest.mark.gpu
+
+
+def _reduced(nsteps=6):
+    # 4D Henon-Heiles with 12 HO-DVR points per mode, short horizon so that
+    # P stays O(0.1) and the finite differences are well conditioned
+    return W.scaled(W.HH4D, n=12, nsteps=nsteps)
+
+
+def _gpu_grad(cfg, prec, ckpt):
+    pq = lib()
+    b = pq.build_model(cfg)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=prec)
+    grids = [b.grid(k)[0] for k in range(cfg["D"])]
+    return s.survival_grad(cfg["K"], cfg["dt"], cfg["theta"], cfg["nsteps"], ckpt,
+                           pq.henon_heiles_param_derivs(grids, cfg["lam"]))
+
+
+_FD_CACHE = {}
+
+
+def _oracle_fd(cfg):
+    key = (cfg["n"], cfg["nsteps"])
+    if key not in _FD_CACHE:
+        _FD_CACHE[key] = _oracle_fd_compute(cfg)
+    return _FD_CACHE[key]
+
+
+def _oracle_fd_compute(cfg):
+    from oracle import adjoint, propagate
+    prob = propagate.problem_from_config(cfg)
+    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], cfg["K"], cfg["dt"],
+                      cfg["nsteps"], record_sets=True)
+    params = [cfg["lam"]] + [1.0] * cfg["D"] + list(cfg["q0"])
+    P, C = adjoint.survival(cfg, params, r["sets"])
+    return P, adjoint.fd_gradient(cfg, params, r["sets"], h=1e-4)
+
+
+@pytest.mark.parametrize("prec,ckpt", [(0, 2), (0, 100), (1, 3)])
+def test_adjoint_vs_oracle_fd(prec, ckpt):
+    cfg = _reduced()
+    P_ref, g_ref = _oracle_fd(cfg)
+    P, g = _gpu_grad(cfg, prec, ckpt)
+    assert abs(P - P_ref) <= (1e-12 if prec == 0 else 1e-6) * max(P_ref, 1e-300)
+    scale = np.abs(g_ref).max()
+    assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref), (g, g_ref)
+    assert np.all(np.abs(g - g_ref) <= 1e-4 * scale), (g, g_ref)
+
+
+def test_adjoint_full_config():
+    """The adjoint workload as specified (4D Henon-Heiles, 24 points per mode,
+    T = 20, checkpoints every 25 steps).  FP64: the gradient does not depend
+    on the checkpoint interval (the recomputation replays the forward run
+    exactly).  FP32-mix forward: agrees with FP64 to 2e-3 -- FP32 storage
+    limits the relative accuracy of a small overlap (P ~ 1e-4 here; the FP32
+    tolerance |dC| <= 1e-5 on C ~ 1e-2 is itself 1e-3 relative)."""
+    cfg = W.ADJOINT4D
+    P64, g64 = _gpu_grad(cfg, 0, cfg["ckpt_every"])
+    P64b, g64b = _gpu_grad(cfg, 0, 2 * cfg["ckpt_every"])
+    assert P64 > 0 and P64b == P64
+    np.testing.assert_allclose(g64b, g64, rtol=1e-12, atol=1e-15)
+    P32, g32 = _gpu_grad(cfg, 1, cfg["ckpt_every"])
+    assert abs(P32 - P64) <= 2e-3 * P64
+    assert np.linalg.norm(g32 - g64) <= 2e-3 * np.linalg.norm(g64), (g32, g64)
+
+
+def test_autograd_function():
+    import torch
+    from paper_1606_04004_gb300.autograd import survival_probability
+    pq = lib()
+    cfg = _reduced(4)
+    theta = torch.tensor([cfg["lam"]] + [1.0] * 4 + list(cfg["q0"]), dtype=torch.float64,
+                         requires_grad=True)
+    P = survival_probability(theta, cfg, pq.FP64, 2)
+    P.backward()
+    _, g = _gpu_grad(cfg, 0, 2)
+    np.testing.assert_allclose(theta.grad.numpy(), g, rtol=1e-12, atol=0)
