@@ -1183,6 +1183,13 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
 
 pq_status apply_H_launch(const State& s, const void* in, void* out, int prec,
                          const double* in_scale, const int* skip, int skip_k, cudaStream_t st) {
+    if (s.pvb) {   // H_AA on the full grid (pvb.cu); called only from the C ABI
+        if (in_scale || skip) {
+            set_error("internal: scaled / skipped H.psi is not defined for pvB");
+            return PQ_EINVAL;
+        }
+        return pvb_apply(const_cast<State&>(s), in, out, prec, st);
+    }
     if (prec == PQ_FP64) return launch_all<double>(s, in, out, in_scale, skip, skip_k, st);
     if (prec == PQ_FP32MIX) return launch_all<float>(s, in, out, in_scale, skip, skip_k, st);
     set_error("unknown precision %d", prec);

@@ -228,6 +228,120 @@ pq_status build_pw_mode(const pq_mode_desc& m, std::vector<double>& x, std::vect
     return PQ_OK;
 }
 
+// Complex Gauss-Jordan inverse with partial pivoting (A: n x n interleaved
+// re/im, row-major; replaced by its inverse).  Returns false if singular.
+static bool complex_inverse(int n, std::vector<double>& A) {
+    std::vector<double> I((size_t)n * n * 2, 0.0);
+    for (int i = 0; i < n; ++i) I[((size_t)i * n + i) * 2] = 1.0;
+    auto at = [n](std::vector<double>& M, int r, int c) { return &M[((size_t)r * n + c) * 2]; };
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        double best = 0.0;
+        for (int r = c; r < n; ++r) {
+            const double* v = at(A, r, c);
+            const double m = v[0] * v[0] + v[1] * v[1];
+            if (m > best) {
+                best = m;
+                piv = r;
+            }
+        }
+        if (!(best > 0.0)) return false;
+        if (piv != c)
+            for (int k = 0; k < n; ++k) {
+                std::swap(at(A, c, k)[0], at(A, piv, k)[0]);
+                std::swap(at(A, c, k)[1], at(A, piv, k)[1]);
+                std::swap(at(I, c, k)[0], at(I, piv, k)[0]);
+                std::swap(at(I, c, k)[1], at(I, piv, k)[1]);
+            }
+        const double pr = at(A, c, c)[0], pi = at(A, c, c)[1], d = pr * pr + pi * pi;
+        const double ir = pr / d, ii = -pi / d;   // 1 / pivot
+        for (int k = 0; k < n; ++k) {
+            double* a = at(A, c, k);
+            double* b = at(I, c, k);
+            const double ar = a[0] * ir - a[1] * ii, ai = a[0] * ii + a[1] * ir;
+            const double br = b[0] * ir - b[1] * ii, bi = b[0] * ii + b[1] * ir;
+            a[0] = ar; a[1] = ai; b[0] = br; b[1] = bi;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double fr = at(A, r, c)[0], fi = at(A, r, c)[1];
+            if (fr == 0.0 && fi == 0.0) continue;
+            for (int k = 0; k < n; ++k) {
+                double* a = at(A, r, k);
+                const double* ac = at(A, c, k);
+                a[0] -= fr * ac[0] - fi * ac[1];
+                a[1] -= fr * ac[1] + fi * ac[0];
+                double* b = at(I, r, k);
+                const double* bc = at(I, c, k);
+                b[0] -= fr * bc[0] - fi * bc[1];
+                b[1] -= fr * bc[1] + fi * bc[0];
+            }
+        }
+    }
+    A.swap(I);
+    return true;
+}
+
+// Biorthogonal projected von Neumann basis (Sec. 2.2) on a sine DVR: von
+// Neumann Gaussians on the lattice Dx Dp = 2 pi (x_a cell-centred, momenta
+// p_b = -p_max + (b + 1/2) Dp, p_max = np Dp / 2, alpha = Dp / (2 Dx)),
+// projected (Eq. pvN_def): G_jm = sqrt(w_j) g_m(x_j); B = G^{-dagger}
+// (Eq. pvb_def: B^dagger G = 1); S = B^dagger B.  Complex n x n, interleaved.
+pq_status build_pvb_mode(const pq_mode_desc& m, std::vector<double>& x, std::vector<double>& w,
+                         std::vector<double>& T, std::vector<double>& G, std::vector<double>& B,
+                         std::vector<double>& S) {
+    const int n = m.n, nx = m.nx_lattice, np_ = m.np_lattice;
+    if (nx < 1 || np_ < 1 || nx * np_ != n) {
+        set_error("pvB needs nx_lattice * np_lattice = n (%d x %d != %d)", nx, np_, n);
+        return PQ_EINVAL;
+    }
+    if (!(m.xmax > m.xmin) || !(m.mass > 0)) {
+        set_error("pvB needs xmax > xmin and mass > 0");
+        return PQ_EINVAL;
+    }
+    sine_dvr(n, m.xmin, m.xmax, m.mass, x, w, T);
+    const double L = m.xmax - m.xmin, dx = L / nx, dp = 2.0 * M_PI / dx, alpha = dp / (2.0 * dx);
+    const double pmax = np_ * dp / 2.0, amp = pow(2.0 * alpha / M_PI, 0.25);
+    G.assign((size_t)n * n * 2, 0.0);
+    for (int a = 0; a < nx; ++a) {
+        const double xa = m.xmin + (a + 0.5) * dx;
+        for (int b = 0; b < np_; ++b) {
+            const double pb = -pmax + (b + 0.5) * dp;
+            for (int j = 0; j < n; ++j) {
+                const double d = x[j] - xa;
+                const double mag = sqrt(w[j]) * (amp * exp(-alpha * d * d));
+                G[((size_t)j * n + a * np_ + b) * 2] = mag * cos(pb * d);
+                G[((size_t)j * n + a * np_ + b) * 2 + 1] = mag * sin(pb * d);
+            }
+        }
+    }
+    std::vector<double> Gi = G;
+    if (!complex_inverse(n, Gi)) {
+        set_error("pvB: the projected von Neumann matrix G is singular");
+        return PQ_ENUMERIC;
+    }
+    B.assign((size_t)n * n * 2, 0.0);   // B = (G^-1)^dagger
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            B[((size_t)i * n + j) * 2] = Gi[((size_t)j * n + i) * 2];
+            B[((size_t)i * n + j) * 2 + 1] = -Gi[((size_t)j * n + i) * 2 + 1];
+        }
+    S.assign((size_t)n * n * 2, 0.0);   // S = B^dagger B
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q) {
+            double sr = 0.0, si = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const double ar = B[((size_t)k * n + p) * 2], ai = -B[((size_t)k * n + p) * 2 + 1];
+                const double br = B[((size_t)k * n + q) * 2], bi = B[((size_t)k * n + q) * 2 + 1];
+                sr += ar * br - ai * bi;
+                si += ar * bi + ai * br;
+            }
+            S[((size_t)p * n + q) * 2] = sr;
+            S[((size_t)p * n + q) * 2 + 1] = si;
+        }
+    return PQ_OK;
+}
+
 pq_status build_dvr_mode(const pq_mode_desc& m, std::vector<double>& x, std::vector<double>& w,
                          std::vector<double>& T) {
     if (m.n < 2 || m.n > kMaxN) {
@@ -257,10 +371,6 @@ pq_status build_dvr_mode(const pq_mode_desc& m, std::vector<double>& x, std::vec
         }
         return PQ_OK;
     }
-    if (m.kind == PQ_PVB) {
-        set_error("the pvB basis is not provided by this build");
-        return PQ_ENOTSUP;
-    }
     set_error("unknown basis kind %d", m.kind);
     return PQ_EINVAL;
 }
@@ -288,6 +398,17 @@ void packet_factors(const Basis& b, const double* q0, const double* p0, const do
         }
         nrm = sqrt(nrm);
         for (int i = 0; i < 2 * n; ++i) f[i] /= nrm;
+        if (!b.Gc[k].empty()) {   // pvB coefficients: G^dagger f (Eq. psi_exp_pvb)
+            std::vector<double> g(2 * n, 0.0);
+            const std::vector<double>& M = b.Gc[k];
+            for (int q = 0; q < n; ++q)
+                for (int j = 0; j < n; ++j) {
+                    const double mr = M[((size_t)j * n + q) * 2], mi = -M[((size_t)j * n + q) * 2 + 1];
+                    g[2 * q] += mr * f[2 * j] - mi * f[2 * j + 1];
+                    g[2 * q + 1] += mr * f[2 * j + 1] + mi * f[2 * j];
+                }
+            for (int i = 0; i < 2 * n; ++i) f[i] = g[i];
+        }
         if (!b.W[k].empty()) {   // pW coefficients: W^T f
             std::vector<double> g(2 * n, 0.0);
             for (int q = 0; q < n; ++q)

@@ -28,6 +28,12 @@ void clear_error() { g_err.clear(); }
 static void free_state(State* s) {
     if (!s) return;
     if (s->rowinfo) cudaFree(s->rowinfo);
+    {
+        void* pv[] = {s->pvbB64, s->pvbB32, s->pvbBh64, s->pvbBh32, s->pvbS64, s->pvbS32,
+                      s->pvbT64, s->pvbT32, s->pvb_grid, s->pvb_vec, s->fac_bra64};
+        for (void* p : pv)
+            if (p) cudaFree(p);
+    }
     if (s->gmat64) cudaFree(s->gmat64);
     if (s->gmat32) cudaFree(s->gmat32);
     if (s->gtmp) cudaFree(s->gtmp);
@@ -192,6 +198,55 @@ static pq_status upload_generic(State& s) {
     return PQ_OK;
 }
 
+// pvB matrices (Sec. 2.2): B, B^dagger, S = B^dagger B and the kinetic
+// matrices as complex [D][kMaxN][kMaxN][2]; full-grid and work buffers.
+static pq_status upload_pvb(State& s) {
+    const Basis& b = *s.basis;
+    const int D = s.lat.D, lv = s.lead_virtual;
+    const size_t msz = (size_t)D * kMaxN * kMaxN * 2;
+    std::vector<double> Bm(msz, 0.0), Bh(msz, 0.0), Sm(msz, 0.0), Tm(msz, 0.0);
+    double smax = 0.0;
+    for (int k = 0; k < D; ++k) {
+        const int ku = k - lv;
+        const int n = ku < 0 ? 1 : b.modes[ku].n;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const size_t o = (((size_t)k * kMaxN + i) * kMaxN + j) * 2;
+                if (ku < 0) {   // virtual size-1 mode: identity, no kinetic energy
+                    Bm[o] = Bh[o] = Sm[o] = 1.0;
+                    continue;
+                }
+                const size_t e = ((size_t)i * n + j) * 2, et = ((size_t)j * n + i) * 2;
+                Bm[o] = b.Bc[ku][e];
+                Bm[o + 1] = b.Bc[ku][e + 1];
+                Bh[o] = b.Bc[ku][et];
+                Bh[o + 1] = -b.Bc[ku][et + 1];
+                Sm[o] = b.Sc[ku][e];
+                Sm[o + 1] = b.Sc[ku][e + 1];
+                smax = std::max(smax, std::hypot(Sm[o], Sm[o + 1]));
+                Tm[o] = b.kin_scale[ku] * b.T[ku][(size_t)i * n + j];
+            }
+    }
+    auto up = [&](const std::vector<double>& h, double** d64, float** d32) -> pq_status {
+        std::vector<float> h32(h.begin(), h.end());
+        pq_status rc;
+        if ((rc = dalloc(d64, h.size() * 8)) || (rc = dalloc(d32, h.size() * 4))) return rc;
+        PQ_CUDA_TRY(cudaMemcpy(*d64, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+        PQ_CUDA_TRY(cudaMemcpy(*d32, h32.data(), h32.size() * 4, cudaMemcpyHostToDevice));
+        return PQ_OK;
+    };
+    pq_status rc;
+    if ((rc = up(Bm, &s.pvbB64, &s.pvbB32)) || (rc = up(Bh, &s.pvbBh64, &s.pvbBh32)) ||
+        (rc = up(Sm, &s.pvbS64, &s.pvbS32)) || (rc = up(Tm, &s.pvbT64, &s.pvbT32)))
+        return rc;
+    if ((rc = dalloc(&s.pvb_grid, (size_t)3 * s.lat.nfull * s.esize)) ||
+        (rc = dalloc(&s.pvb_vec, (size_t)5 * s.cap * s.esize)))
+        return rc;
+    s.pvb_smax = smax > 0 ? smax : 1.0;
+    s.pvb = true;
+    return PQ_OK;
+}
+
 static pq_status create_state(const pq_basis* basis_, int precision, size_t capacity,
                               State** out) {
     const Basis* basis = reinterpret_cast<const Basis*>(basis_);
@@ -226,7 +281,7 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
     L.naxes = 0;
     for (int k = 0; k < L.D; ++k) {
         const int ku = k - s->lead_virtual;
-        if (ku >= 0 && !basis->W[ku].empty()) {
+        if (ku >= 0 && (!basis->W[ku].empty() || !basis->Bc[ku].empty())) {
             const int npl = basis->modes[ku].np_lattice;
             L.axis_n[L.naxes] = basis->modes[ku].nx_lattice;
             L.axis_stride[L.naxes++] = L.stride[k] * (uint32_t)npl;
@@ -268,7 +323,8 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
     cudaMemset(s->bits, 0, nw * 8);
     cudaMemset(s->off, 0, (nw + 1) * 4);
     cudaMemset(s->ks, 0, sizeof(KrylovScalars));
-    if ((rc = basis->generic ? upload_generic(*s) : upload_hamiltonian(*s))) {
+    if ((rc = basis->generic ? upload_generic(*s) : upload_hamiltonian(*s)) ||
+        (basis->pvb && (rc = upload_pvb(*s)))) {
         free_state(s);
         return rc;
     }
@@ -319,10 +375,24 @@ PQ_API pq_status pq_build_basis(const pq_mode_desc* modes, int D, pq_basis** out
     b->w.resize(D);
     b->T.resize(D);
     b->W.resize(D);
+    b->Gc.resize(D);
+    b->Bc.resize(D);
+    b->Sc.resize(D);
+    int npvb = 0;
+    for (int k = 0; k < D; ++k) npvb += modes[k].kind == PQ_PVB;
+    if (npvb != 0 && npvb != D) {
+        set_error("a pvB basis must use pvB for every mode (mixed bases are not provided)");
+        delete b;
+        return PQ_ENOTSUP;
+    }
+    b->pvb = npvb == D;
     double full = 1;
     for (int k = 0; k < D; ++k) {
         pq_status rc = modes[k].kind == PQ_PW
                            ? build_pw_mode(modes[k], b->x[k], b->w[k], b->T[k], b->W[k])
+                       : modes[k].kind == PQ_PVB
+                           ? build_pvb_mode(modes[k], b->x[k], b->w[k], b->T[k], b->Gc[k], b->Bc[k],
+                                            b->Sc[k])
                            : build_dvr_mode(modes[k], b->x[k], b->w[k], b->T[k]);
         if (modes[k].kind == PQ_PW) b->generic = true;
         if (rc) {
@@ -532,6 +602,17 @@ PQ_API pq_status pq_init_packet(const pq_basis* basis_, const double* q0, const 
     }
     cudaMemcpy(s->fac64, fac.data(), fac.size() * 8, cudaMemcpyHostToDevice);
     cudaMemcpy(s->fac32, fac32.data(), fac32.size() * 4, cudaMemcpyHostToDevice);
+    if (b->pvb) {   // bra of the autocorrelation: B^dagger f per mode
+        std::vector<double> bra;
+        Basis tmp = *b;
+        tmp.Gc = b->Bc;
+        packet_factors(tmp, q0, p0, width, bra, s->lead_virtual);
+        if ((rc = dalloc(&s->fac_bra64, bra.size() * 8))) {
+            free_state(s);
+            return rc;
+        }
+        cudaMemcpy(s->fac_bra64, bra.data(), bra.size() * 8, cudaMemcpyHostToDevice);
+    }
     s->theta = theta;
     s->radius = radius;
     for (int k = 0; k < b->D_user; ++k) {
@@ -541,7 +622,8 @@ PQ_API pq_status pq_init_packet(const pq_basis* basis_, const double* q0, const 
     }
     cudaStream_t st = 0;
     if ((rc = init_bits_from_packet(*s, theta, st)) || (rc = check_capacity(*s, st)) ||
-        (rc = set_psi_from_packet(*s, st)) || (rc = observe_launch(*s, theta, st))) {
+        (rc = set_psi_from_packet(*s, st)) ||
+        (rc = s->pvb ? pvb_observe_current(*s, theta, st) : observe_launch(*s, theta, st))) {
         free_state(s);
         return rc;
     }
@@ -690,6 +772,7 @@ PQ_API pq_status pq_propagate(pq_state* state, const pq_prop_desc* desc, int nst
         return PQ_EINVAL;
     }
     s->theta = desc->theta;
+    if (s->pvb) return pvb_propagate(*s, *desc, nsteps, (cudaStream_t)stream);
     return propagate_impl(*s, *desc, nsteps, (cudaStream_t)stream);
 }
 

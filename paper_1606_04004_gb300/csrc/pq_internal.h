@@ -91,6 +91,9 @@ struct Basis {
     // phase-space modes: W (pW coefficients -> DVR coefficients), empty for DVR modes
     std::vector<std::vector<double>> W;
     bool generic = false;                          // some mode is a phase-space basis
+    // pvB modes: G, B = G^-dagger, S = B^dagger B (complex, interleaved), empty otherwise
+    std::vector<std::vector<double>> Gc, Bc, Sc;
+    bool pvb = false;                              // all modes are pvB
     // generic SoP: per term the factor kind and values per mode
     struct GTerm {
         double coef;
@@ -104,6 +107,9 @@ pq_status build_dvr_mode(const pq_mode_desc& m, std::vector<double>& x,
                          std::vector<double>& w, std::vector<double>& T);
 pq_status build_pw_mode(const pq_mode_desc& m, std::vector<double>& x, std::vector<double>& w,
                         std::vector<double>& T, std::vector<double>& W);
+pq_status build_pvb_mode(const pq_mode_desc& m, std::vector<double>& x, std::vector<double>& w,
+                         std::vector<double>& T, std::vector<double>& G, std::vector<double>& B,
+                         std::vector<double>& S);
 // Normalised packet factors f_k(i) = sqrt(w_i) g_k(x_i) / ||.||, complex interleaved.
 void packet_factors(const Basis& b, const double* q0, const double* p0, const double* width,
                     std::vector<double>& out /* D_int * kMaxN * 2 */, int lead_virtual);
@@ -192,6 +198,18 @@ struct State {
     struct GPlan { double coef; std::vector<GPass> passes; };   // passes: descending mode
     std::vector<GPlan> gplan;      // terms with two or more factors
     void* gtmp = nullptr;          // two scratch vectors (capacity each) for those terms
+    // pvB (Sec. 2.2): complex per-mode matrices [D][kMaxN][kMaxN][2], full-grid
+    // buffers (3 x lattice), 5 work vectors (capacity each), the packet's bra
+    // factors B^dagger f (the coefficients use G^dagger f)
+    bool pvb = false;
+    double* pvbB64 = nullptr; float* pvbB32 = nullptr;
+    double* pvbBh64 = nullptr; float* pvbBh32 = nullptr;
+    double* pvbS64 = nullptr; float* pvbS32 = nullptr;
+    double* pvbT64 = nullptr; float* pvbT32 = nullptr;
+    void* pvb_grid = nullptr;
+    void* pvb_vec = nullptr;
+    double* fac_bra64 = nullptr;
+    double pvb_smax = 1.0;
     double* fac64 = nullptr; float* fac32 = nullptr;   // packet factors [D][kMaxN] complex
     // host side
     double t = 0;
@@ -235,6 +253,11 @@ pq_status ensure_krylov(State& s, int K);
 pq_status sil_only(State& s, const pq_prop_desc& d, cudaStream_t st);
 pq_status observe_launch(State& s, double theta, cudaStream_t st);
 pq_status energy_of_current(State& s, double* E, cudaStream_t st);
+
+// pvb.cu
+pq_status pvb_apply(State& s, const void* in, void* out, int prec, cudaStream_t st);
+pq_status pvb_observe_current(State& s, double theta, cudaStream_t st);
+pq_status pvb_propagate(State& s, const pq_prop_desc& d, int nsteps, cudaStream_t st);
 
 // adjoint.cu
 pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,

@@ -52,9 +52,10 @@ def coupled_morse_terms(grids, De, a, qe, coupling):
 
 def modes_of(cfg):
     """Mode descriptors of a workload record (see ``workloads``)."""
-    from . import SINE_DVR, HO_DVR, PW
-    if cfg["basis"] == "pw":
-        return [dict(kind=PW, n=cfg["n"], xmin=cfg["xmin"], xmax=cfg["xmax"], mass=cfg["mass"],
+    from . import SINE_DVR, HO_DVR, PW, PVB
+    if cfg["basis"] in ("pw", "pvb"):
+        kind = PW if cfg["basis"] == "pw" else PVB
+        return [dict(kind=kind, n=cfg["n"], xmin=cfg["xmin"], xmax=cfg["xmax"], mass=cfg["mass"],
                      nx_lattice=cfg["nx_lattice"], np_lattice=cfg["np_lattice"])] * cfg["D"]
     if cfg["basis"] == "sine":
         return [dict(kind=SINE_DVR, n=cfg["n"], xmin=cfg["xmin"], xmax=cfg["xmax"],
@@ -70,7 +71,7 @@ def build_model(cfg, omegas=None, lam=None):
     from . import Basis
     b = Basis(modes_of(cfg))
     grids = [b.grid(k)[0] for k in range(b.D)]
-    if cfg["basis"] in ("sine", "pw"):
+    if cfg["basis"] in ("sine", "pw", "pvb"):
         terms = coupled_morse_terms(grids, cfg["morse_D"], cfg["morse_a"], cfg["morse_qe"],
                                     cfg["coupling"])
     else:

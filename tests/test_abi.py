@@ -65,8 +65,9 @@ def test_argument_errors():
     with pytest.raises(pq.PQError) as e:   # 64^6 > 2^32
         pq.Basis([dict(kind=pq.HO_DVR, n=64)] * 6)
     assert e.value.status == pq.EINVAL
-    with pytest.raises(pq.PQError) as e:
-        pq.Basis([dict(kind=pq.PVB, n=16, xmin=0.5, xmax=6.0, mass=1.0, nx_lattice=4, np_lattice=4)])
+    with pytest.raises(pq.PQError) as e:   # pvB mixed with another basis
+        pq.Basis([dict(kind=pq.PVB, n=16, xmin=0.5, xmax=6.0, mass=1.0, nx_lattice=4, np_lattice=4),
+                  dict(kind=pq.HO_DVR, n=8)])
     assert e.value.status == pq.ENOTSUP
     b = pq.Basis(pq.modes_of(W.scaled(W.HH4D, D=2)))
     with pytest.raises(pq.PQError) as e:   # kinetic times a diagonal factor

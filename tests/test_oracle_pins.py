@@ -430,3 +430,34 @@ def test_pw_theta0_matches_dvr_dynamics():
     for o1, o2 in zip(r1["obs"], r2["obs"]):
         assert abs(o1["C"] - o2["C"]) < 1e-10
         assert abs(o1["E"] - o2["E"]) < 1e-10 * abs(o2["E"])
+
+
+# ------------------------------------------------------------------- pvB
+
+def test_pvb_cg_solves_overlap():
+    from oracle import pvb
+    cfg = W.scaled(W.MORSE3D, D=2, basis="pvb")
+    prob = pvb.PVBProblem(cfg, n=16, nx=4, np_=4)
+    A = W.random_active_set(prob.dims, 0.4, 3)
+    y = W.random_psi(len(A), 4)
+    x = prob.solve_S(A, y)
+    # dense S_AA by brute force
+    SS = np.kron(prob.S, prob.S)[np.ix_(A, A)]
+    np.testing.assert_allclose(SS @ x, y, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(prob.S_AA(A, x), SS @ x, rtol=1e-12, atol=1e-12)
+
+
+def test_pvb_theta0_matches_dvr_dynamics():
+    # Sec. 3.1: with 100 % of the basis pvB gives the DVR (FGH) result: the
+    # autocorrelation and energy of a theta = 0 pvB run equal the DVR run's.
+    from oracle import pvb
+    cfg = W.scaled(W.MORSE3D, D=2, basis="pvb")
+    prob = pvb.PVBProblem(cfg, n=16, nx=4, np_=4)
+    dv = propagate.problem_from_config(W.scaled(W.MORSE2D, n=16))
+    q0, p0, wd = (2.2, 2.35), (0.0, 0.0), (0.2, 0.2)
+    r1 = pvb.run(prob, q0, p0, wd, 0.0, 12, 10.0, 5)
+    r2 = propagate.run(dv, q0, p0, wd, 0.0, 12, 10.0, 5)
+    for o1, o2 in zip(r1["obs"], r2["obs"]):
+        assert abs(o1["C"] - o2["C"]) < 1e-9, (o1["C"], o2["C"])
+        assert abs(o1["norm2"] - o2["norm2"]) < 1e-9
+        assert abs(o1["E"] - o2["E"]) < 1e-9 * abs(o2["E"])
