@@ -1027,6 +1027,343 @@ static pq_status launch_generic(const State& s, ApplyArgs<R> a, const void* in, 
     return PQ_OK;
 }
 
+// ------------------------------------------------------------------------
+// Element-parallel fibre kernels (n[k] <= 32, n[D-1] <= 32).  The tiles of a
+// pruned set are sparse, so per-warp fibre processing leaves most lanes idle
+// and serialises long chains of dependent loads.  Here a CTA takes a batch of
+// kEpBatch fibres (or planes) at a time: phase 1, one warp per fibre compacts
+// its active rows (ballot) and the element offsets of those rows; phase 2, all
+// threads of the CTA gather the batch's active coefficients, one thread per
+// coefficient, into a shared-memory tile; phase 3, one thread per active
+// output forms its dot products over the fibre's active rows (and, in the
+// inner pass, over the row's active points and the potential) and writes or
+// accumulates it.  Every phase is bulk-parallel, so the CTA keeps many loads
+// in flight instead of one dependent chain per warp.
+
+constexpr int kEpBatch = 8;          // fibres per batch (one per warp of 256 threads)
+
+// position of the n-th (0-based) set bit of b
+__device__ __forceinline__ int nth_set_bit(uint32_t b, int n) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const uint32_t lo = b & ((1u << w) - 1u);
+        const int c = __popc(lo);
+        if (n >= c) {
+            n -= c;
+            b >>= w;
+            pos += w;
+        } else {
+            b = lo;
+        }
+    }
+    return pos;
+}
+
+struct EpMeta {
+    int na[kEpBatch];
+    int eoff[kEpBatch + 1];
+    uint32_t rst[kEpBatch][32];
+    uint32_t rbt[kEpBatch][32];
+    int rj[kEpBatch][32];
+    int roff[kEpBatch][33];
+};
+
+// Locate batch element e: fibre f, compact row u, last-mode point s, position.
+__device__ __forceinline__ void ep_locate(const EpMeta& m, int e, int& f, int& u, int& s,
+                                          uint32_t& pos) {
+    f = 0;
+    while (f + 1 < kEpBatch && m.eoff[f + 1] <= e) ++f;
+    const int el = e - m.eoff[f];
+    int lo = 0, hi = m.na[f] - 1;   // largest u with roff[f][u] <= el
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (m.roff[f][mid] <= el) lo = mid;
+        else hi = mid - 1;
+    }
+    u = lo;
+    const int kth = el - m.roff[f][u];
+    s = nth_set_bit(m.rbt[f][u], kth);
+    pos = m.rst[f][u] + (uint32_t)kth;
+}
+
+// Phase 1 for warp f: compact the active rows (given per lane j < n) and
+// their element offsets.
+__device__ __forceinline__ void ep_compact(EpMeta& m, int f, int lane, int j, uint32_t b,
+                                           uint32_t st) {
+    const unsigned act = __ballot_sync(0xffffffffu, b != 0);
+    const int slot = __popc(act & ((1u << lane) - 1u));
+    const int cnt = b ? __popc(b) : 0;
+    int x = cnt;   // inclusive scan of element counts over lanes (slot order = lane order)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (b) {
+        m.rst[f][slot] = st;
+        m.rbt[f][slot] = b;
+        m.rj[f][slot] = j;
+        m.roff[f][slot] = x - cnt;
+    }
+    const int total = __shfl_sync(0xffffffffu, x, 31);
+    if (lane == 0) {
+        m.na[f] = __popc(act);
+        m.roff[f][__popc(act)] = total;
+    }
+}
+
+// Locate element el of fibre f: compact row u, last-mode point s, position.
+__device__ __forceinline__ void ep_locate_f(const EpMeta& m, int f, int el, int& u, int& s,
+                                            uint32_t& pos) {
+    int lo = 0, hi = m.na[f] - 1;   // largest u with roff[f][u] <= el
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (m.roff[f][mid] <= el) lo = mid;
+        else hi = mid - 1;
+    }
+    u = lo;
+    const int kth = el - m.roff[f][u];
+    s = nth_set_bit(m.rbt[f][u], kth);
+    pos = m.rst[f][u] + (uint32_t)kth;
+}
+
+// Element e of the warp's fibre, located from the lane's previous row:
+// lanes walk their elements in increasing order, so the row index only moves
+// forward (amortised O(1) instead of a binary search).
+__device__ __forceinline__ void ep_next(const EpMeta& m, int f, int e, int& u, int& s,
+                                        uint32_t& pos) {
+    while (m.roff[f][u + 1] <= e) ++u;
+    const int kth = e - m.roff[f][u];
+    s = nth_set_bit(m.rbt[f][u], kth);
+    pos = m.rst[f][u] + (uint32_t)kth;
+}
+
+constexpr int kEpChunk = 8;   // elements per lane kept in registers between phases
+
+// One warp per fibre; lanes work over the fibre's active coefficients.
+template <typename R>
+__global__ void __launch_bounds__(kApplyThreads) k_outer_ep(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lattice& L = a.L;
+    const int k = a.mode, nk = L.n[k], nl = L.nlast;
+    const uint32_t rs = L.rstride[k];
+    __shared__ EpMeta m;
+    V* tiles = reinterpret_cast<V*>(smem);                           // [kEpBatch][nk][nl]
+    R* Tk = reinterpret_cast<R*>(tiles + (size_t)kEpBatch * nk * nl);  // [nk][nk]
+    for (int i = threadIdx.x; i < nk * nk; i += blockDim.x)
+        Tk[i] = a.T[(size_t)k * kMaxN * kMaxN + (i / nk) * kMaxN + (i % nk)];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    V* tile = tiles + (size_t)w * nk * nl;
+    const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
+    const int64_t nunits = *a.nunits;
+    for (int64_t u = (int64_t)blockIdx.x * kEpBatch + w; u < nunits;
+         u += (int64_t)gridDim.x * kEpBatch) {
+        const uint32_t r0 = a.units[u];
+        const int i0 = (int)((r0 / rs) % (uint32_t)nk);
+        uint32_t b = 0, st = 0;
+        if (lane < nk && lane >= i0) {
+            const uint32_t r = r0 + (uint32_t)(lane - i0) * rs;
+            if (a.rowinfo) {
+                const uint2 ri = a.rowinfo[r];
+                st = ri.x;
+                b = ri.y;
+            } else {
+                b = (uint32_t)row_bits(a.bits, r, nl);
+                if (b) st = rank_of(a.bits, a.off, (uint64_t)r * nl);
+            }
+        }
+        ep_compact(m, w, lane, lane, b, st);
+        __syncwarp();
+        const int na = m.na[w], E = m.roff[w][na];
+        for (int i = lane; i < na * nl; i += 32) tile[i] = cmake<R>(0, 0);
+        __syncwarp();
+        int row = 0;
+        for (int e = lane; e < E; e += 32) {            // gather
+            int sc;
+            uint32_t pos;
+            ep_next(m, w, e, row, sc, pos);
+            V x = a.in[pos];
+            x.x *= scale;
+            x.y *= scale;
+            tile[row * nl + sc] = x;
+        }
+        __syncwarp();
+        row = 0;
+#pragma unroll 1
+        for (int e = lane; e < E; e += 32) {            // dot products, accumulate
+            int sc;
+            uint32_t pos;
+            ep_next(m, w, e, row, sc, pos);
+            V* o = a.out + pos;
+            V ov = *o;
+            const R* tj = Tk + m.rj[w][row] * nk;
+            R ax = 0, ay = 0;
+            for (int v = 0; v < na; ++v) {
+                const R t = tj[m.rj[w][v]];
+                const V cv = tile[v * nl + sc];
+                ax += t * cv.x;
+                ay += t * cv.y;
+            }
+            ov.x += ax;
+            ov.y += ay;
+            *o = ov;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename R>
+static size_t smem_outer_ep(int nk, int nl) {
+    return (size_t)kEpBatch * nk * nl * 2 * sizeof(R) + (size_t)nk * nk * sizeof(R);
+}
+
+// Inner pass, one warp per plane, lanes over the plane's active coefficients:
+// mode D-2 over the plane's active rows, mode D-1 over the row's active span,
+// the potential split as in k_apply_inner_reg (f(j) + g(s) + both-mode terms).
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::T inner_ep_value(
+    const ApplyArgs<R>& a, const EpMeta& m, int w, const typename Cx<R>::T* tile, const R* Tq,
+    const R* Tlt, const R* pref, const R* fj, const R* gs, int n2, int nl, int D, int g3, int nt,
+    int uu, int sc) {
+    using V = typename Cx<R>::T;
+    const int na = m.na[w];
+    const int j = m.rj[w][uu];
+    const R* tc = Tq + uu * n2;                         // compact T^(D-2) row of uu
+    R ax = 0, ay = 0;
+    for (int v = 0; v < na; ++v) {                      // mode D-2
+        const R t = tc[v];
+        const V c = tile[v * nl + sc];
+        ax += t * c.x;
+        ay += t * c.y;
+    }
+    const uint32_t rb = m.rbt[w][uu];                   // mode D-1 over the row's span
+    const int slo = __ffs(rb) - 1, shi = 31 - __clz(rb);
+    const V* row = tile + uu * nl;
+    for (int ss = slo; ss <= shi; ++ss) {
+        const R t = Tlt[ss * nl + sc];
+        const V c = row[ss];
+        ax += t * c.x;
+        ay += t * c.y;
+    }
+    R vv = fj[uu] + gs[sc];
+    for (int t = g3; t < nt; ++t)
+        vv += pref[t] * a.pot[((size_t)t * D + D - 2) * kMaxN + j] *
+              a.pot[((size_t)t * D + D - 1) * kMaxN + sc];
+    const V c = row[sc];
+    ax += vv * c.x;
+    ay += vv * c.y;
+    return cmake<R>(ax, ay);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kApplyThreads) k_inner_ep(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lattice& L = a.L;
+    const int D = L.D, n2 = L.n[D - 2], nl = L.nlast, nt = a.nterms;
+    const int g1 = a.ngroup[0], g2 = g1 + a.ngroup[1], g3 = g2 + a.ngroup[2];
+    __shared__ EpMeta m;
+    V* tiles = reinterpret_cast<V*>(smem);                             // [kEpBatch][n2][nl]
+    R* prefs = reinterpret_cast<R*>(tiles + (size_t)kEpBatch * n2 * nl); // [kEpBatch][kMaxTerms]
+    R* fjs = prefs + (size_t)kEpBatch * kMaxTerms;                       // [kEpBatch][32]
+    R* gss = fjs + (size_t)kEpBatch * 32;                                // [kEpBatch][32]
+    R* Tq = gss + (size_t)kEpBatch * 32;                                 // [n2][n2]
+    R* Tlt = Tq + n2 * n2;                                               // [nl][nl]: Tlt[ss][s] = T[s][ss]
+    R* Tcs = Tlt + nl * nl;                                              // [kEpBatch][n2][n2] compact T^(D-2)
+    for (int i = threadIdx.x; i < n2 * n2; i += blockDim.x)
+        Tq[i] = a.T[(size_t)(D - 2) * kMaxN * kMaxN + (i / n2) * kMaxN + (i % n2)];
+    for (int i = threadIdx.x; i < nl * nl; i += blockDim.x)
+        Tlt[i] = a.T[(size_t)(D - 1) * kMaxN * kMaxN + (i % nl) * kMaxN + (i / nl)];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    V* tile = tiles + (size_t)w * n2 * nl;
+    R* Tc = Tcs + (size_t)w * n2 * n2;
+    R* pref = prefs + (size_t)w * kMaxTerms;
+    R* fj = fjs + (size_t)w * 32;
+    R* gs = gss + (size_t)w * 32;
+    const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
+    const int64_t nunits = *a.nunits;
+    for (int64_t u = (int64_t)blockIdx.x * kEpBatch + w; u < nunits;
+         u += (int64_t)gridDim.x * kEpBatch) {
+        const uint32_t P = a.units[u];
+        uint32_t b = 0, st = 0;
+        if (lane < n2) {
+            const uint32_t r = P * (uint32_t)n2 + (uint32_t)lane;
+            if (a.rowinfo) {
+                const uint2 ri = a.rowinfo[r];
+                st = ri.x;
+                b = ri.y;
+            } else {
+                b = (uint32_t)row_bits(a.bits, r, nl);
+                if (b) st = rank_of(a.bits, a.off, (uint64_t)r * nl);
+            }
+        }
+        ep_compact(m, w, lane, lane, b, st);
+        for (int t = lane; t < nt; t += 32) {
+            R p = a.potc[t];
+            for (int kk = 0; kk < D - 2; ++kk) {
+                const int d = (int)((P / L.pstride[kk]) % (uint32_t)L.n[kk]);
+                p *= a.pot[((size_t)t * D + kk) * kMaxN + d];
+            }
+            pref[t] = p;
+        }
+        __syncwarp();
+        const int na = m.na[w], E = m.roff[w][na];
+        if (lane < na) {   // f(j) of compact row `lane`
+            const int j = m.rj[w][lane];
+            R f = 0;
+            for (int t = 0; t < g1; ++t) f += pref[t];
+            for (int t = g1; t < g2; ++t) f += pref[t] * a.pot[((size_t)t * D + D - 2) * kMaxN + j];
+            fj[lane] = f;
+        }
+        if (lane < nl) {   // g(s)
+            R g = 0;
+            for (int t = g2; t < g3; ++t) g += pref[t] * a.pot[((size_t)t * D + D - 1) * kMaxN + lane];
+            gs[lane] = g;
+        }
+        for (int i = lane; i < na * nl; i += 32) tile[i] = cmake<R>(0, 0);
+        if (lane < na) {   // compact operator: Tc[uu][v] = T^(D-2)[j_uu][j_v], lane = v
+            const int jv = m.rj[w][lane];
+            for (int uu = 0; uu < na; ++uu) Tc[uu * n2 + lane] = Tq[m.rj[w][uu] * n2 + jv];
+        }
+        __syncwarp();
+        int row = 0;
+        for (int e = lane; e < E; e += 32) {            // gather
+            int sc;
+            uint32_t pos;
+            ep_next(m, w, e, row, sc, pos);
+            V x = a.in[pos];
+            x.x *= scale;
+            x.y *= scale;
+            tile[row * nl + sc] = x;
+        }
+        __syncwarp();
+        row = 0;
+#pragma unroll 1
+        for (int e = lane; e < E; e += 32) {            // outputs
+            int sc;
+            uint32_t pos;
+            ep_next(m, w, e, row, sc, pos);
+            a.out[pos] = inner_ep_value<R>(a, m, w, tile, Tc, Tlt, pref, fj, gs, n2, nl, D, g3, nt,
+                                           row, sc);
+        }
+        __syncwarp();
+    }
+}
+
+template <typename R>
+static size_t smem_inner_ep(int n2, int nl) {
+    return (size_t)kEpBatch * n2 * nl * 2 * sizeof(R) +
+           ((size_t)kEpBatch * (kMaxTerms + 64 + n2 * n2) + n2 * n2 + nl * nl) * sizeof(R);
+}
+
 static size_t smem_inner(const Lattice& L, int nterms, int wpb, size_t esz) {
     const int n2 = L.n[L.D - 2], nl = L.nlast;
     const size_t per_warp = (size_t)n2 * nl * 2 * esz + kMaxN * 8 + kMaxN * 4 + kMaxTerms * esz;
@@ -1123,7 +1460,19 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         a.nunits = s.cnt + CNT_PLANES;
         int wpb = kApplyThreads / 32;
         const int n2 = L.n[L.D - 2], nl = L.nlast;
-        if (n2 == nl && (nl == 16 || nl == 24 || nl == 32)) {
+        if (n2 <= 32 && nl <= 32 && smem_inner_ep<R>(n2, nl) <= kSmemBudget) {
+            static bool ep_attr[2] = {false, false};
+            if (!ep_attr[pi]) {
+                PQ_CUDA_TRY(cudaFuncSetAttribute(k_inner_ep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kSmemBudget));
+                ep_attr[pi] = true;
+            }
+            const size_t sm = smem_inner_ep<R>(n2, nl);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inner_ep<R>, kApplyThreads, sm);
+            k_inner_ep<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+            PQ_CHECK_LAUNCH();
+        } else if (n2 == nl && (nl == 16 || nl == 24 || nl == 32)) {
             pq_status rc = nl == 16 ? launch_inner_reg<R, 16, 16>(a, G, st)
                          : nl == 24 ? launch_inner_reg<R, 24, 24>(a, G, st)
                                     : launch_inner_reg<R, 32, 32>(a, G, st);
@@ -1153,6 +1502,21 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         a.nunits = s.cnt + CNT_LEAD0 + k;
         int wpb = kApplyThreads / 32;
         const int nk = L.n[k];
+        if (L.nlast <= 32 && nk <= 32 && smem_outer_ep<R>(nk, L.nlast) <= kSmemBudget) {
+            static bool ep_attr[2] = {false, false};
+            if (!ep_attr[pi]) {
+                // the batch metadata is static shared memory: leave room for it
+                PQ_CUDA_TRY(cudaFuncSetAttribute(k_outer_ep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kSmemBudget));
+                ep_attr[pi] = true;
+            }
+            const size_t sm = smem_outer_ep<R>(nk, L.nlast);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_outer_ep<R>, kApplyThreads, sm);
+            k_outer_ep<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+            PQ_CHECK_LAUNCH();
+            continue;
+        }
         if (L.nlast <= 32 && (nk == 16 || nk == 24 || nk == 32)) {
             pq_status rc = nk == 16 ? launch_outer_reg<R, 16>(a, G, st)
                          : nk == 24 ? launch_outer_reg<R, 24>(a, G, st)
