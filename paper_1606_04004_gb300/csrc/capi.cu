@@ -302,7 +302,7 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
         (rc = dalloc(&s->planes, s->rows_cap * 4)) ||
         (rc = dalloc(&s->leaders, s->rows_cap * 4 * (size_t)std::max(1, L.D - 1))) ||
         (rc = dalloc(&s->cnt, CNT_SIZE * 8)) || (rc = dalloc(&s->scan_tmp, 1024 * 4)) ||
-        (rc = dalloc(&s->red_tmp, (size_t)grid_size() * 4 * (2 * kMaxK + 8) * 8)) ||
+        (rc = dalloc(&s->red_tmp, (size_t)grid_size() * 8 * (2 * kMaxK + 8) * 8)) ||
         (rc = dalloc(&s->ks, sizeof(KrylovScalars)))) {
         free_state(s);
         return rc;

@@ -21,7 +21,7 @@ namespace pq {
 constexpr int kRedThreads = 256;
 constexpr int kMaxM = 16;   // Krylov vectors handled per dots / update launch
 
-static int red_blocks() { return grid_size() * 4; }
+static int red_blocks() { return grid_size() * 8; }
 
 // accumulator: FP64 for double inputs, double-float for float inputs
 template <typename R> struct Acc;
@@ -38,21 +38,25 @@ template <> struct Acc<float> {
     __device__ double value() const { return df_value(v); }
 };
 
-// Sum `width` per-thread doubles over the block; thread 0 writes them to
-// partials[blockIdx.x * width + j].
-__device__ void block_partials(double* vals, int width, double* partials) {
-    __shared__ double sh[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = 0; j < width; ++j) {
-        double v = warp_sum(vals[j]);
-        if (lane == 0) sh[wid] = v;
-        __syncthreads();
-        if (wid == 0) {
-            double x = lane < nw ? sh[lane] : 0.0;
-            x = warp_sum(x);
-            if (lane == 0) partials[(size_t)blockIdx.x * width + j] = x;
-        }
-        __syncthreads();
+// Sum WIDTH per-thread doubles over the block (blockDim.x == kRedThreads);
+// thread j < WIDTH writes sum j to partials[blockIdx.x * WIDTH + j].  Warp
+// sums first, then one thread per value adds the warps in order.
+template <int WIDTH>
+__device__ __forceinline__ void block_partials(const double (&vals)[WIDTH], double* partials) {
+    constexpr int kWarps = kRedThreads / 32;
+    __shared__ double sh[WIDTH][kWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < WIDTH; ++j) {
+        const double v = warp_sum(vals[j]);
+        if (lane == 0) sh[j][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < WIDTH) {
+        double x = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) x += sh[threadIdx.x][w];
+        partials[(size_t)blockIdx.x * WIDTH + threadIdx.x] = x;
     }
 }
 
@@ -88,8 +92,8 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(const typename Cx<R>::T* 
         const auto v = x[p];
         acc.add(v.x * v.x + v.y * v.y);
     }
-    double vals[1] = {acc.value()};
-    block_partials(vals, 1, partials);
+    const double vals[1] = {acc.value()};
+    block_partials<1>(vals, partials);
 }
 
 // beta_0 = ||psi||; sigma_0 = 1/beta_0; reset the step's scalars.
@@ -115,44 +119,53 @@ __global__ void k_start_step(const double* partials, int G, KrylovScalars* ks, i
 }
 
 // ---------------------------------------------------------------- dots
-// c_i = sigma_i <V_i, W> for i in [i0, i0 + m) and ||W||^2.
-template <typename R>
+// c_i = sigma_i <V_i, W> for i in [i0, i0 + M) and ||W||^2.  Each thread takes
+// two elements per iteration; their products are summed in R before entering
+// the accumulator (double-float for FP32 data, FP64 for FP64 data).
+template <typename R, int M>
 __global__ void __launch_bounds__(kRedThreads) k_dots(const void* psi, const void* Vb, size_t cap,
                                                        const typename Cx<R>::T* __restrict__ W,
-                                                       const int64_t* na, int i0, int m,
+                                                       const int64_t* na, int i0,
                                                        const KrylovScalars* ks, int k,
                                                        double* partials) {
     if (ks->keff <= k) return;
     const int64_t n = min(*na, (int64_t)cap);
-    Acc<R> ar[kMaxM], ai[kMaxM], an;
+    Acc<R> ar[M], ai[M], an;
 #pragma unroll
-    for (int i = 0; i < kMaxM; ++i) {
+    for (int i = 0; i < M; ++i) {
         ar[i].init();
         ai[i].init();
     }
     an.init();
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += 2 * stride) {
+        const int64_t q = p + stride;
+        const bool has2 = q < n;
         const auto w = W[p];
-        an.add(w.x * w.x + w.y * w.y);
+        const auto w2 = has2 ? W[q] : cmake<R>(0, 0);
+        typename Cx<R>::T v[M], v2[M];
 #pragma unroll
-        for (int i = 0; i < kMaxM; ++i) {
-            if (i < m) {
-                const auto v = kvec<R>(psi, Vb, cap, i0 + i)[p];
-                // conj(v) * w
-                ar[i].add(v.x * w.x + v.y * w.y);
-                ai[i].add(v.x * w.y - v.y * w.x);
-            }
+        for (int i = 0; i < M; ++i) {
+            const auto* vi = kvec<R>(psi, Vb, cap, i0 + i);
+            v[i] = vi[p];
+            v2[i] = has2 ? vi[q] : cmake<R>(0, 0);
+        }
+        an.add((w.x * w.x + w.y * w.y) + (w2.x * w2.x + w2.y * w2.y));
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            // conj(v) * w over both elements
+            ar[i].add((v[i].x * w.x + v[i].y * w.y) + (v2[i].x * w2.x + v2[i].y * w2.y));
+            ai[i].add((v[i].x * w.y - v[i].y * w.x) + (v2[i].x * w2.y - v2[i].y * w2.x));
         }
     }
-    double vals[2 * kMaxM + 1];
+    double vals[2 * M + 1];
 #pragma unroll
-    for (int i = 0; i < kMaxM; ++i) {
+    for (int i = 0; i < M; ++i) {
         vals[2 * i] = ar[i].value();
         vals[2 * i + 1] = ai[i].value();
     }
-    vals[2 * m] = an.value();
-    block_partials(vals, 2 * m + 1, partials);
+    vals[2 * M] = an.value();
+    block_partials<2 * M + 1>(vals, partials);
 }
 
 // Finalise the dots of step k: scale by sigma_i, store, record alpha_k.
@@ -179,48 +192,83 @@ __global__ void k_dots_done(const double* partials, int G, int i0, int m, Krylov
 }
 
 // ---------------------------------------------------------------- update
-// W <- W - sum_{i in [i0, i0+m)} c_i sigma_i V_i ; optional ||W||^2 partials.
-template <typename R>
+// W <- W - sum_{i in [i0, i0+M)} c_i sigma_i V_i ; optional ||W||^2 partials.
+template <typename R, int M>
 __global__ void __launch_bounds__(kRedThreads) k_update(const void* psi, const void* Vb, size_t cap,
                                                          typename Cx<R>::T* __restrict__ W,
-                                                         const int64_t* na, int i0, int m,
+                                                         const int64_t* na, int i0,
                                                          const KrylovScalars* ks, int k,
                                                          int want_norm, double* partials) {
     if (ks->keff <= k) return;
     const int64_t n = min(*na, (int64_t)cap);
-    R cr[kMaxM], ci[kMaxM];
+    R cr[M], ci[M];
 #pragma unroll
-    for (int i = 0; i < kMaxM; ++i) {
-        if (i < m) {
-            const double sg = ks->sigma[i0 + i];
-            cr[i] = (R)(ks->dots[2 * (i0 + i)] * sg);
-            ci[i] = (R)(ks->dots[2 * (i0 + i) + 1] * sg);
-        } else {
-            cr[i] = 0;
-            ci[i] = 0;
-        }
+    for (int i = 0; i < M; ++i) {
+        const double sg = ks->sigma[i0 + i];
+        cr[i] = (R)(ks->dots[2 * (i0 + i)] * sg);
+        ci[i] = (R)(ks->dots[2 * (i0 + i) + 1] * sg);
     }
     Acc<R> an;
     an.init();
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += 2 * stride) {
+        const int64_t q = p + stride;
+        const bool has2 = q < n;
         auto w = W[p];
+        auto w2 = has2 ? W[q] : cmake<R>(0, 0);
+        typename Cx<R>::T v[M], v2[M];
 #pragma unroll
-        for (int i = 0; i < kMaxM; ++i) {
-            if (i < m) {
-                const auto v = kvec<R>(psi, Vb, cap, i0 + i)[p];
-                // w -= c * v  (c complex)
-                w.x -= cr[i] * v.x - ci[i] * v.y;
-                w.y -= cr[i] * v.y + ci[i] * v.x;
-            }
+        for (int i = 0; i < M; ++i) {
+            const auto* vi = kvec<R>(psi, Vb, cap, i0 + i);
+            v[i] = vi[p];
+            v2[i] = has2 ? vi[q] : cmake<R>(0, 0);
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            // w -= c * v  (c complex)
+            w.x -= cr[i] * v[i].x - ci[i] * v[i].y;
+            w.y -= cr[i] * v[i].y + ci[i] * v[i].x;
+            w2.x -= cr[i] * v2[i].x - ci[i] * v2[i].y;
+            w2.y -= cr[i] * v2[i].y + ci[i] * v2[i].x;
         }
         W[p] = w;
-        if (want_norm) an.add(w.x * w.x + w.y * w.y);
+        if (has2) W[q] = w2;
+        else w2 = cmake<R>(0, 0);
+        if (want_norm) an.add((w.x * w.x + w.y * w.y) + (w2.x * w2.x + w2.y * w2.y));
     }
     if (want_norm) {
-        double vals[1] = {an.value()};
-        block_partials(vals, 1, partials);
+        const double vals[1] = {an.value()};
+        block_partials<1>(vals, partials);
     }
+}
+
+// Launch k_dots / k_update for a run-time count m in [1, kMaxM].
+template <typename R, int M = 1>
+static void launch_dots(int m, int G, cudaStream_t st, const void* psi, const void* Vb,
+                        size_t cap, const typename Cx<R>::T* W, const int64_t* na, int i0,
+                        const KrylovScalars* ks, int k, double* partials) {
+    if constexpr (M < kMaxM) {
+        if (m != M) {
+            launch_dots<R, M + 1>(m, G, st, psi, Vb, cap, W, na, i0, ks, k, partials);
+            return;
+        }
+    }
+    k_dots<R, M><<<G, kRedThreads, 0, st>>>(psi, Vb, cap, W, na, i0, ks, k, partials);
+}
+
+template <typename R, int M = 1>
+static void launch_update(int m, int G, cudaStream_t st, const void* psi, const void* Vb,
+                          size_t cap, typename Cx<R>::T* W, const int64_t* na, int i0,
+                          const KrylovScalars* ks, int k, int want_norm, double* partials) {
+    if constexpr (M < kMaxM) {
+        if (m != M) {
+            launch_update<R, M + 1>(m, G, st, psi, Vb, cap, W, na, i0, ks, k, want_norm,
+                                    partials);
+            return;
+        }
+    }
+    k_update<R, M><<<G, kRedThreads, 0, st>>>(psi, Vb, cap, W, na, i0, ks, k, want_norm,
+                                               partials);
 }
 
 // beta_k = ||W||; breakdown test; sigma_{k+1} = 1/beta_k.
@@ -248,105 +296,117 @@ __global__ void k_update_done(const double* partials, int G, KrylovScalars* ks, 
 }
 
 // ------------------------------------------------ small exponential
-// exp(-i T dt) e_1 of the keff x keff tridiagonal: cyclic Jacobi with the
-// round-robin (parallel) ordering, one warp, matrices in shared memory.  In
-// every round the m/2 disjoint rotations are applied at once (lane r updates
-// row r for A J and Z J, then column r for J^T A).
-// coef_j = beta_0 sigma_j [Z exp(-i Lambda dt) Z^T e_1]_j.
-__global__ void __launch_bounds__(32) k_tridiag_exp(KrylovScalars* ks, double dt) {
-    __shared__ double A[kMaxK][kMaxK + 1], Z[kMaxK][kMaxK + 1];
-    __shared__ double rc[kMaxK / 2], rs[kMaxK / 2];
-    __shared__ int rp[kMaxK / 2], rq[kMaxK / 2];
-    __shared__ double ph_re[kMaxK], ph_im[kMaxK];
+// exp(-i T dt) e_1 of the keff x keff Lanczos tridiagonal, one warp, lane r =
+// row r.  The spectrum is shifted to its centre (T' = T - mu, the phase
+// exp(-i mu dt) applied at the end) and scaled into [-1, 1] by its Gershgorin
+// bound g; then exp(-i x R) with R = g |dt| is the Chebyshev series
+// J_0(R) + 2 sum_k (-i)^k J_k(R) T_k(x) (Jacobi-Anger), summed with the
+// three-term recurrence on the vector.  The Bessel values come from Miller's
+// backward recurrence normalised by J_0 + 2 sum J_2k = 1.  R above kChebR is
+// split into equal sub-steps, at most kChebSub of them: a larger R (a blown-up
+// tridiagonal) sets the numerical-failure bit instead of looping on.  The loop
+// body is FMAs and shuffles: FP64 division and square root, slow on this
+// part, stay out of it.
+// coef_j = beta_0 sigma_j [exp(-i T dt) e_1]_j.
+constexpr double kChebR = 2000.0;
+constexpr int kChebN = 2304;   // > kChebR + 16 kChebR^(1/3) + 40
+constexpr int kChebSub = 64;
+
+__global__ void __launch_bounds__(32) k_tridiag_exp(KrylovScalars* ks, double dt, int64_t* err) {
+    __shared__ double J[kChebN + 2];
     const int n = ks->keff;
     const int r = threadIdx.x;
     if (n <= 0) return;
-    if (r < n) {
-        for (int c = 0; c < n; ++c) {
-            double v = 0.0;
-            if (c == r) v = ks->alpha[r];
-            else if (c == r + 1) v = ks->beta[r];
-            else if (c + 1 == r) v = ks->beta[c];
-            A[r][c] = v;
-            Z[r][c] = c == r ? 1.0 : 0.0;
+    const bool on = r < n;
+    const double al = on ? ks->alpha[r] : 0.0;
+    const double bu0 = (on && r + 1 < n) ? ks->beta[r] : 0.0;            // T[r][r+1]
+    const double bup = __shfl_up_sync(0xffffffffu, bu0, 1);   // every lane takes part
+    const double bl0 = r > 0 ? bup : 0.0;                        // T[r][r-1]
+    double amax = on ? al : -1e300, amin = on ? al : 1e300;
+    for (int o = 16; o > 0; o >>= 1) {
+        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        amin = fmin(amin, __shfl_xor_sync(0xffffffffu, amin, o));
+    }
+    const double mu = 0.5 * (amax + amin);
+    const double a0 = on ? al - mu : 0.0;
+    double g = fabs(a0) + fabs(bl0) + fabs(bu0);
+    for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+    const double Rtot = g * fabs(dt);
+    double vr = r == 0 ? 1.0 : 0.0, vi = 0.0;
+    if (!(Rtot <= kChebR * kChebSub)) {   // also NaN
+        if (r == 0) *err |= 2;
+        if (on) {
+            ks->coef[2 * r] = 0.0;
+            ks->coef[2 * r + 1] = 0.0;
+        }
+        return;
+    }
+    if (Rtot > 1e-300) {
+        const int nsub = (int)ceil(Rtot / kChebR);
+        const double R = Rtot / nsub;
+        // <= kChebN for R <= kChebR; the clamp only keeps absurd R in bounds
+        const int N = (int)fmin(ceil(R + 16.0 * cbrt(R) + 40.0), (double)kChebN);
+        // Bessel J_k(R), k = 0..N, unnormalised, by lane 0
+        if (r == 0) {
+            const double two_over_R = 2.0 / R;
+            J[N + 1] = 0.0;
+            J[N] = 1e-300;
+            for (int k = N; k > 0; --k) {
+                const double jm = (k * two_over_R) * J[k] - J[k + 1];
+                J[k - 1] = jm;
+                if (fabs(jm) > 1e200)
+                    for (int q = k - 1; q <= N; ++q) J[q] *= 1e-200;
+            }
+        }
+        __syncwarp();
+        double part = 0.0;
+        for (int k = 2 + 2 * r; k <= N; k += 64) part += J[k];
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        const double norm = 1.0 / (J[0] + 2.0 * part);
+        const double f = (dt >= 0 ? 1.0 : -1.0) / g;
+        const double a = a0 * f, bl = bl0 * f, bu = bu0 * f;
+        for (int sub = 0; sub < nsub; ++sub) {
+            // p0 = T_0 v, p1 = T_1 v, acc = sum c_k T_k v
+            double p0r = vr, p0i = vi;
+            double p1r, p1i;
+            {
+                const double ur = __shfl_up_sync(0xffffffffu, p0r, 1);
+                const double ui = __shfl_up_sync(0xffffffffu, p0i, 1);
+                const double dr = __shfl_down_sync(0xffffffffu, p0r, 1);
+                const double di = __shfl_down_sync(0xffffffffu, p0i, 1);
+                p1r = a * p0r + bl * ur + bu * dr;
+                p1i = a * p0i + bl * ui + bu * di;
+            }
+            const double c0 = J[0] * norm, c1 = 2.0 * J[1] * norm;
+            double ar = c0 * p0r + c1 * p1i;   // (-i) c1 (p1r + i p1i)
+            double ai = c0 * p0i - c1 * p1r;
+            for (int k = 2; k <= N; ++k) {
+                const double ur = __shfl_up_sync(0xffffffffu, p1r, 1);
+                const double ui = __shfl_up_sync(0xffffffffu, p1i, 1);
+                const double dr = __shfl_down_sync(0xffffffffu, p1r, 1);
+                const double di = __shfl_down_sync(0xffffffffu, p1i, 1);
+                const double p2r = 2.0 * (a * p1r + bl * ur + bu * dr) - p0r;
+                const double p2i = 2.0 * (a * p1i + bl * ui + bu * di) - p0i;
+                const double ck = 2.0 * J[k] * norm;
+                switch (k & 3) {   // (-i)^k
+                    case 0: ar += ck * p2r; ai += ck * p2i; break;
+                    case 1: ar += ck * p2i; ai -= ck * p2r; break;
+                    case 2: ar -= ck * p2r; ai -= ck * p2i; break;
+                    default: ar -= ck * p2i; ai += ck * p2r; break;
+                }
+                p0r = p1r; p0i = p1i;
+                p1r = p2r; p1i = p2i;
+            }
+            vr = ar;
+            vi = ai;
         }
     }
-    __syncwarp();
-    const int m = (n + 1) & ~1;   // even number of indices (index n is a dummy when n is odd)
-    for (int sweep = 0; sweep < 40 && n > 1; ++sweep) {
-        double off = 0.0, dg = 0.0;
-        if (r < n)
-            for (int c = 0; c < n; ++c) {
-                const double v = A[r][c] * A[r][c];
-                if (c == r) dg += v;
-                else off += v;
-            }
-        off = warp_sum(off);
-        dg = warp_sum(dg);
-        if (off <= 1e-32 * (dg + 1e-300)) break;
-        for (int t = 0; t + 1 < m; ++t) {
-            if (r < m / 2) {   // pair r of round t (circle method)
-                const int a = r == 0 ? 0 : ((r - 1 + t) % (m - 1)) + 1;
-                const int bpos = m - 1 - r;
-                const int b = bpos == 0 ? 0 : ((bpos - 1 + t) % (m - 1)) + 1;
-                const int p = min(a, b), q = max(a, b);
-                double c = 1.0, sn = 0.0;
-                if (q < n) {
-                    const double apq = A[p][q];
-                    if (apq != 0.0) {
-                        const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
-                        const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + tt * tt);
-                        sn = tt * c;
-                    }
-                }
-                rp[r] = p;
-                rq[r] = q;
-                rc[r] = c;
-                rs[r] = sn;
-            }
-            __syncwarp();
-            if (r < n)
-                for (int i = 0; i < m / 2; ++i) {
-                    const int p = rp[i], q = rq[i];
-                    if (q >= n) continue;
-                    const double c = rc[i], sn = rs[i];
-                    const double ap = A[r][p], aq = A[r][q];
-                    A[r][p] = c * ap - sn * aq;
-                    A[r][q] = sn * ap + c * aq;
-                    const double zp = Z[r][p], zq = Z[r][q];
-                    Z[r][p] = c * zp - sn * zq;
-                    Z[r][q] = sn * zp + c * zq;
-                }
-            __syncwarp();
-            if (r < n)
-                for (int i = 0; i < m / 2; ++i) {
-                    const int p = rp[i], q = rq[i];
-                    if (q >= n) continue;
-                    const double c = rc[i], sn = rs[i];
-                    const double ap = A[p][r], aq = A[q][r];
-                    A[p][r] = c * ap - sn * aq;
-                    A[q][r] = sn * ap + c * aq;
-                }
-            __syncwarp();
-        }
-    }
-    if (r < n) {
+    if (on) {
         double sn, cs;
-        sincos(A[r][r] * dt, &sn, &cs);
-        ph_re[r] = cs * Z[0][r];
-        ph_im[r] = -sn * Z[0][r];
-    }
-    __syncwarp();
-    if (r < n) {
-        double re = 0.0, im = 0.0;
-        for (int l = 0; l < n; ++l) {
-            re += Z[r][l] * ph_re[l];
-            im += Z[r][l] * ph_im[l];
-        }
-        const double f = ks->beta0 * ks->sigma[r];
-        ks->coef[2 * r] = re * f;
-        ks->coef[2 * r + 1] = im * f;
+        sincos(-mu * dt, &sn, &cs);   // exp(-i mu dt)
+        const double fb = ks->beta0 * ks->sigma[r];
+        ks->coef[2 * r] = (cs * vr - sn * vi) * fb;
+        ks->coef[2 * r + 1] = (cs * vi + sn * vr) * fb;
     }
 }
 
@@ -411,8 +471,8 @@ __global__ void __launch_bounds__(kRedThreads) k_observe(const uint32_t* __restr
             sig = significant32((float)v.x, (float)v.y, theta2, lo, hi);
         if (!sig) wasted += 1.0;
     }
-    double vals[4] = {cr.value(), ci.value(), nn.value(), wasted};
-    block_partials(vals, 4, partials);
+    const double vals[4] = {cr.value(), ci.value(), nn.value(), wasted};
+    block_partials<4>(vals, partials);
 }
 
 // rec = [t, C re, C im, norm2, E (filled later), n_active, n_wasted, keff]
@@ -498,8 +558,7 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
         else if (!d.reorth) i0 = k > 0 ? k - 1 : 0;
         for (int c0 = i0; c0 <= k; c0 += kMaxM) {
             const int m = min(kMaxM, k - c0 + 1);
-            k_dots<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, cap, W, s.cnt + CNT_NA, c0, m, s.ks,
-                                                 k, s.red_tmp);
+            launch_dots<R>(m, G, st, s.psi, s.V, cap, W, s.cnt + CNT_NA, c0, s.ks, k, s.red_tmp);
             PQ_CHECK_LAUNCH();
             k_dots_done<<<1, 256, 0, st>>>(s.red_tmp, G, c0, m, s.ks, k, prev_E, s.cnt + CNT_ERR);
             PQ_CHECK_LAUNCH();
@@ -508,14 +567,14 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
         for (int c0 = i0; c0 <= k; c0 += kMaxM) {
             const int m = min(kMaxM, k - c0 + 1);
             const bool last = c0 + m > k;
-            k_update<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, cap, W, s.cnt + CNT_NA, c0, m, s.ks,
-                                                   k, last ? 1 : 0, s.red_tmp);
+            launch_update<R>(m, G, st, s.psi, s.V, cap, W, s.cnt + CNT_NA, c0, s.ks, k,
+                             last ? 1 : 0, s.red_tmp);
             PQ_CHECK_LAUNCH();
         }
         k_update_done<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks, k, s.cnt + CNT_ERR);
         PQ_CHECK_LAUNCH();
     }
-    k_tridiag_exp<<<1, 32, 0, st>>>(s.ks, d.dt);
+    k_tridiag_exp<<<1, 32, 0, st>>>(s.ks, d.dt, s.cnt + CNT_ERR);
     PQ_CHECK_LAUNCH();
     k_combine<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, cap, s.cnt + CNT_NA, s.ks);
     PQ_CHECK_LAUNCH();
@@ -669,8 +728,8 @@ static pq_status energy_t(State& s, double* E, cudaStream_t st) {
         cudaFreeAsync(W, st);
         return rc;
     }
-    k_dots<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, s.cap, (const V*)W, s.cnt + CNT_NA, 0, 1,
-                                         s.ks, 0, s.red_tmp);
+    k_dots<R, 1><<<G, kRedThreads, 0, st>>>(s.psi, s.V, s.cap, (const V*)W, s.cnt + CNT_NA, 0,
+                                            s.ks, 0, s.red_tmp);
     PQ_CHECK_LAUNCH();
     double* dE = nullptr;
     PQ_CUDA_TRY(cudaMallocAsync((void**)&dE, sizeof(double), st));
