@@ -1139,8 +1139,6 @@ __device__ __forceinline__ void ep_next(const EpMeta& m, int f, int e, int& u, i
     pos = m.rst[f][u] + (uint32_t)kth;
 }
 
-constexpr int kEpChunk = 8;   // elements per lane kept in registers between phases
-
 // One warp per fibre; lanes work over the fibre's active coefficients.
 template <typename R>
 __global__ void __launch_bounds__(kApplyThreads) k_outer_ep(ApplyArgs<R> a) {
@@ -1364,6 +1362,376 @@ static size_t smem_inner_ep(int n2, int nl) {
            ((size_t)kEpBatch * (kMaxTerms + 64 + n2 * n2) + n2 * n2 + nl * nl) * sizeof(R);
 }
 
+// ------------------------------------------------------------------------
+// Quad-blocked fibre kernels (n[k] <= 32, n[D-1] <= 32), the fast path.
+// One warp per fibre (outer) or plane (inner).  The fibre's active rows are
+// compacted with a ballot; each lane then owns (row, quad) work items, a quad
+// being four consecutive last-mode points.  Gather: every quad of every active
+// row is staged in shared memory (zeros where inactive), the non-empty quads
+// going to a per-warp item list.  Compute: a lane forms the four outputs of
+// its quad together, so each operator element and each staged input is loaded
+// once per four outputs with 16-byte shared-memory loads; positions come from
+// the row's start and one popcount.  The rows of a fibre are contiguous ranges
+// of A, so the global loads and stores of a quad touch consecutive addresses.
+
+constexpr int kQWarps = kApplyThreads / 32;
+
+struct __align__(16) QuadMeta {   // per warp, per fibre
+    uint32_t rst[32];           // first position in A of compact row u
+    uint32_t rbt[32];           // last-mode pattern of compact row u
+    int rj[32];                 // fibre index of compact row u
+    uint16_t item[32 * 8];      // (u << 3) | q of the non-empty quads
+};
+
+template <typename R>
+__device__ __forceinline__ void ld_quad(const typename Cx<R>::T* p, typename Cx<R>::T (&x)[4]) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 lo = reinterpret_cast<const float4*>(p)[0];
+        const float4 hi = reinterpret_cast<const float4*>(p)[1];
+        x[0] = make_float2(lo.x, lo.y);
+        x[1] = make_float2(lo.z, lo.w);
+        x[2] = make_float2(hi.x, hi.y);
+        x[3] = make_float2(hi.z, hi.w);
+    } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) x[t] = p[t];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void st_quad(typename Cx<R>::T* p, const typename Cx<R>::T (&x)[4]) {
+    if constexpr (sizeof(R) == 4) {
+        reinterpret_cast<float4*>(p)[0] = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
+        reinterpret_cast<float4*>(p)[1] = make_float4(x[2].x, x[2].y, x[3].x, x[3].y);
+    } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) p[t] = x[t];
+    }
+}
+
+// four consecutive operator values (16-byte aligned for float, 32 for double)
+template <typename R>
+__device__ __forceinline__ void ld_real4(const R* p, R (&t)[4]) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        t[0] = v.x;
+        t[1] = v.y;
+        t[2] = v.z;
+        t[3] = v.w;
+    } else {
+        const double2 lo = reinterpret_cast<const double2*>(p)[0];
+        const double2 hi = reinterpret_cast<const double2*>(p)[1];
+        t[0] = lo.x;
+        t[1] = lo.y;
+        t[2] = hi.x;
+        t[3] = hi.y;
+    }
+}
+
+// Row table entry of lattice row r: first position in A and pattern.
+template <typename R>
+__device__ __forceinline__ void q_row(const ApplyArgs<R>& a, uint32_t r, int nl, uint32_t& b,
+                                      uint32_t& st) {
+    if (a.rowinfo) {
+        const uint2 ri = a.rowinfo[r];
+        st = ri.x;
+        b = ri.y;
+    } else {
+        b = (uint32_t)row_bits(a.bits, r, nl);
+        st = b ? rank_of(a.bits, a.off, (uint64_t)r * nl) : 0u;
+    }
+}
+
+// Compact the fibre's active rows (lane j holds row j's pattern b and start
+// st) into m; returns the number of active rows.
+__device__ __forceinline__ int q_compact(QuadMeta& m, int lane, uint32_t b, uint32_t st) {
+    const unsigned act = __ballot_sync(0xffffffffu, b != 0);
+    if (b) {
+        const int slot = __popc(act & ((1u << lane) - 1u));
+        m.rst[slot] = st;
+        m.rbt[slot] = b;
+        m.rj[slot] = lane;
+    }
+    return __popc(act);
+}
+
+// Stage all quads of the na active rows into tile (row stride nl4) and list
+// the non-empty ones in m.item; returns the number of items.  Lane owns row
+// offset gu and quad gq of each round of rpr rows.
+template <typename R>
+__device__ __forceinline__ int q_gather(const ApplyArgs<R>& a, QuadMeta& m, typename Cx<R>::T* tile,
+                                        int na, int nl4, int rpr, int gu, int gq, int lane,
+                                        R scale, uint64_t nact) {
+    using V = typename Cx<R>::T;
+    int nitems = 0;
+    for (int u0 = 0; u0 < na; u0 += rpr) {
+        const int uu = u0 + gu;
+        uint32_t bq = 0;
+        if (gu < rpr && uu < na) {
+            const uint32_t rb = m.rbt[uu];
+            bq = (rb >> (4 * gq)) & 0xFu;
+            uint32_t pos = m.rst[uu] + (uint32_t)__popc(rb & ((1u << (4 * gq)) - 1u));
+            V x[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                x[t] = cmake<R>(0, 0);
+                if ((bq >> t) & 1u) {
+                    if (pq_in_bounds(pos, nact, 23, a.cnt)) {
+                        x[t] = a.in[pos];
+                        x[t].x *= scale;
+                        x[t].y *= scale;
+                    }
+                    ++pos;
+                }
+            }
+            st_quad<R>(tile + uu * nl4 + 4 * gq, x);
+        }
+        const unsigned ne = __ballot_sync(0xffffffffu, bq != 0);
+        if (bq) m.item[nitems + __popc(ne & ((1u << lane) - 1u))] = (uint16_t)((uu << 3) | gq);
+        nitems += __popc(ne);
+    }
+    return nitems;
+}
+
+// acc[t] += sum_v trow[rj[v]] x[v][4q + t] over the compact rows.
+template <typename R>
+__device__ __forceinline__ void q_column(const R* trow, const int* rj, const typename Cx<R>::T* xcol,
+                                         int na, int nl4, R (&ax)[4], R (&ay)[4]) {
+    using V = typename Cx<R>::T;
+    for (int v = 0; v < na; ++v) {
+        const R tv = trow[rj[v]];
+        V x[4];
+        ld_quad<R>(xcol + v * nl4, x);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            ax[t] += tv * x[t].x;
+            ay[t] += tv * x[t].y;
+        }
+    }
+}
+
+// out[p] += v.  Each output receives one contribution per pass (its one
+// fibre), so the sum is the same as a load-add-store; the reduction at L2
+// leaves nothing for the warp to wait on.
+__device__ __forceinline__ void q_accumulate(float2* p, float2 v) { atomicAdd(p, v); }
+__device__ __forceinline__ void q_accumulate(double2* p, double2 v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kApplyThreads) k_outer_q(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ QuadMeta meta[kQWarps];
+    const Lattice& L = a.L;
+    const int k = a.mode, nk = L.n[k], nl = L.nlast;
+    const int nq = (nl + 3) >> 2, nl4 = nq * 4, nkp = nk | 1;
+    const uint32_t rs = L.rstride[k];
+    V* tiles = reinterpret_cast<V*>(smem);                            // [kQWarps][nk][nl4]
+    R* Tk = reinterpret_cast<R*>(tiles + (size_t)kQWarps * nk * nl4);   // [nk][nkp]
+    for (int i = threadIdx.x; i < nk * nk; i += blockDim.x) {
+        const int r = i / nk, c = i - r * nk;
+        Tk[r * nkp + c] = a.T[(size_t)k * kMaxN * kMaxN + r * kMaxN + c];
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    QuadMeta& m = meta[w];
+    V* tile = tiles + (size_t)w * nk * nl4;
+    const int rpr = 32 / nq, gu = lane / nq, gq = lane - gu * nq;
+    const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
+    const int64_t nunits = *a.nunits;
+#ifdef PQ_BOUNDS_CHECK
+    const uint64_t nact = (uint64_t)a.cnt[CNT_NA];
+#else
+    const uint64_t nact = 0;
+#endif
+    for (int64_t u = (int64_t)blockIdx.x * kQWarps + w; u < nunits;
+         u += (int64_t)gridDim.x * kQWarps) {
+        if (!pq_in_bounds((uint64_t)u, a.units_cap, 21, a.cnt)) break;
+        const uint32_t r0 = a.units[u];
+        if (!pq_in_bounds(r0, L.nrows, 22, a.cnt)) continue;
+        const int i0 = (int)((r0 / rs) % (uint32_t)nk);
+        uint32_t b = 0, st = 0;
+        if (lane < nk && lane >= i0) q_row<R>(a, r0 + (uint32_t)(lane - i0) * rs, nl, b, st);
+        const int na = q_compact(m, lane, b, st);
+        __syncwarp();
+        const int nitems = q_gather<R>(a, m, tile, na, nl4, rpr, gu, gq, lane, scale, nact);
+        __syncwarp();
+#pragma unroll 1
+        for (int e = lane; e < nitems; e += 32) {
+            const int it = m.item[e];
+            const int uu = it >> 3, q = it & 7;
+            const uint32_t rb = m.rbt[uu];
+            const uint32_t bq = (rb >> (4 * q)) & 0xFu;
+            R ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
+            q_column<R>(Tk + m.rj[uu] * nkp, m.rj, tile + 4 * q, na, nl4, ax, ay);
+            uint32_t p = m.rst[uu] + (uint32_t)__popc(rb & ((1u << (4 * q)) - 1u));
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if ((bq >> t) & 1u) {
+                    if (pq_in_bounds(p, nact, 25, a.cnt)) q_accumulate(a.out + p, cmake<R>(ax[t], ay[t]));
+                    ++p;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename R>
+static size_t smem_outer_q(int nk, int nl) {
+    const int nl4 = ((nl + 3) >> 2) * 4;
+    return (size_t)kQWarps * nk * nl4 * 2 * sizeof(R) + (size_t)nk * (nk | 1) * sizeof(R);
+}
+
+// Inner pass: modes D-2 (across the plane's active rows) and D-1 (along the
+// row's active span) plus the SoP potential, split by the tile modes a term
+// touches: f(j) (neither or D-2 only), g(s) (D-1 only), both-mode terms.
+template <typename R>
+__global__ void __launch_bounds__(kApplyThreads) k_inner_q(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ QuadMeta meta[kQWarps];
+    __shared__ R prefs[kQWarps][kMaxTerms];
+    __shared__ R fjs[kQWarps][32];
+    __shared__ __align__(16) R gss[kQWarps][32];
+    const Lattice& L = a.L;
+    const int D = L.D, n2 = L.n[D - 2], nl = L.nlast, nt = a.nterms;
+    const int nq = (nl + 3) >> 2, nl4 = nq * 4, n2p = n2 | 1;
+    const int g1 = a.ngroup[0], g2 = g1 + a.ngroup[1], g3 = g2 + a.ngroup[2];
+    V* tiles = reinterpret_cast<V*>(smem);                             // [kQWarps][n2][nl4]
+    R* Tlq = reinterpret_cast<R*>(tiles + (size_t)kQWarps * n2 * nl4);   // [nl][nl4]: T[s][s'] at [s'][s]
+    R* potl = Tlq + (size_t)nl * nl4;                                    // [nt - g3][nl4]
+    R* Tq = potl + (size_t)(nt - g3) * nl4;                              // [n2][n2p]
+    for (int i = threadIdx.x; i < nl * nl4; i += blockDim.x) {
+        const int sp = i / nl4, s = i - sp * nl4;
+        Tlq[i] = s < nl ? a.T[(size_t)(D - 1) * kMaxN * kMaxN + s * kMaxN + sp] : (R)0;
+    }
+    for (int i = threadIdx.x; i < (nt - g3) * nl4; i += blockDim.x) {
+        const int t = g3 + i / nl4, s = i % nl4;
+        potl[i] = s < nl ? a.pot[((size_t)t * D + D - 1) * kMaxN + s] : (R)0;
+    }
+    for (int i = threadIdx.x; i < n2 * n2; i += blockDim.x) {
+        const int r = i / n2, c = i - r * n2;
+        Tq[r * n2p + c] = a.T[(size_t)(D - 2) * kMaxN * kMaxN + r * kMaxN + c];
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    QuadMeta& m = meta[w];
+    V* tile = tiles + (size_t)w * n2 * nl4;
+    R* pref = prefs[w];
+    R* fj = fjs[w];
+    R* gs = gss[w];
+    const int rpr = 32 / nq, gu = lane / nq, gq = lane - gu * nq;
+    const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
+    const int64_t nunits = *a.nunits;
+#ifdef PQ_BOUNDS_CHECK
+    const uint64_t nact = (uint64_t)a.cnt[CNT_NA];
+#else
+    const uint64_t nact = 0;
+#endif
+    for (int64_t u = (int64_t)blockIdx.x * kQWarps + w; u < nunits;
+         u += (int64_t)gridDim.x * kQWarps) {
+        if (!pq_in_bounds((uint64_t)u, a.units_cap, 26, a.cnt)) break;
+        const uint32_t P = a.units[u];
+        if (!pq_in_bounds(P, L.nplanes, 27, a.cnt)) continue;
+        uint32_t b = 0, st = 0;
+        if (lane < n2) q_row<R>(a, P * (uint32_t)n2 + (uint32_t)lane, nl, b, st);
+        const int na = q_compact(m, lane, b, st);
+        for (int t = lane; t < nt; t += 32) {
+            R pv = a.potc[t];
+            for (int kk = 0; kk < D - 2; ++kk) {
+                const int d = (int)((P / L.pstride[kk]) % (uint32_t)L.n[kk]);
+                pv *= a.pot[((size_t)t * D + kk) * kMaxN + d];
+            }
+            pref[t] = pv;
+        }
+        __syncwarp();
+        if (lane < na) {   // f(j) of compact row `lane`
+            const int j = m.rj[lane];
+            R f = 0;
+            for (int t = 0; t < g1; ++t) f += pref[t];
+            for (int t = g1; t < g2; ++t) f += pref[t] * a.pot[((size_t)t * D + D - 2) * kMaxN + j];
+            fj[lane] = f;
+        }
+        {   // g(s), zero in the padding
+            R g = 0;
+            if (lane < nl)
+                for (int t = g2; t < g3; ++t)
+                    g += pref[t] * a.pot[((size_t)t * D + D - 1) * kMaxN + lane];
+            gs[lane] = g;
+        }
+        const int nitems = q_gather<R>(a, m, tile, na, nl4, rpr, gu, gq, lane, scale, nact);
+        __syncwarp();
+#pragma unroll 1
+        for (int e = lane; e < nitems; e += 32) {
+            const int it = m.item[e];
+            const int uu = it >> 3, q = it & 7;
+            const uint32_t rb = m.rbt[uu];
+            const uint32_t bq = (rb >> (4 * q)) & 0xFu;
+            const int ju = m.rj[uu];
+            R ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
+            q_column<R>(Tq + ju * n2p, m.rj, tile + 4 * q, na, nl4, ax, ay);   // mode D-2
+            const V* xrow = tile + uu * nl4;
+            {   // mode D-1 over the row's active span
+                const int slo = __ffs(rb) - 1, shi = 31 - __clz(rb);
+                for (int sp = slo; sp <= shi; ++sp) {
+                    const V x = xrow[sp];
+                    R tq[4];
+                    ld_real4<R>(Tlq + sp * nl4 + 4 * q, tq);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        ax[t] += tq[t] * x.x;
+                        ay[t] += tq[t] * x.y;
+                    }
+                }
+            }
+            {   // potential
+                R vv[4];
+                ld_real4<R>(gs + 4 * q, vv);
+                const R f = fj[uu];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) vv[t] += f;
+                for (int tt = g3; tt < nt; ++tt) {
+                    const R pj = pref[tt] * a.pot[((size_t)tt * D + D - 2) * kMaxN + ju];
+                    R pl[4];
+                    ld_real4<R>(potl + (tt - g3) * nl4 + 4 * q, pl);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) vv[t] += pj * pl[t];
+                }
+                V x[4];
+                ld_quad<R>(xrow + 4 * q, x);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    ax[t] += vv[t] * x[t].x;
+                    ay[t] += vv[t] * x[t].y;
+                }
+            }
+            uint32_t p = m.rst[uu] + (uint32_t)__popc(rb & ((1u << (4 * q)) - 1u));
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if ((bq >> t) & 1u) {
+                    if (pq_in_bounds(p, nact, 28, a.cnt)) a.out[p] = cmake<R>(ax[t], ay[t]);
+                    ++p;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename R>
+static size_t smem_inner_q(int n2, int nl, int nboth) {
+    const int nl4 = ((nl + 3) >> 2) * 4;
+    return (size_t)kQWarps * n2 * nl4 * 2 * sizeof(R) +
+           ((size_t)nl * nl4 + (size_t)nboth * nl4 + (size_t)n2 * (n2 | 1)) * sizeof(R);
+}
+
 static size_t smem_inner(const Lattice& L, int nterms, int wpb, size_t esz) {
     const int n2 = L.n[L.D - 2], nl = L.nlast;
     const size_t per_warp = (size_t)n2 * nl * 2 * esz + kMaxN * 8 + kMaxN * 4 + kMaxTerms * esz;
@@ -1460,7 +1828,21 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         a.nunits = s.cnt + CNT_PLANES;
         int wpb = kApplyThreads / 32;
         const int n2 = L.n[L.D - 2], nl = L.nlast;
-        if (n2 <= 32 && nl <= 32 && smem_inner_ep<R>(n2, nl) <= kSmemBudget) {
+        const int nboth = s.nterms - (s.ngroup[0] + s.ngroup[1] + s.ngroup[2]);
+        if (sizeof(R) == 4 && n2 <= 32 && nl <= 32 &&
+            smem_inner_q<R>(n2, nl, nboth) <= kSmemBudget) {
+            static bool q_attr[2] = {false, false};
+            if (!q_attr[pi]) {
+                PQ_CUDA_TRY(cudaFuncSetAttribute(k_inner_q<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kSmemBudget));
+                q_attr[pi] = true;
+            }
+            const size_t sm = smem_inner_q<R>(n2, nl, nboth);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inner_q<R>, kApplyThreads, sm);
+            k_inner_q<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+            PQ_CHECK_LAUNCH();
+        } else if (n2 <= 32 && nl <= 32 && smem_inner_ep<R>(n2, nl) <= kSmemBudget) {
             static bool ep_attr[2] = {false, false};
             if (!ep_attr[pi]) {
                 PQ_CUDA_TRY(cudaFuncSetAttribute(k_inner_ep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1502,6 +1884,21 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         a.nunits = s.cnt + CNT_LEAD0 + k;
         int wpb = kApplyThreads / 32;
         const int nk = L.n[k];
+        if (sizeof(R) == 4 && L.nlast <= 32 && nk <= 32 &&
+            smem_outer_q<R>(nk, L.nlast) <= kSmemBudget) {
+            static bool q_attr[2] = {false, false};
+            if (!q_attr[pi]) {
+                PQ_CUDA_TRY(cudaFuncSetAttribute(k_outer_q<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kSmemBudget));
+                q_attr[pi] = true;
+            }
+            const size_t sm = smem_outer_q<R>(nk, L.nlast);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_outer_q<R>, kApplyThreads, sm);
+            k_outer_q<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+            PQ_CHECK_LAUNCH();
+            continue;
+        }
         if (L.nlast <= 32 && nk <= 32 && smem_outer_ep<R>(nk, L.nlast) <= kSmemBudget) {
             static bool ep_attr[2] = {false, false};
             if (!ep_attr[pi]) {
