@@ -1363,68 +1363,74 @@ static size_t smem_inner_ep(int n2, int nl) {
 }
 
 // ------------------------------------------------------------------------
-// Quad-blocked fibre kernels (n[k] <= 32, n[D-1] <= 32), the fast path.
+// Item-blocked fibre kernels (n[k] <= 32, n[D-1] <= 32), the FP32 fast path.
 // One warp per fibre (outer) or plane (inner).  The fibre's active rows are
-// compacted with a ballot; each lane then owns (row, quad) work items, a quad
-// being four consecutive last-mode points.  Gather: every quad of every active
-// row is staged in shared memory (zeros where inactive), the non-empty quads
-// going to a per-warp item list.  Compute: a lane forms the four outputs of
-// its quad together, so each operator element and each staged input is loaded
-// once per four outputs with 16-byte shared-memory loads; positions come from
-// the row's start and one popcount.  The rows of a fibre are contiguous ranges
-// of A, so the global loads and stores of a quad touch consecutive addresses.
+// compacted with a ballot; each lane then owns (row, item) work units, an item
+// being W consecutive last-mode points.  Gather: every item of every active
+// row is staged in shared memory (zeros where inactive), the non-empty items
+// going to a per-warp list.  Compute: a lane forms the W outputs of its item
+// together, so each operator element and each staged input is loaded once per
+// W outputs with 16-byte shared-memory loads; positions come from the row's
+// start and one popcount.  The rows of a fibre are contiguous ranges
+// of A, so the global loads and stores of an item touch consecutive addresses.
 
 constexpr int kQWarps = kApplyThreads / 32;
+// Last-mode points per work item (build-time; 4, 6 or 8).  On the 6D 24^6 ellipsoid
+// (9.97e6 points) one H.psi took 749 us with 4, 717 us with 6 and 1082 us with 8.
+#ifndef PQ_QW
+#define PQ_QW 6
+#endif
+constexpr int kQW = PQ_QW;
 
 struct __align__(16) QuadMeta {   // per warp, per fibre
     uint32_t rst[32];           // first position in A of compact row u
     uint32_t rbt[32];           // last-mode pattern of compact row u
     int rj[32];                 // fibre index of compact row u
-    uint16_t item[32 * 8];      // (u << 3) | q of the non-empty quads
+    uint16_t item[32 * 8];      // (u << 3) | q of the non-empty items
 };
 
-template <typename R>
-__device__ __forceinline__ void ld_quad(const typename Cx<R>::T* p, typename Cx<R>::T (&x)[4]) {
+// W consecutive complex values (16-byte aligned: W even for float, any W for double)
+template <typename R, int W>
+__device__ __forceinline__ void ld_w(const typename Cx<R>::T* p, typename Cx<R>::T (&x)[W]) {
     if constexpr (sizeof(R) == 4) {
-        const float4 lo = reinterpret_cast<const float4*>(p)[0];
-        const float4 hi = reinterpret_cast<const float4*>(p)[1];
-        x[0] = make_float2(lo.x, lo.y);
-        x[1] = make_float2(lo.z, lo.w);
-        x[2] = make_float2(hi.x, hi.y);
-        x[3] = make_float2(hi.z, hi.w);
+#pragma unroll
+        for (int h = 0; h < W / 2; ++h) {
+            const float4 v = reinterpret_cast<const float4*>(p)[h];
+            x[2 * h] = make_float2(v.x, v.y);
+            x[2 * h + 1] = make_float2(v.z, v.w);
+        }
     } else {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) x[t] = p[t];
+        for (int t = 0; t < W; ++t) x[t] = p[t];
     }
 }
 
-template <typename R>
-__device__ __forceinline__ void st_quad(typename Cx<R>::T* p, const typename Cx<R>::T (&x)[4]) {
+template <typename R, int W>
+__device__ __forceinline__ void st_w(typename Cx<R>::T* p, const typename Cx<R>::T (&x)[W]) {
     if constexpr (sizeof(R) == 4) {
-        reinterpret_cast<float4*>(p)[0] = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
-        reinterpret_cast<float4*>(p)[1] = make_float4(x[2].x, x[2].y, x[3].x, x[3].y);
+#pragma unroll
+        for (int h = 0; h < W / 2; ++h)
+            reinterpret_cast<float4*>(p)[h] =
+                make_float4(x[2 * h].x, x[2 * h].y, x[2 * h + 1].x, x[2 * h + 1].y);
     } else {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) p[t] = x[t];
+        for (int t = 0; t < W; ++t) p[t] = x[t];
     }
 }
 
-// four consecutive operator values (16-byte aligned for float, 32 for double)
-template <typename R>
-__device__ __forceinline__ void ld_real4(const R* p, R (&t)[4]) {
+// W consecutive real values (8-byte aligned for float, W even)
+template <typename R, int W>
+__device__ __forceinline__ void ld_real_w(const R* p, R (&t)[W]) {
     if constexpr (sizeof(R) == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(p);
-        t[0] = v.x;
-        t[1] = v.y;
-        t[2] = v.z;
-        t[3] = v.w;
+#pragma unroll
+        for (int h = 0; h < W / 2; ++h) {
+            const float2 v = reinterpret_cast<const float2*>(p)[h];
+            t[2 * h] = v.x;
+            t[2 * h + 1] = v.y;
+        }
     } else {
-        const double2 lo = reinterpret_cast<const double2*>(p)[0];
-        const double2 hi = reinterpret_cast<const double2*>(p)[1];
-        t[0] = lo.x;
-        t[1] = lo.y;
-        t[2] = hi.x;
-        t[3] = hi.y;
+#pragma unroll
+        for (int h = 0; h < W; ++h) t[h] = p[h];
     }
 }
 
@@ -1455,25 +1461,27 @@ __device__ __forceinline__ int q_compact(QuadMeta& m, int lane, uint32_t b, uint
     return __popc(act);
 }
 
-// Stage all quads of the na active rows into tile (row stride nl4) and list
-// the non-empty ones in m.item; returns the number of items.  Lane owns row
-// offset gu and quad gq of each round of rpr rows.
-template <typename R>
+// Stage all W-point items of the na active rows into tile (row stride nlw,
+// zeros where inactive) and list the non-empty ones in m.item; returns the
+// number of items.  Lane owns row offset gu and item column gq of each round
+// of rpr rows.
+template <typename R, int W>
 __device__ __forceinline__ int q_gather(const ApplyArgs<R>& a, QuadMeta& m, typename Cx<R>::T* tile,
-                                        int na, int nl4, int rpr, int gu, int gq, int lane,
+                                        int na, int nlw, int rpr, int gu, int gq, int lane,
                                         R scale, uint64_t nact) {
     using V = typename Cx<R>::T;
+    constexpr uint32_t kMask = (1u << W) - 1u;
     int nitems = 0;
     for (int u0 = 0; u0 < na; u0 += rpr) {
         const int uu = u0 + gu;
         uint32_t bq = 0;
         if (gu < rpr && uu < na) {
             const uint32_t rb = m.rbt[uu];
-            bq = (rb >> (4 * gq)) & 0xFu;
-            uint32_t pos = m.rst[uu] + (uint32_t)__popc(rb & ((1u << (4 * gq)) - 1u));
-            V x[4];
+            bq = (rb >> (W * gq)) & kMask;
+            uint32_t pos = m.rst[uu] + (uint32_t)__popc(rb & ((1u << (W * gq)) - 1u));
+            V x[W];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
+            for (int t = 0; t < W; ++t) {
                 x[t] = cmake<R>(0, 0);
                 if ((bq >> t) & 1u) {
                     if (pq_in_bounds(pos, nact, 23, a.cnt)) {
@@ -1484,7 +1492,7 @@ __device__ __forceinline__ int q_gather(const ApplyArgs<R>& a, QuadMeta& m, type
                     ++pos;
                 }
             }
-            st_quad<R>(tile + uu * nl4 + 4 * gq, x);
+            st_w<R, W>(tile + uu * nlw + W * gq, x);
         }
         const unsigned ne = __ballot_sync(0xffffffffu, bq != 0);
         if (bq) m.item[nitems + __popc(ne & ((1u << lane) - 1u))] = (uint16_t)((uu << 3) | gq);
@@ -1493,17 +1501,17 @@ __device__ __forceinline__ int q_gather(const ApplyArgs<R>& a, QuadMeta& m, type
     return nitems;
 }
 
-// acc[t] += sum_v trow[rj[v]] x[v][4q + t] over the compact rows.
-template <typename R>
+// acc[t] += sum_v trow[rj[v]] x[v][W q + t] over the compact rows.
+template <typename R, int W>
 __device__ __forceinline__ void q_column(const R* trow, const int* rj, const typename Cx<R>::T* xcol,
-                                         int na, int nl4, R (&ax)[4], R (&ay)[4]) {
+                                         int na, int nlw, R (&ax)[W], R (&ay)[W]) {
     using V = typename Cx<R>::T;
     for (int v = 0; v < na; ++v) {
         const R tv = trow[rj[v]];
-        V x[4];
-        ld_quad<R>(xcol + v * nl4, x);
+        V x[W];
+        ld_w<R, W>(xcol + v * nlw, x);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < W; ++t) {
             ax[t] += tv * x[t].x;
             ay[t] += tv * x[t].y;
         }
@@ -1519,7 +1527,10 @@ __device__ __forceinline__ void q_accumulate(double2* p, double2 v) {
     atomicAdd(&p->y, v.y);
 }
 
-template <typename R>
+// Items per row for width W and last-mode length nl.
+__host__ __device__ constexpr int q_items_per_row(int nl, int W) { return (nl + W - 1) / W; }
+
+template <typename R, int W>
 __global__ void __launch_bounds__(kApplyThreads) k_outer_q(ApplyArgs<R> a) {
     using V = typename Cx<R>::T;
     if (a.skip && *a.skip <= a.skip_k) return;
@@ -1528,10 +1539,10 @@ __global__ void __launch_bounds__(kApplyThreads) k_outer_q(ApplyArgs<R> a) {
     __shared__ QuadMeta meta[kQWarps];
     const Lattice& L = a.L;
     const int k = a.mode, nk = L.n[k], nl = L.nlast;
-    const int nq = (nl + 3) >> 2, nl4 = nq * 4, nkp = nk | 1;
+    const int nq = q_items_per_row(nl, W), nlw = nq * W, nkp = nk | 1;
     const uint32_t rs = L.rstride[k];
-    V* tiles = reinterpret_cast<V*>(smem);                            // [kQWarps][nk][nl4]
-    R* Tk = reinterpret_cast<R*>(tiles + (size_t)kQWarps * nk * nl4);   // [nk][nkp]
+    V* tiles = reinterpret_cast<V*>(smem);                            // [kQWarps][nk][nlw]
+    R* Tk = reinterpret_cast<R*>(tiles + (size_t)kQWarps * nk * nlw);   // [nk][nkp]
     for (int i = threadIdx.x; i < nk * nk; i += blockDim.x) {
         const int r = i / nk, c = i - r * nk;
         Tk[r * nkp + c] = a.T[(size_t)k * kMaxN * kMaxN + r * kMaxN + c];
@@ -1539,7 +1550,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_outer_q(ApplyArgs<R> a) {
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     QuadMeta& m = meta[w];
-    V* tile = tiles + (size_t)w * nk * nl4;
+    V* tile = tiles + (size_t)w * nk * nlw;
     const int rpr = 32 / nq, gu = lane / nq, gq = lane - gu * nq;
     const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
     const int64_t nunits = *a.nunits;
@@ -1558,19 +1569,21 @@ __global__ void __launch_bounds__(kApplyThreads) k_outer_q(ApplyArgs<R> a) {
         if (lane < nk && lane >= i0) q_row<R>(a, r0 + (uint32_t)(lane - i0) * rs, nl, b, st);
         const int na = q_compact(m, lane, b, st);
         __syncwarp();
-        const int nitems = q_gather<R>(a, m, tile, na, nl4, rpr, gu, gq, lane, scale, nact);
+        const int nitems = q_gather<R, W>(a, m, tile, na, nlw, rpr, gu, gq, lane, scale, nact);
         __syncwarp();
 #pragma unroll 1
         for (int e = lane; e < nitems; e += 32) {
             const int it = m.item[e];
             const int uu = it >> 3, q = it & 7;
             const uint32_t rb = m.rbt[uu];
-            const uint32_t bq = (rb >> (4 * q)) & 0xFu;
-            R ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
-            q_column<R>(Tk + m.rj[uu] * nkp, m.rj, tile + 4 * q, na, nl4, ax, ay);
-            uint32_t p = m.rst[uu] + (uint32_t)__popc(rb & ((1u << (4 * q)) - 1u));
+            const uint32_t bq = (rb >> (W * q)) & ((1u << W) - 1u);
+            R ax[W], ay[W];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
+            for (int t = 0; t < W; ++t) ax[t] = ay[t] = 0;
+            q_column<R, W>(Tk + m.rj[uu] * nkp, m.rj, tile + W * q, na, nlw, ax, ay);
+            uint32_t p = m.rst[uu] + (uint32_t)__popc(rb & ((1u << (W * q)) - 1u));
+#pragma unroll
+            for (int t = 0; t < W; ++t) {
                 if ((bq >> t) & 1u) {
                     if (pq_in_bounds(p, nact, 25, a.cnt)) q_accumulate(a.out + p, cmake<R>(ax[t], ay[t]));
                     ++p;
@@ -1581,16 +1594,16 @@ __global__ void __launch_bounds__(kApplyThreads) k_outer_q(ApplyArgs<R> a) {
     }
 }
 
-template <typename R>
+template <typename R, int W>
 static size_t smem_outer_q(int nk, int nl) {
-    const int nl4 = ((nl + 3) >> 2) * 4;
-    return (size_t)kQWarps * nk * nl4 * 2 * sizeof(R) + (size_t)nk * (nk | 1) * sizeof(R);
+    const int nlw = q_items_per_row(nl, W) * W;
+    return (size_t)kQWarps * nk * nlw * 2 * sizeof(R) + (size_t)nk * (nk | 1) * sizeof(R);
 }
 
 // Inner pass: modes D-2 (across the plane's active rows) and D-1 (along the
 // row's active span) plus the SoP potential, split by the tile modes a term
 // touches: f(j) (neither or D-2 only), g(s) (D-1 only), both-mode terms.
-template <typename R>
+template <typename R, int W>
 __global__ void __launch_bounds__(kApplyThreads) k_inner_q(ApplyArgs<R> a) {
     using V = typename Cx<R>::T;
     if (a.skip && *a.skip <= a.skip_k) return;
@@ -1599,21 +1612,21 @@ __global__ void __launch_bounds__(kApplyThreads) k_inner_q(ApplyArgs<R> a) {
     __shared__ QuadMeta meta[kQWarps];
     __shared__ R prefs[kQWarps][kMaxTerms];
     __shared__ R fjs[kQWarps][32];
-    __shared__ __align__(16) R gss[kQWarps][32];
+    __shared__ __align__(16) R gss[kQWarps][40];   // nlw <= 36 for W = 6
     const Lattice& L = a.L;
     const int D = L.D, n2 = L.n[D - 2], nl = L.nlast, nt = a.nterms;
-    const int nq = (nl + 3) >> 2, nl4 = nq * 4, n2p = n2 | 1;
+    const int nq = q_items_per_row(nl, W), nlw = nq * W, n2p = n2 | 1;
     const int g1 = a.ngroup[0], g2 = g1 + a.ngroup[1], g3 = g2 + a.ngroup[2];
-    V* tiles = reinterpret_cast<V*>(smem);                             // [kQWarps][n2][nl4]
-    R* Tlq = reinterpret_cast<R*>(tiles + (size_t)kQWarps * n2 * nl4);   // [nl][nl4]: T[s][s'] at [s'][s]
-    R* potl = Tlq + (size_t)nl * nl4;                                    // [nt - g3][nl4]
-    R* Tq = potl + (size_t)(nt - g3) * nl4;                              // [n2][n2p]
-    for (int i = threadIdx.x; i < nl * nl4; i += blockDim.x) {
-        const int sp = i / nl4, s = i - sp * nl4;
+    V* tiles = reinterpret_cast<V*>(smem);                             // [kQWarps][n2][nlw]
+    R* Tlq = reinterpret_cast<R*>(tiles + (size_t)kQWarps * n2 * nlw);   // [nl][nlw]: T[s][s'] at [s'][s]
+    R* potl = Tlq + (size_t)nl * nlw;                                    // [nt - g3][nlw]
+    R* Tq = potl + (size_t)(nt - g3) * nlw;                              // [n2][n2p]
+    for (int i = threadIdx.x; i < nl * nlw; i += blockDim.x) {
+        const int sp = i / nlw, s = i - sp * nlw;
         Tlq[i] = s < nl ? a.T[(size_t)(D - 1) * kMaxN * kMaxN + s * kMaxN + sp] : (R)0;
     }
-    for (int i = threadIdx.x; i < (nt - g3) * nl4; i += blockDim.x) {
-        const int t = g3 + i / nl4, s = i % nl4;
+    for (int i = threadIdx.x; i < (nt - g3) * nlw; i += blockDim.x) {
+        const int t = g3 + i / nlw, s = i % nlw;
         potl[i] = s < nl ? a.pot[((size_t)t * D + D - 1) * kMaxN + s] : (R)0;
     }
     for (int i = threadIdx.x; i < n2 * n2; i += blockDim.x) {
@@ -1623,7 +1636,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_inner_q(ApplyArgs<R> a) {
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     QuadMeta& m = meta[w];
-    V* tile = tiles + (size_t)w * n2 * nl4;
+    V* tile = tiles + (size_t)w * n2 * nlw;
     R* pref = prefs[w];
     R* fj = fjs[w];
     R* gs = gss[w];
@@ -1665,56 +1678,59 @@ __global__ void __launch_bounds__(kApplyThreads) k_inner_q(ApplyArgs<R> a) {
                 for (int t = g2; t < g3; ++t)
                     g += pref[t] * a.pot[((size_t)t * D + D - 1) * kMaxN + lane];
             gs[lane] = g;
+            if (lane < 8) gs[32 + lane] = 0;
         }
-        const int nitems = q_gather<R>(a, m, tile, na, nl4, rpr, gu, gq, lane, scale, nact);
+        const int nitems = q_gather<R, W>(a, m, tile, na, nlw, rpr, gu, gq, lane, scale, nact);
         __syncwarp();
 #pragma unroll 1
         for (int e = lane; e < nitems; e += 32) {
             const int it = m.item[e];
             const int uu = it >> 3, q = it & 7;
             const uint32_t rb = m.rbt[uu];
-            const uint32_t bq = (rb >> (4 * q)) & 0xFu;
+            const uint32_t bq = (rb >> (W * q)) & ((1u << W) - 1u);
             const int ju = m.rj[uu];
-            R ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
-            q_column<R>(Tq + ju * n2p, m.rj, tile + 4 * q, na, nl4, ax, ay);   // mode D-2
-            const V* xrow = tile + uu * nl4;
+            R ax[W], ay[W];
+#pragma unroll
+            for (int t = 0; t < W; ++t) ax[t] = ay[t] = 0;
+            q_column<R, W>(Tq + ju * n2p, m.rj, tile + W * q, na, nlw, ax, ay);   // mode D-2
+            const V* xrow = tile + uu * nlw;
             {   // mode D-1 over the row's active span
                 const int slo = __ffs(rb) - 1, shi = 31 - __clz(rb);
                 for (int sp = slo; sp <= shi; ++sp) {
                     const V x = xrow[sp];
-                    R tq[4];
-                    ld_real4<R>(Tlq + sp * nl4 + 4 * q, tq);
+                    R tq[W];
+                    ld_real_w<R, W>(Tlq + sp * nlw + W * q, tq);
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
+                    for (int t = 0; t < W; ++t) {
                         ax[t] += tq[t] * x.x;
                         ay[t] += tq[t] * x.y;
                     }
                 }
             }
             {   // potential
-                R vv[4];
-                ld_real4<R>(gs + 4 * q, vv);
+                R vv[W];
+                ld_real_w<R, W>(gs + W * q, vv);
                 const R f = fj[uu];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) vv[t] += f;
+                for (int t = 0; t < W; ++t) vv[t] += f;
                 for (int tt = g3; tt < nt; ++tt) {
                     const R pj = pref[tt] * a.pot[((size_t)tt * D + D - 2) * kMaxN + ju];
-                    R pl[4];
-                    ld_real4<R>(potl + (tt - g3) * nl4 + 4 * q, pl);
+                    R pl[W];
+                    ld_real_w<R, W>(potl + (tt - g3) * nlw + W * q, pl);
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) vv[t] += pj * pl[t];
+                    for (int t = 0; t < W; ++t) vv[t] += pj * pl[t];
                 }
-                V x[4];
-                ld_quad<R>(xrow + 4 * q, x);
+                V x[W];
+                ld_w<R, W>(xrow + W * q, x);
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
+                for (int t = 0; t < W; ++t) {
                     ax[t] += vv[t] * x[t].x;
                     ay[t] += vv[t] * x[t].y;
                 }
             }
-            uint32_t p = m.rst[uu] + (uint32_t)__popc(rb & ((1u << (4 * q)) - 1u));
+            uint32_t p = m.rst[uu] + (uint32_t)__popc(rb & ((1u << (W * q)) - 1u));
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
+            for (int t = 0; t < W; ++t) {
                 if ((bq >> t) & 1u) {
                     if (pq_in_bounds(p, nact, 28, a.cnt)) a.out[p] = cmake<R>(ax[t], ay[t]);
                     ++p;
@@ -1725,11 +1741,11 @@ __global__ void __launch_bounds__(kApplyThreads) k_inner_q(ApplyArgs<R> a) {
     }
 }
 
-template <typename R>
+template <typename R, int W>
 static size_t smem_inner_q(int n2, int nl, int nboth) {
-    const int nl4 = ((nl + 3) >> 2) * 4;
-    return (size_t)kQWarps * n2 * nl4 * 2 * sizeof(R) +
-           ((size_t)nl * nl4 + (size_t)nboth * nl4 + (size_t)n2 * (n2 | 1)) * sizeof(R);
+    const int nlw = q_items_per_row(nl, W) * W;
+    return (size_t)kQWarps * n2 * nlw * 2 * sizeof(R) +
+           ((size_t)nl * nlw + (size_t)nboth * nlw + (size_t)n2 * (n2 | 1)) * sizeof(R);
 }
 
 static size_t smem_inner(const Lattice& L, int nterms, int wpb, size_t esz) {
@@ -1830,17 +1846,17 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         const int n2 = L.n[L.D - 2], nl = L.nlast;
         const int nboth = s.nterms - (s.ngroup[0] + s.ngroup[1] + s.ngroup[2]);
         if (sizeof(R) == 4 && n2 <= 32 && nl <= 32 &&
-            smem_inner_q<R>(n2, nl, nboth) <= kSmemBudget) {
+            smem_inner_q<R, kQW>(n2, nl, nboth) <= kSmemBudget) {
             static bool q_attr[2] = {false, false};
             if (!q_attr[pi]) {
-                PQ_CUDA_TRY(cudaFuncSetAttribute(k_inner_q<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                PQ_CUDA_TRY(cudaFuncSetAttribute(k_inner_q<R, kQW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kSmemBudget));
                 q_attr[pi] = true;
             }
-            const size_t sm = smem_inner_q<R>(n2, nl, nboth);
+            const size_t sm = smem_inner_q<R, kQW>(n2, nl, nboth);
             int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inner_q<R>, kApplyThreads, sm);
-            k_inner_q<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inner_q<R, kQW>, kApplyThreads, sm);
+            k_inner_q<R, kQW><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
             PQ_CHECK_LAUNCH();
         } else if (n2 <= 32 && nl <= 32 && smem_inner_ep<R>(n2, nl) <= kSmemBudget) {
             static bool ep_attr[2] = {false, false};
@@ -1885,17 +1901,17 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         int wpb = kApplyThreads / 32;
         const int nk = L.n[k];
         if (sizeof(R) == 4 && L.nlast <= 32 && nk <= 32 &&
-            smem_outer_q<R>(nk, L.nlast) <= kSmemBudget) {
+            smem_outer_q<R, kQW>(nk, L.nlast) <= kSmemBudget) {
             static bool q_attr[2] = {false, false};
             if (!q_attr[pi]) {
-                PQ_CUDA_TRY(cudaFuncSetAttribute(k_outer_q<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                PQ_CUDA_TRY(cudaFuncSetAttribute(k_outer_q<R, kQW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kSmemBudget));
                 q_attr[pi] = true;
             }
-            const size_t sm = smem_outer_q<R>(nk, L.nlast);
+            const size_t sm = smem_outer_q<R, kQW>(nk, L.nlast);
             int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_outer_q<R>, kApplyThreads, sm);
-            k_outer_q<R><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_outer_q<R, kQW>, kApplyThreads, sm);
+            k_outer_q<R, kQW><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
             PQ_CHECK_LAUNCH();
             continue;
         }
