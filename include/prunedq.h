@@ -60,6 +60,16 @@ typedef enum pq_precision {
     PQ_FP32MIX = 1    /* complex FP32 H.psi, FP64 Lanczos scalars, norms and sums */
 } pq_precision;
 
+/* Neighbour rules of the adaption (Sec. 3.1, "phase-space ball radius"), on
+ * the lattice axes: one per DVR mode, two (x and p) per phase-space mode.
+ * An interior point on k axes gets 2k, 2k^2 or 3^k - 1 neighbours; points
+ * outside the lattice are dropped.  PQ_RADIUS_2 is limited to 8 axes. */
+typedef enum pq_neighbour_rule {
+    PQ_RADIUS_1 = 1,      /* +-1 along one axis                                  */
+    PQ_RADIUS_SQRT2 = 2,  /* +-1 along one axis or along two axes at once        */
+    PQ_RADIUS_2 = 3       /* every offset in {-1, 0, +1}^k except 0              */
+} pq_neighbour_rule;
+
 /* One mode of the direct-product basis.
  *  kind   pq_basis_kind (this build: PQ_SINE_DVR, PQ_HO_DVR).
  *  n      number of DVR points (2..64).
@@ -130,8 +140,8 @@ pq_status pq_set_sop(pq_basis* basis, const pq_sop_term* terms, int nterms);
  *   psi(q) = prod_k (2 pi w_k^2)^(-1/4) exp(-(q_k-q0_k)^2/(4 w_k^2) + i p0_k (q_k-q0_k))
  * projected on the DVR (a_I = prod_k sqrt(w_{i_k}) psi_k(x_{i_k}), each mode
  * normalised, so ||a|| = 1 on the full lattice), followed by the initial
- * adaption of Sec. 2.5 with threshold `theta` and neighbour radius `radius`
- * (this build: 1).  q0, p0, width: D doubles each (host).  `capacity` is the
+ * adaption of Sec. 2.5 with threshold `theta` and neighbour rule `radius`
+ * (pq_neighbour_rule).  q0, p0, width: D doubles each (host).  `capacity` is the
  * largest active-set size the state can hold (0 = the full lattice); device
  * memory for the Krylov space is taken when pq_propagate first needs it.
  * The state keeps the normalised full-lattice packet (as its D factors) as
@@ -180,15 +190,20 @@ pq_status pq_apply_H_host(pq_state* state, const void* in, void* out, int precis
 /* Adaption of Sec. 2.5 on the state's current coefficients: S = {I in A :
  * |a_I| >= theta} (tested as fl(re*re) + fl(im*im) >= fl(theta*theta) in
  * FP64, FP32 values widened exactly), A' = S union (nearest neighbours of S
- * along each lattice axis, clipped at the edges); kept coefficients are
- * carried over, new ones are zero.  Asynchronous; a capacity overflow is
- * reported by the next synchronising call as PQ_ECAPACITY. */
-pq_status pq_prune(pq_state* state, double theta, int radius, void* stream);
+ * of the rule `radius`, pq_neighbour_rule, clipped at the edges); kept
+ * coefficients are carried over, new ones are zero.  Relative exclusion
+ * (Sec. 2.5: functions leave only when their number exceeds a threshold
+ * relative to the set): when at most rel_excl * |A| members of A fall outside
+ * A', all of A stays (rel_excl = 0: no such rule).  Asynchronous; a capacity
+ * overflow is reported by the next synchronising call as PQ_ECAPACITY.
+ * Errors: PQ_EINVAL (theta or rel_excl negative or not finite, unknown rule),
+ * PQ_ENOTSUP (PQ_RADIUS_2 on more than 8 lattice axes). */
+pq_status pq_prune(pq_state* state, double theta, int radius, double rel_excl, void* stream);
 
 /* Propagation (Sec. 3.1): per step, a short-iterative-Lanczos step of order K
  * with time step dt (each new Krylov vector orthogonalised against all
  * previous ones when reorth = 1, against the previous two when reorth = 0;
- * FP64 Lanczos scalars), then the adaption with (theta, radius), then the
+ * FP64 Lanczos scalars), then the adaption with (theta, radius, rel_excl), then the
  * observables of the new state: t, C(t) = <Psi(0)|Psi(t)>, ||psi||^2,
  * E = Re<psi|H psi>/||psi||^2, |A|, and the number of active points with
  * |a| < theta.  Observables accumulate in the state (pq_observables_get).
@@ -198,8 +213,9 @@ typedef struct pq_prop_desc {
     int K;           /* Krylov dimension (H.psi products per step), 1..32     */
     double dt;       /* time step                                            */
     double theta;    /* adaption threshold                                    */
-    int radius;      /* neighbour radius (1)                                  */
+    int radius;      /* neighbour rule of the adaption (pq_neighbour_rule)    */
     int reorth;      /* 1 = full re-orthogonalisation, 0 = three-term         */
+    double rel_excl; /* relative exclusion threshold of the adaption (0: none) */
 } pq_prop_desc;
 
 pq_status pq_propagate(pq_state* state, const pq_prop_desc* desc, int nsteps, void* stream);

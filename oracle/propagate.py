@@ -138,10 +138,11 @@ def observables(prob, A, psi, factors, theta, vd=None):
 
 
 def run(prob, q0, p0, width, theta, K, dt, nsteps, radius=1,
-        record_sets=False, state=None):
+        record_sets=False, state=None, rel_excl=0.0):
     """Propagate ``nsteps`` steps.  Returns a dict with per-step observables
     (index 0 = t = 0 after the initial prune), the final (A, a) and, when
-    asked, the active set after each step."""
+    asked, the active set after each step.  ``radius`` is the neighbour rule
+    and ``rel_excl`` the relative exclusion threshold of the adaption."""
     if state is None:
         A, a, f = initial_state(prob, q0, p0, width, theta, radius)
     else:
@@ -151,7 +152,7 @@ def run(prob, q0, p0, width, theta, K, dt, nsteps, radius=1,
     for _ in range(nsteps):
         vd = prob.vdiag(A)
         a = sil.sil_step(a, lambda v: prob.apply(A, v, vd), K, dt)
-        A, a = pruned.prune(A, a, prob.axes, theta, radius)
+        A, a = pruned.prune(A, a, prob.axes, theta, radius, rel_excl)
         obs.append(observables(prob, A, a, f, theta))
         if record_sets:
             sets.append(A.copy())

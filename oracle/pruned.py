@@ -6,6 +6,8 @@ int64 row-major linear indices (last mode fastest).
 """
 from __future__ import annotations
 
+import itertools
+
 import numpy as np
 
 
@@ -150,17 +152,26 @@ def apply_H_sop(A, a, dims, terms):
     return y
 
 
-def neighbour_offsets(axes, radius=1):
+# Neighbour rules of Sec. 3.1 ("phase-space ball radius" on the lattice axes).
+RADIUS_1 = 1        # +-1 along one axis: 2k neighbours on k axes
+RADIUS_SQRT2 = 2    # radius sqrt(2): also +-1 along two axes at once: 2k^2 neighbours
+RADIUS_2 = 3        # radius 2: +-1 or 0 along every axis at once: 3^k - 1 neighbours
+
+
+def neighbour_offsets(axes, radius=RADIUS_1):
     """The phase-space-ball neighbour rule of Sec. 3.1 on a lattice with the
-    given axes: radius 1 adds +-1 along each lattice axis (2 per axis)."""
-    if radius != 1:
-        raise NotImplementedError("only the radius-1 neighbour rule is built")
+    given axes, as offset vectors with entries in {-1, 0, +1}: radius 1 moves
+    along one axis, radius sqrt(2) along one or two axes, radius 2 along any
+    number of axes (all 3^k - 1 non-zero offsets)."""
+    k = len(axes)
+    if radius not in (RADIUS_1, RADIUS_SQRT2, RADIUS_2):
+        raise ValueError(f"unknown neighbour rule {radius}")
+    maxmoved = {RADIUS_1: 1, RADIUS_SQRT2: 2, RADIUS_2: k}[radius]
     out = []
-    for a in range(len(axes)):
-        for s in (-1, 1):
-            d = [0] * len(axes)
-            d[a] = s
-            out.append(tuple(d))
+    for off in itertools.product((-1, 0, 1), repeat=k):
+        moved = sum(1 for d in off if d)
+        if 1 <= moved <= maxmoved:
+            out.append(off)
     return out
 
 
@@ -195,10 +206,13 @@ def adapt_set(S, axes, radius=1):
     return np.unique(np.concatenate(cand))
 
 
-def prune(A, psi, axes, theta, radius=1):
+def prune(A, psi, axes, theta, radius=RADIUS_1, rel_excl=0.0):
     """Adaption of Sec. 2.5 (one threshold theta, nearest neighbours of
     Sec. 3.1).  S = {I in A : |a_I| >= theta};  A' = S union N(S), where N adds
-    the lattice neighbours (clipped at the lattice edges).  Coefficients of
+    the lattice neighbours (clipped at the lattice edges).  With the relative
+    exclusion threshold rel_excl (Sec. 2.5: functions are excluded only when
+    their number exceeds a fraction of the set), the members of A outside
+    A' stay when there are at most rel_excl * |A| of them.  Coefficients of
     members of A that stay are kept; newly added members start at zero.
 
     ``axes`` are the lattice axes (one per DVR mode, two -- x and p -- per
@@ -208,6 +222,11 @@ def prune(A, psi, axes, theta, radius=1):
     A = np.asarray(A, dtype=np.int64)
     psi = np.asarray(psi)
     Anew = adapt_set(A[significant(psi, theta)], axes, radius)
+    if rel_excl > 0.0:
+        _, inside = lookup(Anew, A)
+        n_out = int(np.count_nonzero(~inside))
+        if n_out <= rel_excl * len(A):
+            Anew = np.union1d(Anew, A)
     pos, found = lookup(A, Anew)
     out = np.zeros(len(Anew), dtype=psi.dtype if psi.dtype.kind == "c" else np.complex128)
     out[found] = psi[pos[found]]

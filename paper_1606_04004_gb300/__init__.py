@@ -28,6 +28,7 @@ _lib = C.CDLL(_LIB_PATH)
 OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, ENUMERIC, ETIMEOUT, EBREAKDOWN, ENOTSUP = range(9)
 SINE_DVR, HO_DVR, PVB, PW = range(4)
 FP64, FP32MIX = 0, 1
+RADIUS_1, RADIUS_SQRT2, RADIUS_2 = 1, 2, 3   # neighbour rules of the adaption
 FACTOR_IDENTITY, FACTOR_KINETIC, FACTOR_DIAG = range(3)
 _STATUS = {0: "PQ_OK", 1: "PQ_EINVAL", 2: "PQ_ENOMEM", 3: "PQ_ECUDA", 4: "PQ_ECAPACITY",
            5: "PQ_ENUMERIC", 6: "PQ_ETIMEOUT", 7: "PQ_EBREAKDOWN", 8: "PQ_ENOTSUP"}
@@ -56,7 +57,7 @@ class SopTerm(C.Structure):
 
 class PropDesc(C.Structure):
     _fields_ = [("K", C.c_int), ("dt", C.c_double), ("theta", C.c_double), ("radius", C.c_int),
-                ("reorth", C.c_int)]
+                ("reorth", C.c_int), ("rel_excl", C.c_double)]
 
 
 class Observables(C.Structure):
@@ -91,7 +92,7 @@ _SIGS = {
     "pq_state_psi_device": [_vp, C.POINTER(_vp)],
     "pq_apply_H": [_vp, _vp, _vp, C.c_int, _vp],
     "pq_apply_H_host": [_vp, _vp, _vp, C.c_int, _vp],
-    "pq_prune": [_vp, C.c_double, C.c_int, _vp],
+    "pq_prune": [_vp, C.c_double, C.c_int, C.c_double, _vp],
     "pq_propagate": [_vp, C.POINTER(PropDesc), C.c_int, _vp],
     "pq_observables_get": [_vp, C.POINTER(Observables)],
     "pq_set_timing": [_vp, C.c_int],
@@ -279,11 +280,13 @@ class State:
         _check(_lib.pq_apply_H_host(self._h, _dptr(xin), _dptr(out), int(prec), None))
         return out
 
-    def prune(self, theta, radius=1, stream=None):
-        _check(_lib.pq_prune(self._h, float(theta), int(radius), _vp(stream or 0)))
+    def prune(self, theta, radius=1, rel_excl=0.0, stream=None):
+        """Adaption (pq_prune); radius: RADIUS_1, RADIUS_SQRT2 or RADIUS_2."""
+        _check(_lib.pq_prune(self._h, float(theta), int(radius), float(rel_excl),
+                             _vp(stream or 0)))
 
-    def propagate(self, K, dt, theta, nsteps, reorth=1, radius=1, stream=None):
-        d = PropDesc(int(K), float(dt), float(theta), int(radius), int(reorth))
+    def propagate(self, K, dt, theta, nsteps, reorth=1, radius=1, rel_excl=0.0, stream=None):
+        d = PropDesc(int(K), float(dt), float(theta), int(radius), int(reorth), float(rel_excl))
         _check(_lib.pq_propagate(self._h, C.byref(d), int(nsteps), _vp(stream or 0)))
 
     def observables(self) -> dict:
@@ -310,7 +313,7 @@ class State:
         return dict(C=complex(out[0], out[1]), norm2=float(out[2]), n_wasted=int(round(out[3])))
 
     def survival_grad(self, K, dt, theta, nsteps, ckpt_every, params, reorth=1, radius=1,
-                      stream=None):
+                      rel_excl=0.0, stream=None):
         """P = |<Psi(0)|Psi(T)>|^2 and dP/dtheta (pq_survival_grad).  params:
         list of ("centre", mode) or ("potential", dH/dtheta SoP terms)."""
         keep = []
@@ -327,7 +330,7 @@ class State:
                 raise ValueError(kind)
         grad = np.zeros(max(1, len(params)))
         P = C.c_double()
-        d = PropDesc(int(K), float(dt), float(theta), int(radius), int(reorth))
+        d = PropDesc(int(K), float(dt), float(theta), int(radius), int(reorth), float(rel_excl))
         _check(_lib.pq_survival_grad(self._h, C.byref(d), int(nsteps), int(ckpt_every), parr,
                                      len(params), _dptr(grad), C.byref(P), _vp(stream or 0)))
         return P.value, grad[:len(params)]

@@ -185,9 +185,9 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
                   kMaxParams);
         return PQ_EINVAL;
     }
-    if (d.radius != 1) {
-        set_error("neighbour radius %d not provided (radius 1 only)", d.radius);
-        return PQ_ENOTSUP;
+    {
+        pq_status nrc = check_neighbour_rule(s.lat, d.radius);
+        if (nrc) return nrc;
     }
     // ---- parameter tables
     std::vector<double> tab, coef;
@@ -333,7 +333,7 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
     };
     if ((rc = record(0))) return rc;
     for (int n = 0; n < nsteps; ++n) {
-        if ((rc = sil_only(s, d, st)) || (rc = prune_launch(s, d.theta, d.radius, st)) ||
+        if ((rc = sil_only(s, d, st)) || (rc = prune_launch(s, d.theta, d.radius, d.rel_excl, st)) ||
             (rc = record(n + 1)))
             return rc;
     }

@@ -579,9 +579,9 @@ PQ_API pq_status pq_init_packet(const pq_basis* basis_, const double* q0, const 
         set_error("theta must be finite and >= 0");
         return PQ_EINVAL;
     }
-    if (radius != 1) {
-        set_error("neighbour radius %d not provided (radius 1 only)", radius);
-        return PQ_ENOTSUP;
+    if (radius != PQ_RADIUS_1 && radius != PQ_RADIUS_SQRT2 && radius != PQ_RADIUS_2) {
+        set_error("unknown neighbour rule %d (1: radius 1, 2: radius sqrt 2, 3: radius 2)", radius);
+        return PQ_EINVAL;
     }
     const Basis* b = reinterpret_cast<const Basis*>(basis_);
     if (b)
@@ -753,14 +753,15 @@ PQ_API pq_status pq_apply_H_host(pq_state* state, const void* in, void* out, int
     return PQ_OK;
 }
 
-PQ_API pq_status pq_prune(pq_state* state, double theta, int radius, void* stream) {
+PQ_API pq_status pq_prune(pq_state* state, double theta, int radius, double rel_excl,
+                          void* stream) {
     clear_error();
     State* s = reinterpret_cast<State*>(state);
     if (!s || !(theta >= 0) || !std::isfinite(theta)) {
         set_error("bad state or theta");
         return PQ_EINVAL;
     }
-    return prune_launch(*s, theta, radius, (cudaStream_t)stream);
+    return prune_launch(*s, theta, radius, rel_excl, (cudaStream_t)stream);
 }
 
 PQ_API pq_status pq_propagate(pq_state* state, const pq_prop_desc* desc, int nsteps,

@@ -611,11 +611,9 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
         set_error("need dt > 0, theta >= 0, nsteps >= 0");
         return PQ_EINVAL;
     }
-    if (d.radius != 1) {
-        set_error("neighbour radius %d not provided (radius 1 only)", d.radius);
-        return PQ_ENOTSUP;
-    }
-    pq_status erc = ensure_krylov(s, d.K);
+    pq_status erc = check_neighbour_rule(s.lat, d.radius);
+    if (erc) return erc;
+    erc = ensure_krylov(s, d.K);
     if (erc) return erc;
     if (nsteps == 0) return PQ_OK;
     double* recs = nullptr;
@@ -627,7 +625,7 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
         double* prevE = recs + (size_t)n * 8 + 4;
         rc = s.prec == PQ_FP64 ? sil_step<double>(s, d, prevE, st) : sil_step<float>(s, d, prevE, st);
         if (rc) break;
-        rc = prune_launch(s, d.theta, d.radius, st);
+        rc = prune_launch(s, d.theta, d.radius, d.rel_excl, st);
         if (rc) break;
         s.t += d.dt;
         rc = observe_rec(s, d.theta, recs + (size_t)(n + 1) * 8, st);

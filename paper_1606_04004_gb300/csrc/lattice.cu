@@ -6,6 +6,8 @@
 // fibre structure rebuilt whenever the basis changes).
 #include <stdio.h>
 
+#include <cmath>
+
 #include "device_util.cuh"
 
 namespace pq {
@@ -273,21 +275,60 @@ pq_status rebuild_from_bits(State& s, bool remap, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------- adaption
+// Neighbour rules of Sec. 3.1 on the lattice axes ("phase-space ball radius"):
+// PQ_RADIUS_1 moves +-1 along one axis (2k neighbours on k axes),
+// PQ_RADIUS_SQRT2 also along two axes at once (2k^2), PQ_RADIUS_2 along any
+// number of axes (3^k - 1).  Neighbours outside the lattice are dropped.
 __device__ __forceinline__ void mark_with_neighbours(uint64_t* bits, uint32_t key,
-                                                     const Lattice& L) {
+                                                     const Lattice& L, int rule) {
     bit_set(bits, key);
+    int dg[2 * kMaxD];
+    for (int a = 0; a < L.naxes; ++a) dg[a] = (int)((key / L.axis_stride[a]) % (uint32_t)L.axis_n[a]);
     for (int a = 0; a < L.naxes; ++a) {
         const uint32_t sa = L.axis_stride[a];
-        const int d = (int)((key / sa) % (uint32_t)L.axis_n[a]);
-        if (d > 0) bit_set(bits, key - sa);
-        if (d + 1 < L.axis_n[a]) bit_set(bits, key + sa);
+        if (dg[a] > 0) bit_set(bits, key - sa);
+        if (dg[a] + 1 < L.axis_n[a]) bit_set(bits, key + sa);
+    }
+    if (rule == PQ_RADIUS_SQRT2) {
+        for (int a = 0; a < L.naxes; ++a)
+            for (int b = a + 1; b < L.naxes; ++b)
+                for (int sa = -1; sa <= 1; sa += 2)
+                    for (int sb = -1; sb <= 1; sb += 2) {
+                        const int da = dg[a] + sa, db = dg[b] + sb;
+                        if (da < 0 || da >= L.axis_n[a] || db < 0 || db >= L.axis_n[b]) continue;
+                        bit_set(bits, key + (uint32_t)(sa * (int64_t)L.axis_stride[a] +
+                                                       sb * (int64_t)L.axis_stride[b]));
+                    }
+    } else if (rule == PQ_RADIUS_2) {
+        // offsets in {-1, 0, 1}^k, counted in base 3 (digit 0 -> -1, 1 -> 0, 2 -> +1)
+        int c[2 * kMaxD];
+        for (int a = 0; a < L.naxes; ++a) c[a] = 0;
+        while (true) {
+            int moved = 0;
+            bool ok = true;
+            int64_t delta = 0;
+            for (int a = 0; a < L.naxes; ++a) {
+                const int o = c[a] - 1;
+                if (o) {
+                    ++moved;
+                    const int d = dg[a] + o;
+                    ok = ok && d >= 0 && d < L.axis_n[a];
+                    delta += o * (int64_t)L.axis_stride[a];
+                }
+            }
+            if (ok && moved >= 2) bit_set(bits, (uint32_t)((int64_t)key + delta));
+            int a = 0;   // next offset
+            while (a < L.naxes && c[a] == 2) c[a++] = 0;
+            if (a == L.naxes) break;
+            ++c[a];
+        }
     }
 }
 
 template <typename R>
 __global__ void k_prune_mark(const uint32_t* __restrict__ keys, const int64_t* na, int64_t cap,
                              const typename Cx<R>::T* __restrict__ psi, double theta2,
-                             float lo, float hi, Lattice L, uint64_t* bits,
+                             float lo, float hi, Lattice L, int rule, uint64_t* bits,
                              const int64_t* cnt) {
     if (cnt[CNT_ERR] & 1) return;
     const int64_t n = min(*na, cap);
@@ -299,8 +340,33 @@ __global__ void k_prune_mark(const uint32_t* __restrict__ keys, const int64_t* n
             sig = significant64((double)v.x, (double)v.y, theta2);
         else
             sig = significant32((float)v.x, (float)v.y, theta2, lo, hi);
-        if (sig) mark_with_neighbours(bits, keys[p], L);
+        if (sig) mark_with_neighbours(bits, keys[p], L, rule);
     }
+}
+
+// Relative exclusion (Sec. 2.5): count the members of A that the new bitmap
+// drops, then, if there are at most rel_excl * |A| of them, put them back.
+__global__ void k_excl_count(const uint32_t* __restrict__ keys, const int64_t* na, int64_t cap,
+                             const uint64_t* __restrict__ bits, int64_t* cnt) {
+    if (cnt[CNT_ERR] & 1) return;
+    const int64_t n = min(*na, cap);
+    int64_t c = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        c += bit_test(bits, keys[p]) ? 0 : 1;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c)
+        atomicAdd(reinterpret_cast<unsigned long long*>(cnt + CNT_EXCL), (unsigned long long)c);
+}
+
+__global__ void k_excl_keep(const uint32_t* __restrict__ keys, const int64_t* na, int64_t cap,
+                            double rel_excl, uint64_t* bits, const int64_t* cnt) {
+    if (cnt[CNT_ERR] & 1) return;
+    const int64_t n = min(*na, cap);
+    if ((double)cnt[CNT_EXCL] > rel_excl * (double)n) return;   // exclusion goes ahead
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        bit_set(bits, keys[p]);
 }
 
 static void guard_band(double theta2, float* lo, float* hi) {
@@ -315,12 +381,27 @@ static void guard_band(double theta2, float* lo, float* hi) {
     }
 }
 
-pq_status prune_launch(State& s, double theta, int radius, cudaStream_t st) {
-    if (radius != 1) {
-        set_error("neighbour radius %d not provided (radius 1 only)", radius);
+pq_status check_neighbour_rule(const Lattice& L, int radius) {
+    if (radius != PQ_RADIUS_1 && radius != PQ_RADIUS_SQRT2 && radius != PQ_RADIUS_2) {
+        set_error("unknown neighbour rule %d (1: radius 1, 2: radius sqrt 2, 3: radius 2)", radius);
+        return PQ_EINVAL;
+    }
+    if (radius == PQ_RADIUS_2 && L.naxes > kMaxBoxAxes) {
+        set_error("neighbour radius 2 adds 3^k - 1 points: at most %d lattice axes (%d given)",
+                  kMaxBoxAxes, L.naxes);
         return PQ_ENOTSUP;
     }
+    return PQ_OK;
+}
+
+pq_status prune_launch(State& s, double theta, int radius, double rel_excl, cudaStream_t st) {
     const Lattice& L = s.lat;
+    pq_status rc = check_neighbour_rule(L, radius);
+    if (rc) return rc;
+    if (!(rel_excl >= 0) || !std::isfinite(rel_excl)) {
+        set_error("relative exclusion threshold must be finite and >= 0");
+        return PQ_EINVAL;
+    }
     PQ_CUDA_TRY(cudaMemsetAsync(s.bits_alt, 0, (size_t)L.nwords * 8, st));
     const double theta2 = theta * theta;
     float lo, hi;
@@ -328,13 +409,21 @@ pq_status prune_launch(State& s, double theta, int radius, cudaStream_t st) {
     const int G = grid_size() * 8;
     if (s.prec == PQ_FP64)
         k_prune_mark<double><<<G, 256, 0, st>>>(s.keys, s.cnt + CNT_NA, (int64_t)s.cap,
-                                                (const double2*)s.psi, theta2, lo, hi, L,
+                                                (const double2*)s.psi, theta2, lo, hi, L, radius,
                                                 s.bits_alt, s.cnt);
     else
         k_prune_mark<float><<<G, 256, 0, st>>>(s.keys, s.cnt + CNT_NA, (int64_t)s.cap,
-                                               (const float2*)s.psi, theta2, lo, hi, L,
+                                               (const float2*)s.psi, theta2, lo, hi, L, radius,
                                                s.bits_alt, s.cnt);
     PQ_CHECK_LAUNCH();
+    if (rel_excl > 0.0) {
+        PQ_CUDA_TRY(cudaMemsetAsync(s.cnt + CNT_EXCL, 0, sizeof(int64_t), st));
+        k_excl_count<<<G, 256, 0, st>>>(s.keys, s.cnt + CNT_NA, (int64_t)s.cap, s.bits_alt, s.cnt);
+        PQ_CHECK_LAUNCH();
+        k_excl_keep<<<G, 256, 0, st>>>(s.keys, s.cnt + CNT_NA, (int64_t)s.cap, rel_excl,
+                                       s.bits_alt, s.cnt);
+        PQ_CHECK_LAUNCH();
+    }
     return rebuild_from_bits(s, true, st);
 }
 
@@ -342,7 +431,7 @@ pq_status prune_launch(State& s, double theta, int radius, cudaStream_t st) {
 // Initial adaption over the full lattice: a0_I = prod_k f_k(i_k) (complex
 // FP64, multiplied in mode order), S = {|a0_I| >= theta}, A = S + neighbours.
 __global__ void k_init_mark(Lattice L, const double2* __restrict__ fac, double theta2,
-                            uint64_t* bits) {
+                            int rule, uint64_t* bits) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)L.nfull;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t key = (uint32_t)i;
@@ -355,7 +444,7 @@ __global__ void k_init_mark(Lattice L, const double2* __restrict__ fac, double t
             re = nr;
             im = ni;
         }
-        if (significant64(re, im, theta2)) mark_with_neighbours(bits, key, L);
+        if (significant64(re, im, theta2)) mark_with_neighbours(bits, key, L, rule);
     }
 }
 
@@ -386,8 +475,10 @@ __global__ void k_packet_on_set(const uint32_t* __restrict__ keys, const int64_t
 pq_status init_bits_from_packet(State& s, double theta, cudaStream_t st) {
     const Lattice& L = s.lat;
     PQ_CUDA_TRY(cudaMemsetAsync(s.bits_alt, 0, (size_t)L.nwords * 8, st));
+    pq_status rc = check_neighbour_rule(L, s.radius);
+    if (rc) return rc;
     k_init_mark<<<grid_size() * 16, 256, 0, st>>>(L, (const double2*)s.fac64, theta * theta,
-                                                  s.bits_alt);
+                                                  s.radius, s.bits_alt);
     PQ_CHECK_LAUNCH();
     return rebuild_from_bits(s, false, st);
 }

@@ -138,6 +138,7 @@ enum Counter : int {
     CNT_PLANES = 2,    // active planes
     CNT_ERR = 3,       // error bits (1: capacity overflow, 2: numeric)
     CNT_NA_OLD = 4,    // active points before the last rebuild
+    CNT_EXCL = 5,      // adaption: members of A outside S + N(S)
     CNT_LEAD0 = 8,     // fibre leaders of outer mode k at CNT_LEAD0 + k
     CNT_FAULT = 24,    // bounds-check build: site, index, bound of the first bad access
     CNT_SIZE = 32
@@ -228,7 +229,11 @@ struct State {
 // lattice.cu
 pq_status lattice_setup(State& s);
 pq_status rebuild_from_bits(State& s, bool remap, cudaStream_t st);
-pq_status prune_launch(State& s, double theta, int radius, cudaStream_t st);
+// Neighbour rules (pq_neighbour_rule) and the relative exclusion threshold
+// of the adaption; radius 2 (the full box) needs at most kMaxBoxAxes axes.
+constexpr int kMaxBoxAxes = 8;
+pq_status check_neighbour_rule(const Lattice& L, int radius);
+pq_status prune_launch(State& s, double theta, int radius, double rel_excl, cudaStream_t st);
 pq_status init_bits_from_packet(State& s, double theta, cudaStream_t st);
 pq_status set_psi_from_packet(State& s, cudaStream_t st);
 // Replace the active set by n sorted keys on the device; with remap the

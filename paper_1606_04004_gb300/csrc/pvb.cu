@@ -461,7 +461,7 @@ pq_status pvb_propagate(State& s, const pq_prop_desc& d, int nsteps, cudaStream_
             Pvb<float> P(s, st);
             if ((rc = P.count()) || (rc = P.sil(d.K, d.dt, tol))) return rc;
         }
-        if ((rc = prune_launch(s, d.theta, d.radius, st))) return rc;
+        if ((rc = prune_launch(s, d.theta, d.radius, d.rel_excl, st))) return rc;
         s.t += d.dt;
         if ((rc = pvb_observe_current(s, d.theta, st))) return rc;
     }

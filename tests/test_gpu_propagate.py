@@ -108,3 +108,25 @@ def test_energy_and_norm_conserved_unpruned():
     s, o = _gpu(cfg, 30, pq.FP64, theta=0.0)
     assert np.max(np.abs(o["norm2"] - o["norm2"][0])) < 1e-12
     assert np.max(np.abs(o["energy"] - o["energy"][0])) < 1e-11 * abs(o["energy"][0])
+
+
+@pytest.mark.parametrize("rule,rho", [(2, 0.0), (3, 0.0), (1, 0.05)])
+def test_morse2d_fp64_neighbour_rules(rule, rho):
+    # the adaption variants of Sec. 3.1 / Sec. 2.5 inside the propagation:
+    # identical active sets every step, C(t) within 1e-10
+    from oracle import propagate
+    pq = lib()
+    cfg = W.MORSE2D
+    n = 40
+    prob = propagate.problem_from_config(cfg)
+    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], cfg["K"],
+                      cfg["dt"], n, radius=rule, rel_excl=rho)
+    b = pq.build_model(cfg)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP64,
+                 radius=rule)
+    s.propagate(cfg["K"], cfg["dt"], cfg["theta"], n, radius=rule, rel_excl=rho)
+    o = s.observables()
+    np.testing.assert_array_equal(o["n_active"], _series(r, "n_active"))
+    assert np.max(np.abs(o["C"] - _series(r, "C"))) < 1e-10
+    A, psi = s.read()
+    np.testing.assert_array_equal(A, r["A"])

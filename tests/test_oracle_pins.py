@@ -188,6 +188,76 @@ def test_prune_edges_and_empty():
     assert len(An) == 0 and len(pn) == 0
 
 
+def _brute_prune_ball(A, psi, axes, theta, radius, rel_excl=0.0):
+    """The neighbour rules of Sec. 3.1 written as distances on the lattice: a
+    point L is kept iff some significant active point P has
+    max_a |L_a - P_a| <= 1 and sum_a (L_a - P_a)^2 <= r^2, with r = 1,
+    sqrt(2) or 2 ("phase-space ball radius").  Relative exclusion (Sec. 2.5):
+    when at most rel_excl * |A| members of A would leave, none leave."""
+    r2 = {pruned.RADIUS_1: 1, pruned.RADIUS_SQRT2: 2, pruned.RADIUS_2: 4}[radius]
+    big = [np.array(np.unravel_index(int(i), axes)) for k, i in enumerate(A)
+           if abs(complex(psi[k])) ** 2 >= theta * theta]
+    keep = set()
+    for L in range(int(np.prod(axes))):
+        dig = np.array(np.unravel_index(L, axes))
+        for P in big:
+            d = np.abs(dig - P)
+            if d.max() <= 1 and int((d * d).sum()) <= r2:
+                keep.add(L)
+                break
+    leaving = [int(i) for i in A if int(i) not in keep]
+    if rel_excl > 0 and len(leaving) <= rel_excl * len(A):
+        keep |= {int(i) for i in A}
+    Aset = {int(i): k for k, i in enumerate(A)}
+    out = sorted(keep)
+    coef = [psi[Aset[L]] if L in Aset else 0 for L in out]
+    return np.array(out, dtype=np.int64), np.array(coef, dtype=complex)
+
+
+def test_neighbour_counts_match_the_paper():
+    # Sec. 3.1 counts for an interior point on k lattice axes: 2k neighbours
+    # for ball radius 1, 2k^2 for radius sqrt(2), 3^k - 1 for radius 2
+    # (catches a missing sign, a missing diagonal pair or a wrong box).
+    for k in range(1, 5):
+        axes = (5,) * k
+        centre = np.array([int(np.ravel_multi_index((2,) * k, axes))])
+        for rule, count in [(pruned.RADIUS_1, 2 * k), (pruned.RADIUS_SQRT2, 2 * k * k),
+                            (pruned.RADIUS_2, 3 ** k - 1)]:
+            assert len(pruned.adapt_set(centre, axes, rule)) == count + 1
+
+
+@pytest.mark.parametrize("rule", [2, 3])
+@pytest.mark.parametrize("axes,seed", [((7, 6), 0), ((4, 3, 5), 1), ((2, 3, 2, 3), 2)])
+def test_prune_ball_rules_bruteforce(axes, seed, rule):
+    rng = np.random.default_rng(seed + 40)
+    A = W.random_active_set(axes, 0.4, seed + 40)
+    theta = 0.45
+    psi = rng.uniform(0, 0.6, len(A)) * np.exp(2j * np.pi * rng.random(len(A)))
+    An, pn = pruned.prune(A, psi, axes, theta, rule)
+    Ab, pb = _brute_prune_ball(A, psi, axes, theta, rule)
+    np.testing.assert_array_equal(An, Ab)
+    np.testing.assert_array_equal(pn, pb)
+
+
+def test_prune_relative_exclusion_bruteforce():
+    # exclusion happens only when more than rel_excl * |A| members would
+    # leave; at exactly that many they stay (the paper's "larger than").
+    axes = (6, 5)
+    rng = np.random.default_rng(77)
+    A = W.random_active_set(axes, 0.6, 77)
+    psi = rng.uniform(0, 0.6, len(A)) * np.exp(2j * np.pi * rng.random(len(A)))
+    theta = 0.5
+    A0, _ = pruned.prune(A, psi, axes, theta)
+    n_out = len(np.setdiff1d(A, A0))
+    assert 0 < n_out < len(A)
+    for rho in (0.0, (n_out - 0.5) / len(A), n_out / len(A), 0.99):
+        An, pn = pruned.prune(A, psi, axes, theta, pruned.RADIUS_1, rho)
+        Ab, pb = _brute_prune_ball(A, psi, axes, theta, pruned.RADIUS_1, rho)
+        np.testing.assert_array_equal(An, Ab)
+        np.testing.assert_array_equal(pn, pb)
+        assert (len(np.setdiff1d(A, An)) == 0) == (n_out <= rho * len(A))
+
+
 # -------------------------------------------------------------------- SIL
 
 def test_sil_full_krylov_is_exact_exponential():
