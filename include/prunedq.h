@@ -52,7 +52,8 @@ typedef enum pq_basis_kind {
     PQ_SINE_DVR = 0,  /* sine DVR on a box (Sec. 2.2: admissible non-periodic DVR) */
     PQ_HO_DVR = 1,    /* harmonic-oscillator (Gauss-Hermite) DVR (Sec. 3.3)       */
     PQ_PVB = 2,       /* biorthogonal projected von Neumann basis (Sec. 2.2)      */
-    PQ_PW = 3         /* projected Weylets (Sec. 2.4)                             */
+    PQ_PW = 3,        /* projected Weylets (Sec. 2.4)                             */
+    PQ_FGH_DVR = 4    /* Fourier grid DVR on a periodic box (Sec. 2.2, Sec. 3.2)  */
 } pq_basis_kind;
 
 typedef enum pq_precision {
@@ -71,9 +72,12 @@ typedef enum pq_neighbour_rule {
 } pq_neighbour_rule;
 
 /* One mode of the direct-product basis.
- *  kind   pq_basis_kind (this build: PQ_SINE_DVR, PQ_HO_DVR).
- *  n      number of DVR points (2..64).
- *  xmin, xmax  box edges of the sine DVR (points at xmin + j L/(n+1), j=1..n).
+ *  kind   pq_basis_kind.
+ *  n      number of points (DVRs: 2..256, pvB and pW: 2..64).  Lattices
+ *         with a mode longer than 64 use a point-parallel H.psi meant for
+ *         small lattices (the 2D FGH double well).
+ *  xmin, xmax  box edges: sine DVR points at xmin + j L/(n+1), j=1..n; FGH
+ *         points at xmin + j L/n, j=0..n-1 on the periodic box [xmin, xmax).
  *  mass   mass in the kinetic energy -d^2/dx^2 / (2 mass).
  *  omega  frequency of the HO-DVR's underlying oscillator (with `mass`).
  *  nx_lattice, np_lattice  phase-space lattice of pvB / pW modes (unused for DVRs).

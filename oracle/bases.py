@@ -34,6 +34,33 @@ def sine_dvr(n: int, xmin: float, xmax: float, mass: float):
     return x, w, T
 
 
+def fgh_dvr(n: int, xmin: float, xmax: float, mass: float):
+    """Fourier grid Hamiltonian DVR on the periodic box [xmin, xmax) (Sec. 2.2:
+    the FGH DVR, whose functions cover the same phase-space area as a
+    periodic lattice; the double-well grids of Sec. 3.2).
+
+    Points x_j = xmin + j L/n, j = 0..n-1 (xmax is identified with xmin),
+    weight w = L/n.  The kinetic matrix is p^2/2m in the discrete Fourier
+    basis transformed to the grid: T = F^H diag(k_l^2 / 2m) F with the unitary
+    DFT F and momenta k_l = 2 pi l / L on the centred integer range
+    l = -(n-1)//2 .. n//2 (for even n the last one is the Nyquist mode).
+    Built here from numpy's FFT of the identity.
+
+    Returns (x, w, T) with w an array of equal weights.
+    """
+    L = xmax - xmin
+    j = np.arange(n)
+    x = xmin + j * L / n
+    F = np.fft.fft(np.eye(n), axis=0) / np.sqrt(n)   # F[l, j] = exp(-2 pi i l j / n) / sqrt(n)
+    l = np.fft.fftfreq(n, d=1.0 / n)                  # integer frequencies in FFT order
+    if n % 2 == 0:
+        l[n // 2] = n // 2                            # the Nyquist mode taken as +n/2
+    k = 2.0 * np.pi * l / L
+    T = (F.conj().T @ np.diag(k * k / (2.0 * mass)) @ F).real
+    w = np.full(n, L / n)
+    return x, w, T
+
+
 def ho_dvr(n: int, mass: float = 1.0, omega: float = 1.0):
     """Harmonic-oscillator (Gauss-Hermite) DVR.
 

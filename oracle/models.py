@@ -2,8 +2,8 @@
 coordinates (the oracle never uses a sum-of-products form for V: a DVR
 potential is diagonal, Sec. 2.1, so V_II = V(x_I) is all that is needed).
 
-None of these models is from the paper; they are the synthetic stand-ins the
-workloads define (coupled Morse in 2D/3D, Henon-Heiles chains in 4D/6D).
+The coupled Morse and Henon-Heiles models are synthetic stand-ins the
+workloads define; the double well is the paper's own model (Sec. 3.2).
 """
 from __future__ import annotations
 
@@ -34,6 +34,14 @@ def coupled_morse(q: np.ndarray, De: float, a: float, qe: float,
         for j in range(i + 1, D):
             v = v + coupling * q[..., i] * q[..., j]
     return v
+
+
+def double_well(q: np.ndarray, c1: float = 6.4, c2: float = 37.5, c3: float = 10.0) -> np.ndarray:
+    """The 2D double well of Sec. 3.2 (Eq. ex_dwell), q of shape (..., 2):
+    V = c1 (x-1)^2 (x-2)^2 + c2 (y-2)^2 + c3 x^2 y."""
+    q = np.asarray(q, dtype=np.float64)
+    x, y = q[..., 0], q[..., 1]
+    return c1 * (x - 1.0) ** 2 * (x - 2.0) ** 2 + c2 * (y - 2.0) ** 2 + c3 * x * x * y
 
 
 def gaussian_1d(x, q0: float, p0: float, width: float) -> np.ndarray:

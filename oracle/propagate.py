@@ -97,6 +97,13 @@ def problem_from_config(cfg, omegas=None, lam=None):
     D, n = cfg["D"], cfg["n"]
     if cfg["basis"] == "pw":
         return pw_problem_from_config(cfg)
+    if cfg["basis"] == "fgh":
+        xs, ws, Ts = [], [], []
+        for k in range(D):
+            x, w, T = bases.fgh_dvr(n[k], cfg["xmin"][k], cfg["xmax"][k], cfg["mass"])
+            xs.append(x); ws.append(w); Ts.append(T)
+        c = cfg["dw_coef"]
+        return DVRProblem(xs, ws, Ts, lambda q: models.double_well(q, *c))
     if cfg["basis"] == "sine":
         x, w, T = bases.sine_dvr(n, cfg["xmin"], cfg["xmax"], cfg["mass"])
         vf = lambda q: models.coupled_morse(q, cfg["morse_D"], cfg["morse_a"],

@@ -26,7 +26,7 @@ _lib = C.CDLL(_LIB_PATH)
 
 # ----------------------------------------------------------------- enums
 OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, ENUMERIC, ETIMEOUT, EBREAKDOWN, ENOTSUP = range(9)
-SINE_DVR, HO_DVR, PVB, PW = range(4)
+SINE_DVR, HO_DVR, PVB, PW, FGH_DVR = range(5)
 FP64, FP32MIX = 0, 1
 RADIUS_1, RADIUS_SQRT2, RADIUS_2 = 1, 2, 3   # neighbour rules of the adaption
 FACTOR_IDENTITY, FACTOR_KINETIC, FACTOR_DIAG = range(3)
@@ -344,5 +344,5 @@ class State:
         return dict(apply_ms=ms.value, n_apply=int(n.value), coef_applied=coef.value)
 
 
-from .hamiltonians import (build_model, henon_heiles_terms, coupled_morse_terms,  # noqa: E402
+from .hamiltonians import (build_model, henon_heiles_terms, coupled_morse_terms, double_well_terms,  # noqa: E402
                            modes_of, henon_heiles_param_derivs)

@@ -48,6 +48,7 @@ struct ApplyArgs {
     uint64_t units_cap;         // entries of the units array (bounds-check build)
     int ngroup[4];              // potential terms by tile modes touched (neither, D-2, D-1, both)
     const uint2* rowinfo;       // per-row (start, pattern) table, or null
+    const uint32_t* keys;       // sorted active linear indices (point-parallel pass)
     // generic single-mode pass (phase-space bases)
     const R* mat;               // n x n matrix of the pass (row stride kMaxN)
     double coef;                // result scale
@@ -72,8 +73,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_inner(ApplyArgs<R> a) {
     const size_t tile_elems = (size_t)n2 * nl;
     V* tiles = reinterpret_cast<V*>(smem);
     uint64_t* rbits_all = reinterpret_cast<uint64_t*>(tiles + tile_elems * a.wpb);
-    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + (size_t)kMaxN * a.wpb);
-    R* pref_all = reinterpret_cast<R*>(rstart_all + (size_t)kMaxN * a.wpb);
+    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + (size_t)kMaxNTile * a.wpb);
+    R* pref_all = reinterpret_cast<R*>(rstart_all + (size_t)kMaxNTile * a.wpb);
     R* Tq = pref_all + (size_t)kMaxTerms * a.wpb;   // [n2][n2]
     R* Tlt = Tq + n2 * n2;                          // [nl][nl], Tlt[ss][s] = T[s][ss]
     R* potq = Tlt + nl * nl;                        // [nt][n2]
@@ -93,8 +94,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_inner(ApplyArgs<R> a) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w >= a.wpb) return;
     V* tile = tiles + tile_elems * w;
-    uint64_t* rbits = rbits_all + (size_t)kMaxN * w;
-    uint32_t* rstart = rstart_all + (size_t)kMaxN * w;
+    uint64_t* rbits = rbits_all + (size_t)kMaxNTile * w;
+    uint32_t* rstart = rstart_all + (size_t)kMaxNTile * w;
     R* pref = pref_all + (size_t)kMaxTerms * w;
     const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
     const int64_t nunits = *a.nunits;
@@ -191,8 +192,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_outer(ApplyArgs<R> a) {
     const size_t tile_elems = (size_t)nk * nl;
     V* tiles = reinterpret_cast<V*>(smem);
     uint64_t* rbits_all = reinterpret_cast<uint64_t*>(tiles + tile_elems * a.wpb);
-    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + (size_t)kMaxN * a.wpb);
-    R* Tk = reinterpret_cast<R*>(rstart_all + (size_t)kMaxN * a.wpb);   // [nk][nk]
+    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + (size_t)kMaxNTile * a.wpb);
+    R* Tk = reinterpret_cast<R*>(rstart_all + (size_t)kMaxNTile * a.wpb);   // [nk][nk]
     for (int i = threadIdx.x; i < nk * nk; i += blockDim.x)
         Tk[i] = a.T[(size_t)k * kMaxN * kMaxN + (i / nk) * kMaxN + (i % nk)];
     __syncthreads();
@@ -200,8 +201,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_outer(ApplyArgs<R> a) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w >= a.wpb) return;
     V* tile = tiles + tile_elems * w;
-    uint64_t* rbits = rbits_all + (size_t)kMaxN * w;
-    uint32_t* rstart = rstart_all + (size_t)kMaxN * w;
+    uint64_t* rbits = rbits_all + (size_t)kMaxNTile * w;
+    uint32_t* rstart = rstart_all + (size_t)kMaxNTile * w;
     const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
     const int64_t nunits = *a.nunits;
 #ifdef PQ_BOUNDS_CHECK
@@ -541,20 +542,20 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_outer_cmp(ApplyArgs<R> 
     // per warp: xin [nk][32] V, rbits [64], rstart [64], rowj [64], trow [64] R
     V* tiles = reinterpret_cast<V*>(smem);
     uint64_t* rbits_all = reinterpret_cast<uint64_t*>(tiles + (size_t)nk * 32 * a.wpb);
-    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + kMaxN * a.wpb);
-    int* rowj_all = reinterpret_cast<int*>(rstart_all + kMaxN * a.wpb);
-    R* trow_all = reinterpret_cast<R*>(rowj_all + kMaxN * a.wpb);
-    R* Tk = trow_all + kMaxN * a.wpb;                       // [nk][nk]
+    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + kMaxNTile * a.wpb);
+    int* rowj_all = reinterpret_cast<int*>(rstart_all + kMaxNTile * a.wpb);
+    R* trow_all = reinterpret_cast<R*>(rowj_all + kMaxNTile * a.wpb);
+    R* Tk = trow_all + kMaxNTile * a.wpb;                       // [nk][nk]
     for (int i = threadIdx.x; i < nk * nk; i += blockDim.x)
         Tk[i] = a.T[(size_t)k * kMaxN * kMaxN + (i / nk) * kMaxN + (i % nk)];
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w >= a.wpb) return;
     V* xin = tiles + (size_t)nk * 32 * w;
-    uint64_t* rbits = rbits_all + kMaxN * w;
-    uint32_t* rstart = rstart_all + kMaxN * w;
-    int* rowj = rowj_all + kMaxN * w;
-    R* trow = trow_all + kMaxN * w;
+    uint64_t* rbits = rbits_all + kMaxNTile * w;
+    uint32_t* rstart = rstart_all + kMaxNTile * w;
+    int* rowj = rowj_all + kMaxNTile * w;
+    R* trow = trow_all + kMaxNTile * w;
     const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
     const int64_t nunits = *a.nunits;
     const uint64_t lmask = (1ull << lane) - 1ull;
@@ -643,12 +644,12 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_inner_cmp(ApplyArgs<R> 
     // pref [kMaxTerms] R, fj [64] R; shared: Tq [n2][n2], Tlt [nl][32]
     V* tiles = reinterpret_cast<V*>(smem);
     uint64_t* rbits_all = reinterpret_cast<uint64_t*>(tiles + (size_t)n2 * 32 * a.wpb);
-    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + kMaxN * a.wpb);
-    int* rowj_all = reinterpret_cast<int*>(rstart_all + kMaxN * a.wpb);
-    R* trow_all = reinterpret_cast<R*>(rowj_all + kMaxN * a.wpb);
-    R* pref_all = trow_all + kMaxN * a.wpb;
+    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + kMaxNTile * a.wpb);
+    int* rowj_all = reinterpret_cast<int*>(rstart_all + kMaxNTile * a.wpb);
+    R* trow_all = reinterpret_cast<R*>(rowj_all + kMaxNTile * a.wpb);
+    R* pref_all = trow_all + kMaxNTile * a.wpb;
     R* fj_all = pref_all + kMaxTerms * a.wpb;
-    R* Tq = fj_all + kMaxN * a.wpb;                         // [n2][n2]
+    R* Tq = fj_all + kMaxNTile * a.wpb;                         // [n2][n2]
     R* Tlt = Tq + n2 * n2;                                  // [nl][32]: Tlt[ss][s] = T[s][ss]
     for (int i = threadIdx.x; i < n2 * n2; i += blockDim.x)
         Tq[i] = a.T[(size_t)(D - 2) * kMaxN * kMaxN + (i / n2) * kMaxN + (i % n2)];
@@ -660,12 +661,12 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_inner_cmp(ApplyArgs<R> 
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w >= a.wpb) return;
     V* tile = tiles + (size_t)n2 * 32 * w;
-    uint64_t* rbits = rbits_all + kMaxN * w;
-    uint32_t* rstart = rstart_all + kMaxN * w;
-    int* rowj = rowj_all + kMaxN * w;
-    R* trow = trow_all + kMaxN * w;
+    uint64_t* rbits = rbits_all + kMaxNTile * w;
+    uint32_t* rstart = rstart_all + kMaxNTile * w;
+    int* rowj = rowj_all + kMaxNTile * w;
+    R* trow = trow_all + kMaxNTile * w;
     R* pref = pref_all + kMaxTerms * w;
-    R* fj = fj_all + kMaxN * w;
+    R* fj = fj_all + kMaxNTile * w;
     const int ls = lane < nl ? lane : nl - 1;
     const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
     const int64_t nunits = *a.nunits;
@@ -767,13 +768,13 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_inner_cmp(ApplyArgs<R> 
 template <typename R>
 static size_t smem_outer_cmp(int nk, int wpb) {
     const size_t esz = sizeof(R);
-    return (size_t)wpb * ((size_t)nk * 32 * 2 * esz + kMaxN * (8 + 4 + 4 + esz)) + (size_t)nk * nk * esz;
+    return (size_t)wpb * ((size_t)nk * 32 * 2 * esz + kMaxNTile * (8 + 4 + 4 + esz)) + (size_t)nk * nk * esz;
 }
 template <typename R>
 static size_t smem_inner_cmp(int n2, int nl, int wpb) {
     const size_t esz = sizeof(R);
-    return (size_t)wpb * ((size_t)n2 * 32 * 2 * esz + kMaxN * (8 + 4 + 4 + esz) + kMaxTerms * esz +
-                          kMaxN * esz) +
+    return (size_t)wpb * ((size_t)n2 * 32 * 2 * esz + kMaxNTile * (8 + 4 + 4 + esz) + kMaxTerms * esz +
+                          kMaxNTile * esz) +
            ((size_t)n2 * n2 + (size_t)nl * 32) * esz;
 }
 
@@ -801,7 +802,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_pass_row(ApplyArgs<R> a) {
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w >= a.wpb) return;
-    V* xrow = xrow_all + kMaxN * w;
+    V* xrow = xrow_all + kMaxNTile * w;
     const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
     const R coef = (R)a.coef;
     const int64_t nunits = *a.nunits;
@@ -855,15 +856,15 @@ __global__ void __launch_bounds__(kApplyThreads) k_pass_fibre(ApplyArgs<R> a) {
     const size_t tile_elems = (size_t)nk * nl;
     V* tiles = reinterpret_cast<V*>(smem);
     uint64_t* rbits_all = reinterpret_cast<uint64_t*>(tiles + tile_elems * a.wpb);
-    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + (size_t)kMaxN * a.wpb);
-    R* Mk = reinterpret_cast<R*>(rstart_all + (size_t)kMaxN * a.wpb);   // [nk][nk]
+    uint32_t* rstart_all = reinterpret_cast<uint32_t*>(rbits_all + (size_t)kMaxNTile * a.wpb);
+    R* Mk = reinterpret_cast<R*>(rstart_all + (size_t)kMaxNTile * a.wpb);   // [nk][nk]
     for (int i = threadIdx.x; i < nk * nk; i += blockDim.x) Mk[i] = a.mat[(i / nk) * kMaxN + (i % nk)];
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w >= a.wpb) return;
     V* tile = tiles + tile_elems * w;
-    uint64_t* rbits = rbits_all + (size_t)kMaxN * w;
-    uint32_t* rstart = rstart_all + (size_t)kMaxN * w;
+    uint64_t* rbits = rbits_all + (size_t)kMaxNTile * w;
+    uint32_t* rstart = rstart_all + (size_t)kMaxNTile * w;
     const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
     const R coef = (R)a.coef;
     const int64_t nunits = *a.nunits;
@@ -953,7 +954,7 @@ static pq_status launch_pass(const State& s, ApplyArgs<R> a, int mode, int mat, 
     int wpb = kApplyThreads / 32;
     if (mode == L.D - 1) {
         const int nl = L.nlast;
-        const size_t sm = (size_t)((nl * nl + 1) & ~1) * esz + (size_t)wpb * kMaxN * 2 * esz;
+        const size_t sm = (size_t)((nl * nl + 1) & ~1) * esz + (size_t)wpb * kMaxNTile * 2 * esz;
         a.wpb = wpb;
         a.units = s.rows;
         a.units_cap = s.rows_cap;
@@ -966,7 +967,7 @@ static pq_status launch_pass(const State& s, ApplyArgs<R> a, int mode, int mat, 
     }
     const int nk = L.n[mode], nl = L.nlast;
     auto smem = [&](int wp) {
-        return (size_t)wp * ((size_t)nk * nl * 2 * esz + kMaxN * 12) + (size_t)nk * nk * esz;
+        return (size_t)wp * ((size_t)nk * nl * 2 * esz + kMaxNTile * 12) + (size_t)nk * nk * esz;
     };
     while (wpb > 1 && smem(wpb) > kSmemBudget) --wpb;
     a.wpb = wpb;
@@ -1750,13 +1751,13 @@ static size_t smem_inner_q(int n2, int nl, int nboth) {
 
 static size_t smem_inner(const Lattice& L, int nterms, int wpb, size_t esz) {
     const int n2 = L.n[L.D - 2], nl = L.nlast;
-    const size_t per_warp = (size_t)n2 * nl * 2 * esz + kMaxN * 8 + kMaxN * 4 + kMaxTerms * esz;
+    const size_t per_warp = (size_t)n2 * nl * 2 * esz + kMaxNTile * 8 + kMaxNTile * 4 + kMaxTerms * esz;
     const size_t shared = ((size_t)n2 * n2 + (size_t)nl * nl + (size_t)nterms * (n2 + nl)) * esz;
     return per_warp * wpb + shared;
 }
 static size_t smem_outer(const Lattice& L, int k, int wpb, size_t esz) {
     const int nk = L.n[k], nl = L.nlast;
-    const size_t per_warp = (size_t)nk * nl * 2 * esz + kMaxN * 8 + kMaxN * 4;
+    const size_t per_warp = (size_t)nk * nl * 2 * esz + kMaxNTile * 8 + kMaxNTile * 4;
     return per_warp * wpb + (size_t)nk * nk * esz;
 }
 
@@ -1796,6 +1797,52 @@ static pq_status launch_outer_reg(ApplyArgs<R> a, int G, cudaStream_t st) {
 
 
 
+// ------------------------------------------------------------------------
+// Point-parallel pass for lattices with a mode longer than the tiled kernels
+// take (n > 64, e.g. the FGH grids of the double well, Sec. 3.2): one thread
+// per active point forms the whole pruned product for its point, every mode's
+// fibre found by bitmap tests and rank queries on the fly, the SoP potential
+// evaluated from the per-mode tables.  Meant for small lattices.
+template <typename R>
+__global__ void __launch_bounds__(256) k_apply_point(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    const Lattice& L = a.L;
+    const int D = L.D, nt = a.nterms;
+    const int64_t n = a.cnt[CNT_NA];
+    const R scale = a.in_scale ? (R)(*a.in_scale) : (R)1;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = a.keys[p];
+        int dg[kMaxD];
+        for (int k = 0; k < D; ++k) dg[k] = (int)((key / L.stride[k]) % (uint32_t)L.n[k]);
+        R vv = 0;
+        for (int t = 0; t < nt; ++t) {
+            R f = a.potc[t];
+            for (int k = 0; k < D; ++k) f *= a.pot[((size_t)t * D + k) * kMaxN + dg[k]];
+            vv += f;
+        }
+        const V xp = a.in[p];
+        R ax = vv * xp.x, ay = vv * xp.y;
+        for (int k = 0; k < D; ++k) {
+            const uint32_t sk = L.stride[k];
+            const uint32_t base = key - (uint32_t)dg[k] * sk;
+            const R* trow = a.T + ((size_t)k * kMaxN + dg[k]) * kMaxN;
+            for (int j = 0; j < L.n[k]; ++j) {
+                const uint32_t q = base + (uint32_t)j * sk;
+                if (!bit_test(a.bits, q)) continue;
+                const uint32_t pos = rank_of(a.bits, a.off, q);
+                if (!pq_in_bounds(pos, (uint64_t)n, 29, a.cnt)) continue;
+                const V x = a.in[pos];
+                ax += trow[j] * x.x;
+                ay += trow[j] * x.y;
+            }
+        }
+        a.out[p] = cmake<R>(scale * ax, scale * ay);
+    }
+}
+
 template <typename R>
 static pq_status launch_all(const State& s, const void* in, void* out, const double* in_scale,
                             const int* skip, int skip_k, cudaStream_t st) {
@@ -1818,6 +1865,14 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
     a.nterms = s.nterms;
     a.cnt = s.cnt;
     if (s.generic) return launch_generic<R>(s, a, in, out, in_scale, st);
+    bool big = false;
+    for (int k = 0; k < L.D; ++k) big = big || L.n[k] > kMaxNTile;
+    if (big) {   // a mode longer than the tiled kernels take
+        a.keys = s.keys;
+        k_apply_point<R><<<grid_size() * 8, 256, 0, st>>>(a);
+        PQ_CHECK_LAUNCH();
+        return PQ_OK;
+    }
     static bool attr_set[2][2] = {{false, false}, {false, false}};
     const int pi = sizeof(R) == 8 ? 1 : 0;
     if (!attr_set[pi][0]) {

@@ -88,6 +88,28 @@ static void sine_dvr(int n, double xmin, double xmax, double mass, std::vector<d
         }
 }
 
+// Fourier grid (FGH) DVR on the periodic box [xmin, xmax): x_j = xmin + j L/n,
+// w = L/n, T_ij = (1/n) sum_l (k_l^2 / 2m) cos(k_l (x_i - x_j)), k_l = 2 pi l / L,
+// l = -(n-1)/2 .. n/2 (integer division; for even n the last is the Nyquist mode).
+static void fgh_dvr(int n, double xmin, double xmax, double mass, std::vector<double>& x,
+                    std::vector<double>& w, std::vector<double>& T) {
+    const double L = xmax - xmin;
+    x.resize(n);
+    w.assign(n, L / n);
+    for (int j = 0; j < n; ++j) x[j] = xmin + j * L / n;
+    T.assign((size_t)n * n, 0.0);
+    const int lo = -((n - 1) / 2), hi = n / 2;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            double acc = 0.0;
+            for (int l = lo; l <= hi; ++l) {
+                const double k = 2.0 * M_PI * l / L;
+                acc += k * k / (2.0 * mass) * cos(2.0 * M_PI * (double)l * (a - b) / n);
+            }
+            T[(size_t)a * n + b] = acc / n;
+        }
+}
+
 // Normalised HO functions phi_0..phi_{n} at x (three-term recurrence in
 // xi = sqrt(m omega) x): phi_{k+1} = sqrt(2/(k+1)) xi phi_k - sqrt(k/(k+1)) phi_{k-1}.
 static void ho_functions(int n, double mass, double omega, double x, double* phi) {
@@ -171,6 +193,10 @@ static int ho_dvr(int n, double mass, double omega, std::vector<double>& x,
 pq_status build_pw_mode(const pq_mode_desc& m, std::vector<double>& x, std::vector<double>& w,
                         std::vector<double>& T, std::vector<double>& W) {
     const int n = m.n, nx = m.nx_lattice, np_ = m.np_lattice;
+    if (n > kMaxNTile) {
+        set_error("projected Weylets: at most %d functions per mode (%d given)", kMaxNTile, n);
+        return PQ_ENOTSUP;
+    }
     if (nx < 1 || np_ < 1 || nx * np_ != n) {
         set_error("projected Weylets need nx_lattice * np_lattice = n (%d x %d != %d)", nx, np_, n);
         return PQ_EINVAL;
@@ -291,6 +317,10 @@ pq_status build_pvb_mode(const pq_mode_desc& m, std::vector<double>& x, std::vec
                          std::vector<double>& T, std::vector<double>& G, std::vector<double>& B,
                          std::vector<double>& S) {
     const int n = m.n, nx = m.nx_lattice, np_ = m.np_lattice;
+    if (n > kMaxNTile) {
+        set_error("pvB: at most %d functions per mode (%d given)", kMaxNTile, n);
+        return PQ_ENOTSUP;
+    }
     if (nx < 1 || np_ < 1 || nx * np_ != n) {
         set_error("pvB needs nx_lattice * np_lattice = n (%d x %d != %d)", nx, np_, n);
         return PQ_EINVAL;
@@ -358,6 +388,14 @@ pq_status build_dvr_mode(const pq_mode_desc& m, std::vector<double>& x, std::vec
             return PQ_EINVAL;
         }
         sine_dvr(m.n, m.xmin, m.xmax, m.mass, x, w, T);
+        return PQ_OK;
+    }
+    if (m.kind == PQ_FGH_DVR) {
+        if (!(m.xmax > m.xmin)) {
+            set_error("FGH DVR needs xmax > xmin");
+            return PQ_EINVAL;
+        }
+        fgh_dvr(m.n, m.xmin, m.xmax, m.mass, x, w, T);
         return PQ_OK;
     }
     if (m.kind == PQ_HO_DVR) {

@@ -233,6 +233,10 @@ pq_status rebuild_tables(State& s, cudaStream_t st) {
     }
     OpPlanes opl{s.rows, s.cnt + CNT_ROWS, s.planes, L.n[L.D - 2], s.rows_cap, s.cnt};
     if ((rc = run_scan(opl, s.scan_tmp, s.cnt + CNT_PLANES, -1, nullptr, 0, st))) return rc;
+    if (L.nlast > kMaxNTile) {   // fibre leaders serve the tiled kernels only
+        PQ_CUDA_TRY(cudaMemsetAsync(s.cnt + CNT_LEAD0, 0, sizeof(int64_t) * (kMaxD - 1), st));
+        return PQ_OK;
+    }
     for (int k = 0; k + 1 < L.D; ++k) {   // fibre leaders of every mode but the last
         OpLeaders ol{s.rows, s.cnt + CNT_ROWS, s.bits, s.leaders + (size_t)k * s.rows_cap,
                      L.rstride[k], L.n[k], L.nlast, s.rows_cap, s.cnt};

@@ -14,7 +14,8 @@
 namespace pq {
 
 constexpr int kMaxD = 8;        // modes (a virtual size-1 mode is added for D = 1)
-constexpr int kMaxN = 64;       // points per mode
+constexpr int kMaxN = 256;      // points per mode (row stride of the per-mode tables)
+constexpr int kMaxNTile = 64;   // points per mode of the shared-memory tiled kernels and phase-space bases
 constexpr int kMaxTerms = 64;   // potential terms
 constexpr int kMaxK = 32;       // Krylov dimension
 

@@ -5,6 +5,7 @@ potential is a sum of products of diagonal factors).
 Kinetic energy: one term per mode with the mode's kinetic factor.
 Henon-Heiles chain: sum_k 1/2 omega_k^2 q_k^2 + lam sum_{k<D} (q_k^2 q_{k+1} - q_{k+1}^3 / 3).
 Coupled Morse:      sum_k De (1 - exp(-a (q_k - qe)))^2 + c sum_{i<j} q_i q_j.
+Double well (Sec. 3.2, Eq. ex_dwell): c1 (x-1)^2 (x-2)^2 + c2 (y-2)^2 + c3 x^2 y.
 """
 from __future__ import annotations
 
@@ -50,9 +51,21 @@ def coupled_morse_terms(grids, De, a, qe, coupling):
     return terms
 
 
+def double_well_terms(grids, c1, c2, c3):
+    x, y = grids
+    terms = kinetic_terms(2)
+    terms.append((c1, [(x - 1.0) ** 2 * (x - 2.0) ** 2, None]))
+    terms.append((c2, [None, (y - 2.0) ** 2]))
+    terms.append((c3, [x * x, y]))
+    return terms
+
+
 def modes_of(cfg):
     """Mode descriptors of a workload record (see ``workloads``)."""
-    from . import SINE_DVR, HO_DVR, PW, PVB
+    from . import SINE_DVR, HO_DVR, PW, PVB, FGH_DVR
+    if cfg["basis"] == "fgh":
+        return [dict(kind=FGH_DVR, n=cfg["n"][k], xmin=cfg["xmin"][k], xmax=cfg["xmax"][k],
+                     mass=cfg["mass"]) for k in range(cfg["D"])]
     if cfg["basis"] in ("pw", "pvb"):
         kind = PW if cfg["basis"] == "pw" else PVB
         return [dict(kind=kind, n=cfg["n"], xmin=cfg["xmin"], xmax=cfg["xmax"], mass=cfg["mass"],
@@ -71,7 +84,9 @@ def build_model(cfg, omegas=None, lam=None):
     from . import Basis
     b = Basis(modes_of(cfg))
     grids = [b.grid(k)[0] for k in range(b.D)]
-    if cfg["basis"] in ("sine", "pw", "pvb"):
+    if cfg["basis"] == "fgh":
+        terms = double_well_terms(grids, *cfg["dw_coef"])
+    elif cfg["basis"] in ("sine", "pw", "pvb"):
         terms = coupled_morse_terms(grids, cfg["morse_D"], cfg["morse_a"], cfg["morse_qe"],
                                     cfg["coupling"])
     else:

@@ -49,6 +49,20 @@ def ho_problem(dims, seed, nterms=3):
     return b, Ts, pot
 
 
+def fgh_problem(dims, seed, nterms=3, box=(-1.0, 2.0), mass=3.0):
+    """Library basis (FGH DVR modes of any length up to 256, kinetic + random
+    potential) and the oracle's kinetic matrices for the same lattice."""
+    from oracle import bases
+    pq = lib()
+    b = pq.Basis([dict(kind=pq.FGH_DVR, n=int(n), xmin=box[0], xmax=box[1], mass=mass)
+                  for n in dims])
+    pot = random_sop(dims, seed, nterms)
+    terms = [(1.0, ["T" if k == m else None for k in range(len(dims))]) for m in range(len(dims))]
+    b.set_sop(terms + pot)
+    Ts = [bases.fgh_dvr(int(n), box[0], box[1], mass)[2] for n in dims]
+    return b, Ts, pot
+
+
 def state_with(b, A, psi, precision):
     """A library state on basis b loaded with (A, psi)."""
     pq = lib()

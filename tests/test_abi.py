@@ -52,6 +52,22 @@ def test_host_bases_match_oracle():
     np.testing.assert_allclose(xl, x, atol=1e-14)
     np.testing.assert_allclose(wl, w, rtol=1e-14)
     np.testing.assert_allclose(b.kinetic(1), T, atol=1e-14 * abs(T).max())
+    b = pq.Basis(pq.modes_of(W.DWELL2D))
+    for k in range(2):
+        cfg = W.DWELL2D
+        x, w, T = bases.fgh_dvr(cfg["n"][k], cfg["xmin"][k], cfg["xmax"][k], cfg["mass"])
+        xl, wl = b.grid(k)
+        np.testing.assert_allclose(xl, x, atol=1e-14)
+        np.testing.assert_allclose(wl, w, rtol=1e-14)
+        np.testing.assert_allclose(b.kinetic(k), T, atol=1e-12 * abs(T).max())
+
+
+def test_phase_space_bases_limited_to_64():
+    pq = _lib()
+    with pytest.raises(pq.PQError) as e:
+        pq.Basis([dict(kind=pq.PW, n=66, xmin=0.5, xmax=6.0, mass=1.0, nx_lattice=11,
+                       np_lattice=6)])
+    assert e.value.status == pq.ENOTSUP
 
 
 def test_argument_errors():
@@ -60,7 +76,7 @@ def test_argument_errors():
         pq.Basis([dict(kind=pq.SINE_DVR, n=1, xmin=0, xmax=1, mass=1)])
     assert e.value.status == pq.EINVAL
     with pytest.raises(pq.PQError) as e:
-        pq.Basis([dict(kind=pq.HO_DVR, n=65)])
+        pq.Basis([dict(kind=pq.HO_DVR, n=257)])
     assert e.value.status == pq.EINVAL
     with pytest.raises(pq.PQError) as e:   # 64^6 > 2^32
         pq.Basis([dict(kind=pq.HO_DVR, n=64)] * 6)

@@ -8,18 +8,18 @@ import numpy as np
 import pytest
 
 import workloads as W
-from gpu_helpers import ho_problem, lib, rel_bound, state_with, vdiag_of
+from gpu_helpers import fgh_problem, ho_problem, lib, rel_bound, state_with, vdiag_of
 
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-13, 1: 4e-6}
 
 
-def _run(dims, A, seed, prec, nterms=3):
+def _run(dims, A, seed, prec, nterms=3, problem=ho_problem, tol=None):
     import torch
     from oracle import pruned
     pq = lib()
-    b, Ts, pot = ho_problem(dims, seed, nterms)
+    b, Ts, pot = problem(dims, seed, nterms)
     psi = W.random_psi(len(A), seed + 1)
     dt = np.complex128 if prec == pq.FP64 else np.complex64
     psi = psi.astype(dt)
@@ -38,7 +38,8 @@ def _run(dims, A, seed, prec, nterms=3):
     ref = pruned.apply_H(A, psi.astype(np.complex128), dims, Ts, vd)
     bound = rel_bound(Ts, A, psi, dims, vd)
     err = np.abs(got - ref)
-    assert np.all(err <= TOL[prec] * bound + 1e-300), (err / np.maximum(bound, 1e-300)).max()
+    tl = TOL[prec] if tol is None else tol[prec]
+    assert np.all(err <= tl * bound + 1e-300), (err / np.maximum(bound, 1e-300)).max()
     # host-buffer entry point gives the same numbers
     got_h = s.apply_H_host(psi)
     np.testing.assert_array_equal(got_h, y.cpu().numpy())
@@ -125,3 +126,15 @@ def test_apply_hh6d_initial_state_sampled():
                               [np.abs(T) for T in prob.Ts], np.abs(vd), pos).real
     err = np.abs(got[pos] - ref)
     assert np.all(err <= 4e-6 * scale + 1e-30), (err / scale).max()
+
+
+# Lattices with a mode longer than 64 (FGH DVR, point-parallel pass): up to
+# 246 terms per output, so the FP32 bound is taken at 1e-5 of the rounding scale.
+BIG = [((165, 81), 0.3), ((70, 9), 0.5), ((100, 3, 5), 0.4), ((9, 130), 0.5), ((5, 4, 66), 0.6)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dims,frac", BIG)
+def test_apply_long_modes(dims, frac, prec):
+    A = W.random_active_set(dims, frac, seed=len(dims) * 3 + int(frac * 10))
+    _run(dims, A, 7, prec, problem=fgh_problem, tol={0: 1e-13, 1: 1e-5})

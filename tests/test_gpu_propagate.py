@@ -130,3 +130,23 @@ def test_morse2d_fp64_neighbour_rules(rule, rho):
     assert np.max(np.abs(o["C"] - _series(r, "C"))) < 1e-10
     A, psi = s.read()
     np.testing.assert_array_equal(A, r["A"])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_double_well_steps(prec):
+    # the paper's double well (Sec. 3.2) on its FGH grids of 165 x 81 points:
+    # FP64 identical active sets and C(t) within 1e-10 of the oracle; FP32-mix
+    # C(t) within 1e-5
+    pq = lib()
+    cfg = W.DWELL2D
+    n = 150
+    prob, r = _oracle(cfg, n)
+    s, o = _gpu(cfg, n, prec)
+    if prec == pq.FP64:
+        np.testing.assert_array_equal(o["n_active"], _series(r, "n_active"))
+        assert np.max(np.abs(o["C"] - _series(r, "C"))) < 1e-10
+        A, psi = s.read()
+        np.testing.assert_array_equal(A, r["A"])
+        assert np.linalg.norm(psi - r["a"]) <= 1e-10 * np.linalg.norm(r["a"])
+    else:
+        assert np.max(np.abs(o["C"] - _series(r, "C"))) < 1e-5

@@ -13,6 +13,33 @@ from oracle import bases, models, pruned, sil, propagate
 
 # ---------------------------------------------------------------- 1D bases
 
+def test_fgh_free_particle_spectrum():
+    # Closed form: on a periodic box of length L the FGH DVR is exact for the
+    # plane waves it carries, so the eigenvalues of T are (2 pi l / L)^2 / 2m
+    # for l = -(n-1)//2 .. n//2 (catches a wrong L, mass, grid or Nyquist term).
+    for n, lo, hi, m in [(165, -0.5, 3.7, 200.0), (81, 1.0, 2.9, 200.0), (8, 0.0, 1.0, 1.0)]:
+        x, w, T = bases.fgh_dvr(n, lo, hi, m)
+        L = hi - lo
+        l = np.arange(-((n - 1) // 2), n // 2 + 1)
+        ref = np.sort((2 * np.pi * l / L) ** 2 / (2 * m))
+        np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(T)), ref, rtol=1e-12,
+                                   atol=1e-12 * ref.max())
+        np.testing.assert_allclose(np.diff(x), L / n, rtol=1e-12)
+        assert x[0] == lo and abs(x[-1] + L / n - hi) < 1e-12
+        np.testing.assert_allclose(w, L / n, rtol=1e-15)
+
+
+def test_fgh_is_circulant_and_gives_ho_levels():
+    # a periodic DVR's T depends on (i - j) mod n only; on a wide box it gives
+    # the HO levels n + 1/2 (catches an asymmetric or mis-phased kernel).
+    x, w, T = bases.fgh_dvr(64, -8.0, 8.0, 1.0)
+    for s in range(1, 64):
+        np.testing.assert_allclose(np.diag(np.roll(T, s, axis=1)), np.roll(T, s, axis=1)[0, 0],
+                                   atol=1e-13)
+    ev = np.linalg.eigvalsh(T + np.diag(0.5 * x * x))
+    np.testing.assert_allclose(ev[:10], np.arange(10) + 0.5, atol=1e-10)
+
+
 def test_sine_dvr_free_particle_levels():
     # Closed form: a particle in a box of length L has E_k = (k pi / L)^2 / 2m,
     # and the sine DVR is exact for it for k <= n (catches a wrong U, L or m).
@@ -339,6 +366,23 @@ def test_autocorrelation_2t_identity():
         states.append(a)
     for s in range(4):
         assert abs(r["obs"][2 * s]["C"] - np.sum(states[s] ** 2)) < 1e-11
+
+
+def test_double_well_autocorrelation_2t_identity():
+    # Eq. acorr on the paper's own double well (Sec. 3.2, real packet, real
+    # FGH DVR, theta = 0): C(2t) = sum_I a_I(t)^2, at the full grid of 13365
+    # points (catches a wrong potential sign or a complex-conjugation slip).
+    cfg = W.DWELL2D
+    prob = propagate.problem_from_config(cfg)
+    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], 0.0, cfg["K"], cfg["dt"], 6)
+    A, a, f = propagate.initial_state(prob, cfg["q0"], cfg["p0"], cfg["width"], 0.0)
+    assert len(A) == 165 * 81
+    states = [a]
+    for _ in range(3):
+        a = sil.sil_step(a, lambda v: prob.apply(A, v), cfg["K"], cfg["dt"])
+        states.append(a)
+    for s in range(4):
+        assert abs(r["obs"][2 * s]["C"] - np.sum(states[s] ** 2)) < 1e-10
 
 
 def test_hh_lambda0_coherent_state_closed_form():
