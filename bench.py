@@ -348,6 +348,41 @@ def run_apply(args, cfg):
                       "peak_kind": kind, "reps": args.reps}), flush=True)
 
 
+def run_dwell(args, cfg):
+    """Accuracy study on the paper's 2D double well (Sec. 3.2; the comparisons
+    of its neighbour-radius and threshold figures, here for the pruned FGH
+    DVR): for each neighbour rule and threshold, propagate to t_e = 24.6 in
+    FP64, and report the mean number of basis functions used (percent of the
+    165 x 81 lattice) and the infidelity, the Euclidean L2 distance between
+    the C(t) series of the pruned run and of the unpruned run (theta = 0)."""
+    import paper_1606_04004_gb300 as pq
+    b = pq.build_model(cfg)
+    nfull = int(np.prod(cfg["n"]))
+
+    def series(theta, rule):
+        s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], theta, precision=pq.FP64, radius=rule)
+        s.propagate(cfg["K"], cfg["dt"], theta, cfg["nsteps"], radius=rule)
+        o = s.observables()
+        s.free()
+        return o
+
+    t0 = time.perf_counter()
+    exact = series(0.0, 1)
+    assert int(exact["n_active"].min()) == nfull
+    rows = []
+    for rule, name in ((pq.RADIUS_1, "1"), (pq.RADIUS_SQRT2, "sqrt2"), (pq.RADIUS_2, "2")):
+        for theta in (3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 1e-6, 1e-8):
+            o = series(theta, rule)
+            inf = float(np.linalg.norm(o["C"] - exact["C"]))
+            rows.append({"radius": name, "theta": theta,
+                         "mean_basis_pct": float(100.0 * o["n_active"].mean() / nfull),
+                         "infidelity": inf})
+            print(json.dumps(dict(mode="dwell", **rows[-1])), flush=True)
+    print(json.dumps({"mode": "dwell", "summary": True, "t_end": cfg["dt"] * cfg["nsteps"],
+                      "steps": cfg["nsteps"], "K": cfg["K"], "dt": cfg["dt"],
+                      "seconds": time.perf_counter() - t0}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,7 +395,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "apply"])
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "dwell"])
     ap.add_argument("--radius", type=float, default=11.2)
     ap.add_argument("--reps", type=int, default=20)
     args = ap.parse_args()
@@ -369,6 +404,8 @@ def main():
     cfg = W.CONFIGS[args.config]
     if args.mode == "apply":
         run_apply(args, cfg)
+    elif args.mode == "dwell":
+        run_dwell(args, W.DWELL2D)
     elif args.impl == "reference":
         run_reference(args, cfg)
     else:
