@@ -348,18 +348,18 @@ def run_apply(args, cfg):
                       "peak_kind": kind, "reps": args.reps}), flush=True)
 
 
-def run_dwell(args, cfg):
+def run_dwell(args):
     """Accuracy study on the paper's 2D double well (Sec. 3.2; the comparisons
-    of its neighbour-radius and threshold figures, here for the pruned FGH
-    DVR): for each neighbour rule and threshold, propagate to t_e = 24.6 in
-    FP64, and report the mean number of basis functions used (percent of the
-    165 x 81 lattice) and the infidelity, the Euclidean L2 distance between
-    the C(t) series of the pruned run and of the unpruned run (theta = 0)."""
+    of its neighbour-radius and basis figures): the pruned FGH DVR and the
+    projected Weylets built on the same FGH grids.  For each basis, neighbour
+    rule and threshold, propagate to t_e = 24.6 in FP64 and report the mean
+    number of basis functions used (percent of the 13365) and the infidelity,
+    the Euclidean L2 distance between the C(t) series of the pruned run and of
+    the unpruned FGH run (theta = 0)."""
     import paper_1606_04004_gb300 as pq
-    b = pq.build_model(cfg)
-    nfull = int(np.prod(cfg["n"]))
 
-    def series(theta, rule):
+    def series(cfg, theta, rule):
+        b = pq.build_model(cfg)
         s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], theta, precision=pq.FP64, radius=rule)
         s.propagate(cfg["K"], cfg["dt"], theta, cfg["nsteps"], radius=rule)
         o = s.observables()
@@ -367,19 +367,23 @@ def run_dwell(args, cfg):
         return o
 
     t0 = time.perf_counter()
-    exact = series(0.0, 1)
+    nfull = int(np.prod(W.DWELL2D["n"]))
+    exact = series(W.DWELL2D, 0.0, 1)
     assert int(exact["n_active"].min()) == nfull
-    rows = []
-    for rule, name in ((pq.RADIUS_1, "1"), (pq.RADIUS_SQRT2, "sqrt2"), (pq.RADIUS_2, "2")):
-        for theta in (3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 1e-6, 1e-8):
-            o = series(theta, rule)
-            inf = float(np.linalg.norm(o["C"] - exact["C"]))
-            rows.append({"radius": name, "theta": theta,
-                         "mean_basis_pct": float(100.0 * o["n_active"].mean() / nfull),
-                         "infidelity": inf})
-            print(json.dumps(dict(mode="dwell", **rows[-1])), flush=True)
-    print(json.dumps({"mode": "dwell", "summary": True, "t_end": cfg["dt"] * cfg["nsteps"],
-                      "steps": cfg["nsteps"], "K": cfg["K"], "dt": cfg["dt"],
+    thetas = (3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 1e-6, 1e-8)
+    # on the 2D coordinate lattice radius sqrt 2 and radius 2 add the same 8 neighbours
+    plan = [(W.DWELL2D, "fgh", pq.RADIUS_1, "1"), (W.DWELL2D, "fgh", pq.RADIUS_SQRT2, "sqrt2"),
+            (W.DWELL2D_PW, "pw", pq.RADIUS_1, "1"), (W.DWELL2D_PW, "pw", pq.RADIUS_SQRT2, "sqrt2"),
+            (W.DWELL2D_PW, "pw", pq.RADIUS_2, "2")]
+    for cfg, basis, rule, name in plan:
+        for theta in thetas:
+            o = series(cfg, theta, rule)
+            row = {"mode": "dwell", "basis": basis, "radius": name, "theta": theta,
+                   "mean_basis_pct": float(100.0 * o["n_active"].mean() / nfull),
+                   "infidelity": float(np.linalg.norm(o["C"] - exact["C"]))}
+            print(json.dumps(row), flush=True)
+    print(json.dumps({"mode": "dwell", "summary": True, "t_end": W.DWELL2D["dt"] * W.DWELL2D["nsteps"],
+                      "steps": W.DWELL2D["nsteps"], "K": W.DWELL2D["K"], "dt": W.DWELL2D["dt"],
                       "seconds": time.perf_counter() - t0}), flush=True)
 
 
@@ -405,7 +409,7 @@ def main():
     if args.mode == "apply":
         run_apply(args, cfg)
     elif args.mode == "dwell":
-        run_dwell(args, W.DWELL2D)
+        run_dwell(args)
     elif args.impl == "reference":
         run_reference(args, cfg)
     else:

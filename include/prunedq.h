@@ -73,7 +73,7 @@ typedef enum pq_neighbour_rule {
 
 /* One mode of the direct-product basis.
  *  kind   pq_basis_kind.
- *  n      number of points (DVRs: 2..256, pvB and pW: 2..64).  Lattices
+ *  n      number of points (DVRs and pW: 2..256, pvB: 2..64).  Lattices
  *         with a mode longer than 64 use a point-parallel H.psi meant for
  *         small lattices (the 2D FGH double well).
  *  xmin, xmax  box edges: sine DVR points at xmin + j L/(n+1), j=1..n; FGH
@@ -81,6 +81,8 @@ typedef enum pq_neighbour_rule {
  *  mass   mass in the kinetic energy -d^2/dx^2 / (2 mass).
  *  omega  frequency of the HO-DVR's underlying oscillator (with `mass`).
  *  nx_lattice, np_lattice  phase-space lattice of pvB / pW modes (unused for DVRs).
+ *  dvr    underlying DVR of a pvB / pW mode: PQ_SINE_DVR (0, default) or
+ *         PQ_FGH_DVR (Sec. 3.2 builds both phase-space bases on the FGH grid).
  */
 typedef struct pq_mode_desc {
     int kind;
@@ -89,6 +91,7 @@ typedef struct pq_mode_desc {
     double mass;
     double omega;
     int nx_lattice, np_lattice;
+    int dvr;
 } pq_mode_desc;
 
 typedef struct pq_basis pq_basis;

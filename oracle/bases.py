@@ -89,8 +89,9 @@ def ho_dvr(n: int, mass: float = 1.0, omega: float = 1.0):
     return x, w, T
 
 
-def pw_basis(n, xmin, xmax, mass, nx, np_):
-    """Projected Weylets on a sine DVR (Sec. 2.4).
+def pw_basis(n, xmin, xmax, mass, nx, np_, dvr="sine"):
+    """Projected Weylets on a sine DVR, or on an FGH DVR with dvr="fgh" (Sec. 2.4;
+    Sec. 3.2 uses the FGH grid).
 
     Momentum-symmetrised Gaussians (Eq. sG_def) on a doubly dense phase-space
     lattice (Delta x Delta p = pi, p_l > 0): x_a = xmin + (a + 1/2) Dx with
@@ -103,7 +104,7 @@ def pw_basis(n, xmin, xmax, mass, nx, np_):
     Returns (x, w, T, W) where x, w, T are the underlying DVR's."""
     if nx * np_ != n:
         raise ValueError("the phase-space lattice must have as many functions as DVR points")
-    x, w, T = sine_dvr(n, xmin, xmax, mass)
+    x, w, T = (fgh_dvr if dvr == "fgh" else sine_dvr)(n, xmin, xmax, mass)
     L = xmax - xmin
     dx = L / nx
     dp = np.pi / dx

@@ -92,9 +92,27 @@ def pw_problem_from_config(cfg, n=None, nx=None, np_=None):
     return PWProblem([x] * D, [w] * D, [T] * D, [W] * D, [(nx, np_)] * D, terms)
 
 
+def dwell_pw_problem(cfg):
+    """pW problem of the double well (Sec. 3.2): projected Weylets on the FGH
+    grids of each mode, the double-well SoP terms transformed by congruence."""
+    xs, ws, Ts, Wm, lat = [], [], [], [], []
+    for k in range(cfg["D"]):
+        x, w, T, Wk = bases.pw_basis(cfg["n"][k], cfg["xmin"][k], cfg["xmax"][k], cfg["mass"],
+                                     cfg["nx_lattice"][k], cfg["np_lattice"][k], dvr="fgh")
+        xs.append(x); ws.append(w); Ts.append(T); Wm.append(Wk)
+        lat.append((cfg["nx_lattice"][k], cfg["np_lattice"][k]))
+    c1, c2, c3 = cfg["dw_coef"]
+    x, y = xs
+    terms = [(1.0, {0: "T"}), (1.0, {1: "T"}), (c1, {0: (x - 1.0) ** 2 * (x - 2.0) ** 2}),
+             (c2, {1: (y - 2.0) ** 2}), (c3, {0: x * x, 1: y})]
+    return PWProblem(xs, ws, Ts, Wm, lat, terms)
+
+
 def problem_from_config(cfg, omegas=None, lam=None):
     """Build the problem of a workload record (see ``workloads``)."""
     D, n = cfg["D"], cfg["n"]
+    if cfg["basis"] == "pw" and cfg.get("dvr") == "fgh":
+        return dwell_pw_problem(cfg)
     if cfg["basis"] == "pw":
         return pw_problem_from_config(cfg)
     if cfg["basis"] == "fgh":

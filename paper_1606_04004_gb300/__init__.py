@@ -44,7 +44,7 @@ class PQError(RuntimeError):
 class ModeDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("n", C.c_int), ("xmin", C.c_double), ("xmax", C.c_double),
                 ("mass", C.c_double), ("omega", C.c_double), ("nx_lattice", C.c_int),
-                ("np_lattice", C.c_int)]
+                ("np_lattice", C.c_int), ("dvr", C.c_int)]
 
 
 class Factor(C.Structure):
@@ -143,7 +143,7 @@ class Basis:
             arr[i] = ModeDesc(int(m.get("kind", 0)), int(m["n"]), float(m.get("xmin", 0.0)),
                               float(m.get("xmax", 0.0)), float(m.get("mass", 1.0)),
                               float(m.get("omega", 1.0)), int(m.get("nx_lattice", 0)),
-                              int(m.get("np_lattice", 0)))
+                              int(m.get("np_lattice", 0)), int(m.get("dvr", 0)))
         h = _vp()
         _check(_lib.pq_build_basis(arr, len(modes), C.byref(h)))
         self._h = h

@@ -937,6 +937,45 @@ __global__ void k_zero(typename Cx<R>::T* out, const int64_t* na, const int* ski
         out[p] = cmake<R>(0, 0);
 }
 
+// Point-parallel single-mode pass (lattices with a mode longer than 64):
+// out_I (+)= coef * sum_j M[i_k][j] in_{I[k->j]} over the active j, one thread
+// per active point.
+template <typename R>
+__global__ void __launch_bounds__(256) k_pass_point(ApplyArgs<R> a) {
+    using V = typename Cx<R>::T;
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    const Lattice& L = a.L;
+    const int k = a.mode, nk = L.n[k];
+    const uint32_t sk = L.stride[k];
+    const int64_t n = a.cnt[CNT_NA];
+    const R scale = (a.in_scale ? (R)(*a.in_scale) : (R)1) * (R)a.coef;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = a.keys[p];
+        const int d = (int)((key / sk) % (uint32_t)nk);
+        const uint32_t base = key - (uint32_t)d * sk;
+        const R* mrow = a.mat + (size_t)d * kMaxN;
+        R ax = 0, ay = 0;
+        for (int j = 0; j < nk; ++j) {
+            const uint32_t q = base + (uint32_t)j * sk;
+            if (!bit_test(a.bits, q)) continue;
+            const uint32_t pos = rank_of(a.bits, a.off, q);
+            if (!pq_in_bounds(pos, (uint64_t)n, 30, a.cnt)) continue;
+            const V x = a.in[pos];
+            ax += mrow[j] * x.x;
+            ay += mrow[j] * x.y;
+        }
+        V y = cmake<R>(scale * ax, scale * ay);
+        if (a.accumulate) {
+            const V o = a.out[p];
+            y.x += o.x;
+            y.y += o.y;
+        }
+        a.out[p] = y;
+    }
+}
+
 template <typename R>
 static pq_status launch_pass(const State& s, ApplyArgs<R> a, int mode, int mat, const void* in,
                              void* out, const double* in_scale, double coef, int accumulate,
@@ -952,6 +991,14 @@ static pq_status launch_pass(const State& s, ApplyArgs<R> a, int mode, int mat, 
     a.mode = mode;
     const int G = grid_size();
     int wpb = kApplyThreads / 32;
+    bool big = false;
+    for (int k = 0; k < L.D; ++k) big = big || L.n[k] > kMaxNTile;
+    if (big) {   // a mode longer than the tiled passes take
+        a.keys = s.keys;
+        k_pass_point<R><<<G * 8, 256, 0, st>>>(a);
+        PQ_CHECK_LAUNCH();
+        return PQ_OK;
+    }
     if (mode == L.D - 1) {
         const int nl = L.nlast;
         const size_t sm = (size_t)((nl * nl + 1) & ~1) * esz + (size_t)wpb * kMaxNTile * 2 * esz;

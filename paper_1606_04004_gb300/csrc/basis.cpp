@@ -184,7 +184,7 @@ static int ho_dvr(int n, double mass, double omega, std::vector<double>& x,
     return 0;
 }
 
-// Projected Weylets (Sec. 2.4) on a sine DVR: momentum-symmetrised Gaussians
+// Projected Weylets (Sec. 2.4) on a sine or FGH DVR: momentum-symmetrised Gaussians
 // (Eq. sG_def) on the doubly dense lattice Dx Dp = pi (x_a cell-centred,
 // p_b = (b + 1/2) Dp > 0, alpha = Dp / (2 Dx)), projected on the DVR
 // (Phi_ji = sqrt(w_j) phi_i(x_j), i = a np + b) and orthogonalised
@@ -193,9 +193,9 @@ static int ho_dvr(int n, double mass, double omega, std::vector<double>& x,
 pq_status build_pw_mode(const pq_mode_desc& m, std::vector<double>& x, std::vector<double>& w,
                         std::vector<double>& T, std::vector<double>& W) {
     const int n = m.n, nx = m.nx_lattice, np_ = m.np_lattice;
-    if (n > kMaxNTile) {
-        set_error("projected Weylets: at most %d functions per mode (%d given)", kMaxNTile, n);
-        return PQ_ENOTSUP;
+    if (n < 2 || n > kMaxN) {
+        set_error("projected Weylets: %d functions per mode outside 2..%d", n, kMaxN);
+        return PQ_EINVAL;
     }
     if (nx < 1 || np_ < 1 || nx * np_ != n) {
         set_error("projected Weylets need nx_lattice * np_lattice = n (%d x %d != %d)", nx, np_, n);
@@ -205,7 +205,8 @@ pq_status build_pw_mode(const pq_mode_desc& m, std::vector<double>& x, std::vect
         set_error("projected Weylets need xmax > xmin and mass > 0");
         return PQ_EINVAL;
     }
-    sine_dvr(n, m.xmin, m.xmax, m.mass, x, w, T);
+    if (m.dvr == PQ_FGH_DVR) fgh_dvr(n, m.xmin, m.xmax, m.mass, x, w, T);
+    else sine_dvr(n, m.xmin, m.xmax, m.mass, x, w, T);
     const double L = m.xmax - m.xmin, dx = L / nx, dp = M_PI / dx, alpha = dp / (2.0 * dx);
     const double shift = sqrt(M_PI / (8.0 * alpha)), amp = pow(8.0 * alpha / M_PI, 0.25);
     std::vector<double> Phi((size_t)n * n);
@@ -329,7 +330,8 @@ pq_status build_pvb_mode(const pq_mode_desc& m, std::vector<double>& x, std::vec
         set_error("pvB needs xmax > xmin and mass > 0");
         return PQ_EINVAL;
     }
-    sine_dvr(n, m.xmin, m.xmax, m.mass, x, w, T);
+    if (m.dvr == PQ_FGH_DVR) fgh_dvr(n, m.xmin, m.xmax, m.mass, x, w, T);
+    else sine_dvr(n, m.xmin, m.xmax, m.mass, x, w, T);
     const double L = m.xmax - m.xmin, dx = L / nx, dp = 2.0 * M_PI / dx, alpha = dp / (2.0 * dx);
     const double pmax = np_ * dp / 2.0, amp = pow(2.0 * alpha / M_PI, 0.25);
     G.assign((size_t)n * n * 2, 0.0);

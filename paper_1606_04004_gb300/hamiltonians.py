@@ -66,6 +66,11 @@ def modes_of(cfg):
     if cfg["basis"] == "fgh":
         return [dict(kind=FGH_DVR, n=cfg["n"][k], xmin=cfg["xmin"][k], xmax=cfg["xmax"][k],
                      mass=cfg["mass"]) for k in range(cfg["D"])]
+    if cfg["basis"] in ("pw", "pvb") and cfg.get("dvr") == "fgh":
+        kind = PW if cfg["basis"] == "pw" else PVB
+        return [dict(kind=kind, n=cfg["n"][k], xmin=cfg["xmin"][k], xmax=cfg["xmax"][k],
+                     mass=cfg["mass"], nx_lattice=cfg["nx_lattice"][k],
+                     np_lattice=cfg["np_lattice"][k], dvr=FGH_DVR) for k in range(cfg["D"])]
     if cfg["basis"] in ("pw", "pvb"):
         kind = PW if cfg["basis"] == "pw" else PVB
         return [dict(kind=kind, n=cfg["n"], xmin=cfg["xmin"], xmax=cfg["xmax"], mass=cfg["mass"],
@@ -84,7 +89,7 @@ def build_model(cfg, omegas=None, lam=None):
     from . import Basis
     b = Basis(modes_of(cfg))
     grids = [b.grid(k)[0] for k in range(b.D)]
-    if cfg["basis"] == "fgh":
+    if "dw_coef" in cfg:
         terms = double_well_terms(grids, *cfg["dw_coef"])
     elif cfg["basis"] in ("sine", "pw", "pvb"):
         terms = coupled_morse_terms(grids, cfg["morse_D"], cfg["morse_a"], cfg["morse_qe"],

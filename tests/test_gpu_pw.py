@@ -106,3 +106,24 @@ def test_pw_propagation_fp64(name, D, n, nx, np_, nsteps):
     np.testing.assert_array_equal(A, r["A"])
     assert np.linalg.norm(psi - r["a"]) <= 1e-10 * np.linalg.norm(r["a"])
     assert np.max(np.abs(o["C"] - np.array([x["C"] for x in r["obs"]]))) < 1e-10
+
+
+def test_pw_double_well_propagation_fp64():
+    # the double well of Sec. 3.2 in projected Weylets on its FGH grids
+    # (165 and 81 functions per mode: point-parallel passes): identical active
+    # sets on the (15 x 11) x (9 x 9) phase-space lattice, C(t) within 1e-10
+    from oracle import propagate
+    pq = lib()
+    cfg = W.DWELL2D_PW
+    n = 30
+    b = pq.build_model(cfg)
+    prob = propagate.problem_from_config(cfg)
+    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], cfg["K"], cfg["dt"], n)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP64)
+    s.propagate(cfg["K"], cfg["dt"], cfg["theta"], n)
+    o = s.observables()
+    np.testing.assert_array_equal(o["n_active"], [x["n_active"] for x in r["obs"]])
+    A, psi = s.read()
+    np.testing.assert_array_equal(A, r["A"])
+    assert np.linalg.norm(psi - r["a"]) <= 1e-10 * np.linalg.norm(r["a"])
+    assert np.max(np.abs(o["C"] - np.array([x["C"] for x in r["obs"]]))) < 1e-10

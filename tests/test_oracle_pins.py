@@ -546,6 +546,21 @@ def test_pw_theta0_matches_dvr_dynamics():
         assert abs(o1["E"] - o2["E"]) < 1e-10 * abs(o2["E"])
 
 
+def test_pw_on_fgh_theta0_matches_fgh_dynamics():
+    # Sec. 3.2 builds the projected Weylets on the FGH grid; at 100 % basis
+    # they reproduce the FGH DVR dynamics of the double well (small grids).
+    cfg = W.scaled(W.DWELL2D, n=(20, 12))
+    pcfg = W.scaled(W.DWELL2D_PW, n=(20, 12), nx_lattice=(5, 4), np_lattice=(4, 3))
+    dv = propagate.problem_from_config(cfg)
+    pw = propagate.problem_from_config(pcfg)
+    args = (cfg["q0"], cfg["p0"], cfg["width"], 0.0, cfg["K"], cfg["dt"], 8)
+    r1, r2 = propagate.run(pw, *args), propagate.run(dv, *args)
+    assert r1["obs"][0]["n_active"] == 240
+    for o1, o2 in zip(r1["obs"], r2["obs"]):
+        assert abs(o1["C"] - o2["C"]) < 1e-10
+        assert abs(o1["E"] - o2["E"]) < 1e-10 * abs(o2["E"])
+
+
 # ------------------------------------------------------------------- pvB
 
 def test_pvb_cg_solves_overlap():
