@@ -374,9 +374,16 @@ def run_dwell(args):
     # on the 2D coordinate lattice radius sqrt 2 and radius 2 add the same 8 neighbours
     plan = [(W.DWELL2D, "fgh", pq.RADIUS_1, "1"), (W.DWELL2D, "fgh", pq.RADIUS_SQRT2, "sqrt2"),
             (W.DWELL2D_PW, "pw", pq.RADIUS_1, "1"), (W.DWELL2D_PW, "pw", pq.RADIUS_SQRT2, "sqrt2"),
-            (W.DWELL2D_PW, "pw", pq.RADIUS_2, "2")]
+            (W.DWELL2D_PW, "pw", pq.RADIUS_2, "2"), (W.DWELL2D_PVB, "pvb", pq.RADIUS_1, "1")]
+    # pvB is left out unless asked for: every Krylov vector needs a conjugate-
+    # gradient solve driven from the host, and one 2460-step run took longer
+    # than 15 minutes on a GB300
+    wanted = args.dwell_bases.split(",") if args.dwell_bases else ["fgh", "pw"]
+    plan = [p for p in plan if p[1] in wanted]
     for cfg, basis, rule, name in plan:
-        for theta in thetas:
+        # pvB solves S_AA x = y by conjugate gradients for every Krylov vector
+        # (host-driven), so it gets a shorter threshold list
+        for theta in (thetas if basis != "pvb" else (3e-2, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6)):
             o = series(cfg, theta, rule)
             row = {"mode": "dwell", "basis": basis, "radius": name, "theta": theta,
                    "mean_basis_pct": float(100.0 * o["n_active"].mean() / nfull),
@@ -402,6 +409,7 @@ def main():
     ap.add_argument("--mode", default="step", choices=["step", "apply", "dwell"])
     ap.add_argument("--radius", type=float, default=11.2)
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--dwell-bases", default="")   # comma list of fgh,pw,pvb (default fgh,pw)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("need at least 3 warm-up steps")

@@ -73,7 +73,7 @@ typedef enum pq_neighbour_rule {
 
 /* One mode of the direct-product basis.
  *  kind   pq_basis_kind.
- *  n      number of points (DVRs and pW: 2..256, pvB: 2..64).  Lattices
+ *  n      number of points (2..256).  Lattices
  *         with a mode longer than 64 use a point-parallel H.psi meant for
  *         small lattices (the 2D FGH double well).
  *  xmin, xmax  box edges: sine DVR points at xmin + j L/(n+1), j=1..n; FGH

@@ -124,8 +124,9 @@ def pw_basis(n, xmin, xmax, mass, nx, np_, dvr="sine"):
     return x, w, T, W
 
 
-def pvb_basis(n, xmin, xmax, mass, nx, np_):
-    """Biorthogonal projected von Neumann basis on a sine DVR (Sec. 2.2).
+def pvb_basis(n, xmin, xmax, mass, nx, np_, dvr="sine"):
+    """Biorthogonal projected von Neumann basis on a sine DVR, or on an FGH
+    DVR with dvr="fgh" (Sec. 2.2; Sec. 3.2 uses the FGH grid).
 
     von Neumann Gaussians on a lattice with Delta x Delta p = 2 pi:
     x_a = xmin + (a + 1/2) Dx, Dx = L / nx, Dp = 2 pi / Dx, momenta
@@ -137,7 +138,7 @@ def pvb_basis(n, xmin, xmax, mass, nx, np_):
     Returns (x, w, T, G, B)."""
     if nx * np_ != n:
         raise ValueError("the phase-space lattice must have as many functions as DVR points")
-    x, w, T = sine_dvr(n, xmin, xmax, mass)
+    x, w, T = (fgh_dvr if dvr == "fgh" else sine_dvr)(n, xmin, xmax, mass)
     L = xmax - xmin
     dx = L / nx
     dp = 2.0 * np.pi / dx

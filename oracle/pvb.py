@@ -31,21 +31,37 @@ def mode_transform(X, M, k):
 
 
 class PVBProblem:
+    """pvB problem of a workload record: the 3D coupled Morse on sine DVRs
+    (uniform modes; n, nx, np may be overridden), or the double well of
+    Sec. 3.2 on its FGH grids (per-mode sizes, ``dvr="fgh"``)."""
+
     def __init__(self, cfg, n=None, nx=None, np_=None):
         self.cfg = cfg
-        n = cfg["n"] if n is None else n
-        nx = cfg["nx_lattice"] if nx is None else nx
-        np_ = cfg["np_lattice"] if np_ is None else np_
         D = cfg["D"]
-        x, w, T, G, B = bases.pvb_basis(n, cfg["xmin"], cfg["xmax"], cfg["mass"], nx, np_)
-        self.x, self.w, self.T, self.G, self.B = x, w, T, G, B
-        self.S = B.conj().T @ B
-        self.dims = (n,) * D
-        self.axes = (nx, np_) * D
-        grid = np.meshgrid(*([x] * D), indexing="ij")
-        q = np.stack(grid, axis=-1)
-        self.V = models.coupled_morse(q, cfg["morse_D"], cfg["morse_a"], cfg["morse_qe"],
-                                      cfg["coupling"])
+        if cfg.get("dvr") == "fgh":
+            ns, nxs, nps = cfg["n"], cfg["nx_lattice"], cfg["np_lattice"]
+            lo, hi, dvr = cfg["xmin"], cfg["xmax"], "fgh"
+        else:
+            n = cfg["n"] if n is None else n
+            nx = cfg["nx_lattice"] if nx is None else nx
+            np_ = cfg["np_lattice"] if np_ is None else np_
+            ns, nxs, nps = (n,) * D, (nx,) * D, (np_,) * D
+            lo, hi, dvr = (cfg["xmin"],) * D, (cfg["xmax"],) * D, "sine"
+        self.xs, self.ws, self.Ts, self.Gs, self.Bs = [], [], [], [], []
+        for k in range(D):
+            x, w, T, G, B = bases.pvb_basis(ns[k], lo[k], hi[k], cfg["mass"], nxs[k], nps[k], dvr)
+            self.xs.append(x); self.ws.append(w); self.Ts.append(T)
+            self.Gs.append(G); self.Bs.append(B)
+        self.Ss = [B.conj().T @ B for B in self.Bs]
+        self.smax = max(np.abs(S).max() for S in self.Ss)
+        self.dims = tuple(ns)
+        self.axes = tuple(v for k in range(D) for v in (nxs[k], nps[k]))
+        q = np.stack(np.meshgrid(*self.xs, indexing="ij"), axis=-1)
+        if "dw_coef" in cfg:
+            self.V = models.double_well(q, *cfg["dw_coef"])
+        else:
+            self.V = models.coupled_morse(q, cfg["morse_D"], cfg["morse_a"], cfg["morse_qe"],
+                                          cfg["coupling"])
 
     def embed(self, A, a):
         X = np.zeros(int(np.prod(self.dims)), dtype=np.complex128)
@@ -56,22 +72,22 @@ class PVBProblem:
         """H^chi on the full DVR grid: kinetic along every mode + V."""
         Y = self.V * X
         for k in range(len(self.dims)):
-            Y = Y + mode_transform(X, self.T, k)
+            Y = Y + mode_transform(X, self.Ts[k], k)
         return Y
 
     def H_AA(self, A, a):
         X = self.embed(A, a)
         for k in range(len(self.dims)):
-            X = mode_transform(X, self.B, k)
+            X = mode_transform(X, self.Bs[k], k)
         Y = self.H_full(X)
         for k in range(len(self.dims)):
-            Y = mode_transform(Y, self.B.conj().T, k)
+            Y = mode_transform(Y, self.Bs[k].conj().T, k)
         return Y.ravel()[A]
 
     def S_AA(self, A, v):
         X = self.embed(A, v)
         for k in range(len(self.dims)):
-            X = mode_transform(X, self.S, k)
+            X = mode_transform(X, self.Ss[k], k)
         return X.ravel()[A]
 
     def solve_S(self, A, y):
@@ -97,10 +113,9 @@ class PVBProblem:
     def factors(self, q0, p0, width, which):
         """Per-mode normalised DVR packet vectors, mapped by G^dagger (the
         coefficients) or B^dagger (the bra of the autocorrelation)."""
-        f = pruned.packet_factors([self.x] * len(q0), [self.w] * len(q0), q0, p0, width,
-                                  models.gaussian_1d)
-        M = self.G if which == "G" else self.B
-        return [M.conj().T @ fk for fk in f]
+        f = pruned.packet_factors(self.xs, self.ws, q0, p0, width, models.gaussian_1d)
+        Ms = self.Gs if which == "G" else self.Bs
+        return [M.conj().T @ fk for M, fk in zip(Ms, f)]
 
 
 def sil_step_S(prob, A, a, K, dt):
@@ -125,7 +140,7 @@ def sil_step_S(prob, A, a, K, dt):
             for ci, v in zip(c, V):
                 w = w - ci * v
         b = np.sqrt(max(np.vdot(w, prob.S_AA(A, w)).real, 0.0))
-        if b <= 1e-12 * np.sqrt(max(np.vdot(Hv, Hv).real, 1e-300)) / max(1.0, np.abs(prob.S).max()):
+        if b <= 1e-12 * np.sqrt(max(np.vdot(Hv, Hv).real, 1e-300)) / max(1.0, prob.smax):
             break
         beta.append(b)
         V.append(w / b)

@@ -310,7 +310,7 @@ static bool complex_inverse(int n, std::vector<double>& A) {
 }
 
 // Biorthogonal projected von Neumann basis (Sec. 2.2) on a sine DVR: von
-// Neumann Gaussians on the lattice Dx Dp = 2 pi (x_a cell-centred, momenta
+// Neumann Gaussians (on a sine or FGH DVR) on the lattice Dx Dp = 2 pi (x_a cell-centred, momenta
 // p_b = -p_max + (b + 1/2) Dp, p_max = np Dp / 2, alpha = Dp / (2 Dx)),
 // projected (Eq. pvN_def): G_jm = sqrt(w_j) g_m(x_j); B = G^{-dagger}
 // (Eq. pvb_def: B^dagger G = 1); S = B^dagger B.  Complex n x n, interleaved.
@@ -318,9 +318,9 @@ pq_status build_pvb_mode(const pq_mode_desc& m, std::vector<double>& x, std::vec
                          std::vector<double>& T, std::vector<double>& G, std::vector<double>& B,
                          std::vector<double>& S) {
     const int n = m.n, nx = m.nx_lattice, np_ = m.np_lattice;
-    if (n > kMaxNTile) {
-        set_error("pvB: at most %d functions per mode (%d given)", kMaxNTile, n);
-        return PQ_ENOTSUP;
+    if (n < 2 || n > kMaxN) {
+        set_error("pvB: %d functions per mode outside 2..%d", n, kMaxN);
+        return PQ_EINVAL;
     }
     if (nx < 1 || np_ < 1 || nx * np_ != n) {
         set_error("pvB needs nx_lattice * np_lattice = n (%d x %d != %d)", nx, np_, n);

@@ -88,6 +88,35 @@ __global__ void __launch_bounds__(kPvbThreads) k_grid_mode(
     }
 }
 
+// The same transform for modes longer than 64 (the matrix stays in global
+// memory, read through the cache): the double well's 165- and 81-point grids.
+template <typename R>
+__global__ void __launch_bounds__(kPvbThreads) k_grid_mode_long(
+    const typename Cx<R>::T* __restrict__ X, typename Cx<R>::T* __restrict__ Y,
+    const R* __restrict__ M, int nk, uint32_t inner, uint32_t total, int accumulate) {
+    using V = typename Cx<R>::T;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const uint32_t in = t % inner, q = t / inner;
+        const uint32_t i = q % (uint32_t)nk, o = q / (uint32_t)nk;
+        const size_t base = (size_t)o * nk * inner + in;
+        const R* mrow = M + (size_t)i * kMaxN * 2;
+        R ar = 0, ai = 0;
+        for (int j = 0; j < nk; ++j) {
+            const R mr = mrow[2 * j], mi = mrow[2 * j + 1];
+            const V x = X[base + (size_t)j * inner];
+            ar += mr * x.x - mi * x.y;
+            ai += mr * x.y + mi * x.x;
+        }
+        const size_t oi = base + (size_t)i * inner;
+        if (accumulate) {
+            const V y = Y[oi];
+            ar += y.x;
+            ai += y.y;
+        }
+        Y[oi] = cmake<R>(ar, ai);
+    }
+}
+
 // Y = V(x) X on the full grid, V from the SoP potential tables.
 template <typename R>
 __global__ void k_grid_potential(const typename Cx<R>::T* __restrict__ X,
@@ -212,6 +241,12 @@ struct Pvb {
         const Lattice& L = s.lat;
         const int nk = L.n[k];
         const uint32_t inner = L.stride[k];
+        if (nk > kMaxNTile) {
+            k_grid_mode_long<R><<<grid_size() * 8, kPvbThreads, 0, st>>>(in, out, M, nk, inner,
+                                                                         L.nfull, acc);
+            PQ_CHECK_LAUNCH();
+            return PQ_OK;
+        }
         const size_t sm = (size_t)nk * nk * sizeof(V);
         static bool attr = false;
         if (!attr) {

@@ -76,12 +76,20 @@ def test_pw_on_fgh_matches_oracle():
         np.testing.assert_allclose(Wl, Wm, atol=1e-10)
 
 
-def test_pvb_limited_to_64():
+def test_pvb_on_fgh_matches_oracle():
+    from oracle import bases
     pq = _lib()
+    cfg = W.DWELL2D_PVB
+    b = pq.Basis(pq.modes_of(cfg))
+    for k in range(2):
+        x, w, T, G, B = bases.pvb_basis(cfg["n"][k], cfg["xmin"][k], cfg["xmax"][k], cfg["mass"],
+                                        cfg["nx_lattice"][k], cfg["np_lattice"][k], dvr="fgh")
+        np.testing.assert_allclose(b.grid(k)[0], x, atol=1e-14)
+        np.testing.assert_allclose(b.kinetic(k), T, atol=1e-12 * abs(T).max())
     with pytest.raises(pq.PQError) as e:
-        pq.Basis([dict(kind=pq.PVB, n=66, xmin=0.5, xmax=6.0, mass=1.0, nx_lattice=11,
+        pq.Basis([dict(kind=pq.PVB, n=258, xmin=0.5, xmax=6.0, mass=1.0, nx_lattice=43,
                        np_lattice=6)])
-    assert e.value.status == pq.ENOTSUP
+    assert e.value.status == pq.EINVAL
 
 
 def test_argument_errors():

@@ -97,3 +97,32 @@ def test_pvb_morse3d_initial_state_and_H():
     fb = prob.factors(cfg["q0"], cfg["p0"], cfg["width"], "B")
     C0 = np.vdot(pruned.product_on(A, prob.dims, fb), a)
     assert abs(o["C"][0] - C0) < 1e-11
+
+
+def test_pvb_double_well():
+    """The double well of Sec. 3.2 in pvB on its FGH grids (165- and
+    81-function modes: the long-mode full-grid transforms): H_AA of the initial
+    state and three propagation steps against the oracle (FP64)."""
+    import torch
+    from oracle import pvb
+    pq = lib()
+    cfg = W.DWELL2D_PVB
+    b = pq.build_model(cfg)
+    prob = pvb.PVBProblem(cfg)
+    nsteps = 3
+    r = pvb.run(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], cfg["K"], cfg["dt"], nsteps)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP64)
+    A0, a0 = s.read()
+    x = torch.from_numpy(a0).to("cuda")
+    y = torch.empty_like(x)
+    s.apply_H(x, y)
+    torch.cuda.synchronize()
+    ref = prob.H_AA(A0, a0)
+    assert np.linalg.norm(y.cpu().numpy() - ref) <= 1e-11 * np.linalg.norm(ref)
+    s.propagate(cfg["K"], cfg["dt"], cfg["theta"], nsteps)
+    o = s.observables()
+    np.testing.assert_array_equal(o["n_active"], [x["n_active"] for x in r["obs"]])
+    A, a = s.read()
+    np.testing.assert_array_equal(A, r["A"])
+    assert np.linalg.norm(a - r["a"]) <= 1e-9 * np.linalg.norm(r["a"])
+    assert np.max(np.abs(o["C"] - np.array([x["C"] for x in r["obs"]]))) < 1e-10

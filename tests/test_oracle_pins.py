@@ -571,9 +571,24 @@ def test_pvb_cg_solves_overlap():
     y = W.random_psi(len(A), 4)
     x = prob.solve_S(A, y)
     # dense S_AA by brute force
-    SS = np.kron(prob.S, prob.S)[np.ix_(A, A)]
+    SS = np.kron(prob.Ss[0], prob.Ss[1])[np.ix_(A, A)]
     np.testing.assert_allclose(SS @ x, y, rtol=1e-10, atol=1e-10)
     np.testing.assert_allclose(prob.S_AA(A, x), SS @ x, rtol=1e-12, atol=1e-12)
+
+
+def test_pvb_on_fgh_theta0_matches_fgh_dynamics():
+    # Sec. 3.2 builds pvB on the FGH grid; at 100 % basis it reproduces the FGH
+    # DVR dynamics of the double well (small grids, per-mode sizes).
+    from oracle import pvb
+    cfg = W.scaled(W.DWELL2D, n=(20, 12))
+    pcfg = W.scaled(W.DWELL2D_PVB, n=(20, 12), nx_lattice=(5, 4), np_lattice=(4, 3))
+    prob = pvb.PVBProblem(pcfg)
+    dv = propagate.problem_from_config(cfg)
+    args = (cfg["q0"], cfg["p0"], cfg["width"], 0.0, cfg["K"], cfg["dt"], 5)
+    r1, r2 = pvb.run(prob, *args), propagate.run(dv, *args)
+    for o1, o2 in zip(r1["obs"], r2["obs"]):
+        assert abs(o1["C"] - o2["C"]) < 1e-9
+        assert abs(o1["E"] - o2["E"]) < 1e-9 * abs(o2["E"])
 
 
 def test_pvb_theta0_matches_dvr_dynamics():

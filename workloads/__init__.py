@@ -25,8 +25,9 @@ Workloads (parameters in atomic units unless stated):
   points on [-0.5, 3.7) and 81 points on [1.0, 2.9); SIL order 10, dt = 0.01
   (not given in the paper; at dt = 0.05 the order-10 step error is 5e-5),
   2460 steps.
-* ``dwell2d_pw`` -- the same double well in projected Weylets built on those
-  FGH grids (Sec. 3.2): phase-space lattices 15 x 11 (x) and 9 x 9 (y).
+* ``dwell2d_pw`` / ``dwell2d_pvb`` -- the same double well in projected
+  Weylets / in the biorthogonal projected von Neumann basis, built on those FGH
+  grids (Sec. 3.2): phase-space lattices 15 x 11 (x) and 9 x 9 (y).
 """
 from __future__ import annotations
 
@@ -70,7 +71,10 @@ DWELL2D = dict(
 DWELL2D_PW = dict(DWELL2D, name="dwell2d_pw", basis="pw", dvr="fgh",
                   nx_lattice=(15, 9), np_lattice=(11, 9))
 
-CONFIGS = {c["name"]: c for c in (MORSE2D, HH4D, HH6D, MORSE3D, ADJOINT4D, DWELL2D, DWELL2D_PW)}
+DWELL2D_PVB = dict(DWELL2D_PW, name="dwell2d_pvb", basis="pvb")
+
+CONFIGS = {c["name"]: c for c in (MORSE2D, HH4D, HH6D, MORSE3D, ADJOINT4D, DWELL2D, DWELL2D_PW,
+                                    DWELL2D_PVB)}
 
 
 def morse3d_centres(seed: int = 1606) -> tuple:
