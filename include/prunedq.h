@@ -223,7 +223,14 @@ typedef struct pq_prop_desc {
     int radius;      /* neighbour rule of the adaption (pq_neighbour_rule)    */
     int reorth;      /* 1 = full re-orthogonalisation, 0 = three-term         */
     double rel_excl; /* relative exclusion threshold of the adaption (0: none) */
+    int integrator;  /* pq_integrator: PQ_SIL (order K) or PQ_RK4             */
 } pq_prop_desc;
+
+/* Time steppers of pq_propagate.  PQ_RK4 is the classical fourth-order
+ * Runge-Kutta step (four H.psi per step; not in the paper, whose propagator
+ * is SIL, Sec. 3.1); it is not norm-conserving and needs dt ||H|| < 2.8.
+ * Not provided for pvB states or by pq_survival_grad (PQ_ENOTSUP). */
+typedef enum pq_integrator { PQ_SIL = 0, PQ_RK4 = 1 } pq_integrator;
 
 pq_status pq_propagate(pq_state* state, const pq_prop_desc* desc, int nsteps, void* stream);
 

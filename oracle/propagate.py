@@ -163,11 +163,12 @@ def observables(prob, A, psi, factors, theta, vd=None):
 
 
 def run(prob, q0, p0, width, theta, K, dt, nsteps, radius=1,
-        record_sets=False, state=None, rel_excl=0.0):
+        record_sets=False, state=None, rel_excl=0.0, integrator="sil"):
     """Propagate ``nsteps`` steps.  Returns a dict with per-step observables
     (index 0 = t = 0 after the initial prune), the final (A, a) and, when
     asked, the active set after each step.  ``radius`` is the neighbour rule
-    and ``rel_excl`` the relative exclusion threshold of the adaption."""
+    and ``rel_excl`` the relative exclusion threshold of the adaption;
+    ``integrator`` is "sil" (order K) or "rk4"."""
     if state is None:
         A, a, f = initial_state(prob, q0, p0, width, theta, radius)
     else:
@@ -176,7 +177,10 @@ def run(prob, q0, p0, width, theta, K, dt, nsteps, radius=1,
     sets = [A.copy()] if record_sets else None
     for _ in range(nsteps):
         vd = prob.vdiag(A)
-        a = sil.sil_step(a, lambda v: prob.apply(A, v, vd), K, dt)
+        if integrator == "rk4":
+            a = sil.rk4_step(a, lambda v: prob.apply(A, v, vd), dt)
+        else:
+            a = sil.sil_step(a, lambda v: prob.apply(A, v, vd), K, dt)
         A, a = pruned.prune(A, a, prob.axes, theta, radius, rel_excl)
         obs.append(observables(prob, A, a, f, theta))
         if record_sets:

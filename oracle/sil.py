@@ -63,3 +63,16 @@ def sil_step(psi, apply, K, dt, return_info=False):
     if return_info:
         return out, dict(alpha=alpha, beta=beta, K=len(alpha))
     return out
+
+
+def rk4_step(psi, apply, dt):
+    """One classical fourth-order Runge-Kutta step of i da/dt = H a (the
+    alternative integrator to SIL; not in the paper):
+    k1 = -i H a, k2 = -i H (a + dt/2 k1), k3 = -i H (a + dt/2 k2),
+    k4 = -i H (a + dt k3), a' = a + dt/6 (k1 + 2 k2 + 2 k3 + k4)."""
+    a = np.asarray(psi, dtype=np.complex128)
+    k1 = -1j * apply(a)
+    k2 = -1j * apply(a + 0.5 * dt * k1)
+    k3 = -1j * apply(a + 0.5 * dt * k2)
+    k4 = -1j * apply(a + dt * k3)
+    return a + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)

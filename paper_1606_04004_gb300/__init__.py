@@ -29,6 +29,7 @@ OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, ENUMERIC, ETIMEOUT, EBREAKDOWN, ENOTSUP = 
 SINE_DVR, HO_DVR, PVB, PW, FGH_DVR = range(5)
 FP64, FP32MIX = 0, 1
 RADIUS_1, RADIUS_SQRT2, RADIUS_2 = 1, 2, 3   # neighbour rules of the adaption
+SIL, RK4 = 0, 1                                # integrators of propagate
 FACTOR_IDENTITY, FACTOR_KINETIC, FACTOR_DIAG = range(3)
 _STATUS = {0: "PQ_OK", 1: "PQ_EINVAL", 2: "PQ_ENOMEM", 3: "PQ_ECUDA", 4: "PQ_ECAPACITY",
            5: "PQ_ENUMERIC", 6: "PQ_ETIMEOUT", 7: "PQ_EBREAKDOWN", 8: "PQ_ENOTSUP"}
@@ -57,7 +58,7 @@ class SopTerm(C.Structure):
 
 class PropDesc(C.Structure):
     _fields_ = [("K", C.c_int), ("dt", C.c_double), ("theta", C.c_double), ("radius", C.c_int),
-                ("reorth", C.c_int), ("rel_excl", C.c_double)]
+                ("reorth", C.c_int), ("rel_excl", C.c_double), ("integrator", C.c_int)]
 
 
 class Observables(C.Structure):
@@ -285,8 +286,10 @@ class State:
         _check(_lib.pq_prune(self._h, float(theta), int(radius), float(rel_excl),
                              _vp(stream or 0)))
 
-    def propagate(self, K, dt, theta, nsteps, reorth=1, radius=1, rel_excl=0.0, stream=None):
-        d = PropDesc(int(K), float(dt), float(theta), int(radius), int(reorth), float(rel_excl))
+    def propagate(self, K, dt, theta, nsteps, reorth=1, radius=1, rel_excl=0.0, integrator=0,
+                  stream=None):
+        d = PropDesc(int(K), float(dt), float(theta), int(radius), int(reorth), float(rel_excl),
+                     int(integrator))
         _check(_lib.pq_propagate(self._h, C.byref(d), int(nsteps), _vp(stream or 0)))
 
     def observables(self) -> dict:

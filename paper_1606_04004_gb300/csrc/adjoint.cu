@@ -189,6 +189,10 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
         pq_status nrc = check_neighbour_rule(s.lat, d.radius);
         if (nrc) return nrc;
     }
+    if (d.integrator != PQ_SIL) {
+        set_error("the adjoint gradient provides SIL only");
+        return PQ_ENOTSUP;
+    }
     // ---- parameter tables
     std::vector<double> tab, coef;
     std::vector<int> toff(1, 0), pot_idx, cen_idx, cen_mode;

@@ -14,6 +14,8 @@
 // block sums them in block order.
 #include <math.h>
 
+#include <algorithm>
+
 #include "device_util.cuh"
 
 namespace pq {
@@ -581,6 +583,106 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
     return PQ_OK;
 }
 
+// ------------------------------------------------------------------ RK4
+// Classical fourth-order Runge-Kutta step of i da/dt = H a (an alternative to
+// SIL; not in the paper): k_s = -i H y_s with y_1 = a, y_2 = a + dt/2 k_1,
+// y_3 = a + dt/2 k_2, y_4 = a + dt k_3; a' = a + dt/6 (k_1 + 2 k_2 + 2 k_3 + k_4).
+// Buffers: Krylov slots 0 (next stage input), 1 (H y), 2 (accumulated a').
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_rk4_energy(const typename Cx<R>::T* __restrict__ a,
+                                                             const typename Cx<R>::T* __restrict__ Ha,
+                                                             const int64_t* na, int64_t cap,
+                                                             double* partials) {
+    const int64_t n = min(*na, cap);
+    Acc<R> e, nn;
+    e.init();
+    nn.init();
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const auto x = a[p], y = Ha[p];
+        e.add(x.x * y.x + x.y * y.y);
+        nn.add(x.x * x.x + x.y * x.y);
+    }
+    const double vals[2] = {e.value(), nn.value()};
+    block_partials<2>(vals, partials);
+}
+
+__global__ void k_rk4_energy_done(const double* partials, int G, double* E) {
+    __shared__ double tot[2];
+    sum_partials(partials, G, 2, tot);
+    __syncthreads();
+    if (threadIdx.x == 0 && E) *E = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
+}
+
+// stage 0: acc = a + c_acc t, next = a + c_next t;  stages 1, 2: acc += c_acc t,
+// next = a + c_next t;  stage 3: a = acc + c_acc t;  t = -i H y.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_rk4_stage(typename Cx<R>::T* a,
+                                                            const typename Cx<R>::T* __restrict__ Hy,
+                                                            typename Cx<R>::T* next,
+                                                            typename Cx<R>::T* acc, const int64_t* na,
+                                                            int64_t cap, R c_acc, R c_next,
+                                                            int stage) {
+    using V = typename Cx<R>::T;
+    const int64_t n = min(*na, cap);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const V h = Hy[p];
+        const V t = cmake<R>(h.y, -h.x);   // -i (h.x + i h.y)
+        if (stage == 3) {
+            const V c = acc[p];
+            a[p] = cmake<R>(c.x + c_acc * t.x, c.y + c_acc * t.y);
+            continue;
+        }
+        const V x = a[p];
+        V c = stage == 0 ? x : acc[p];
+        c.x += c_acc * t.x;
+        c.y += c_acc * t.y;
+        acc[p] = c;
+        next[p] = cmake<R>(x.x + c_next * t.x, x.y + c_next * t.y);
+    }
+}
+
+template <typename R>
+static pq_status rk4_step(State& s, const pq_prop_desc& d, double* prev_E, cudaStream_t st) {
+    using V = typename Cx<R>::T;
+    const int G = red_blocks();
+    const size_t cap = s.cap;
+    V* next = (V*)s.V;
+    V* Hy = (V*)s.V + cap;
+    V* acc = (V*)s.V + 2 * cap;
+    const R dt = (R)d.dt;
+    const R c_acc[4] = {dt / 6, dt / 3, dt / 3, dt / 6};
+    const R c_next[4] = {dt / 2, dt / 2, dt, 0};
+    for (int stage = 0; stage < 4; ++stage) {
+        const void* in = stage == 0 ? s.psi : (const void*)next;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (s.timing.enabled) {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, st);
+        }
+        pq_status rc = apply_H_launch(s, in, Hy, s.prec, nullptr, nullptr, 0, st);
+        if (rc) return rc;
+        if (s.timing.enabled) {
+            cudaEventRecord(e1, st);
+            s.timing.ev_start.push_back(e0);
+            s.timing.ev_stop.push_back(e1);
+        }
+        if (stage == 0) {   // E of the state at the start of the step
+            k_rk4_energy<R><<<G, kRedThreads, 0, st>>>((const V*)s.psi, Hy, s.cnt + CNT_NA,
+                                                       (int64_t)cap, s.red_tmp);
+            PQ_CHECK_LAUNCH();
+            k_rk4_energy_done<<<1, 256, 0, st>>>(s.red_tmp, G, prev_E);
+            PQ_CHECK_LAUNCH();
+        }
+        k_rk4_stage<R><<<G, kRedThreads, 0, st>>>((V*)s.psi, Hy, next, acc, s.cnt + CNT_NA,
+                                                  (int64_t)cap, c_acc[stage], c_next[stage], stage);
+        PQ_CHECK_LAUNCH();
+    }
+    return PQ_OK;
+}
+
 pq_status ensure_krylov(State& s, int K) {
     if (s.V_K >= K) return PQ_OK;
     if (s.V) cudaFree(s.V);
@@ -611,9 +713,14 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
         set_error("need dt > 0, theta >= 0, nsteps >= 0");
         return PQ_EINVAL;
     }
+    if (d.integrator != PQ_SIL && d.integrator != PQ_RK4) {
+        set_error("unknown integrator %d (0: SIL, 1: RK4)", d.integrator);
+        return PQ_EINVAL;
+    }
+    const bool rk4 = d.integrator == PQ_RK4;
     pq_status erc = check_neighbour_rule(s.lat, d.radius);
     if (erc) return erc;
-    erc = ensure_krylov(s, d.K);
+    erc = ensure_krylov(s, rk4 ? std::max(d.K, 3) : d.K);
     if (erc) return erc;
     if (nsteps == 0) return PQ_OK;
     double* recs = nullptr;
@@ -623,7 +730,10 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
     pq_status rc = PQ_OK;
     for (int n = 0; n < nsteps && rc == PQ_OK; ++n) {
         double* prevE = recs + (size_t)n * 8 + 4;
-        rc = s.prec == PQ_FP64 ? sil_step<double>(s, d, prevE, st) : sil_step<float>(s, d, prevE, st);
+        if (rk4)
+            rc = s.prec == PQ_FP64 ? rk4_step<double>(s, d, prevE, st) : rk4_step<float>(s, d, prevE, st);
+        else
+            rc = s.prec == PQ_FP64 ? sil_step<double>(s, d, prevE, st) : sil_step<float>(s, d, prevE, st);
         if (rc) break;
         rc = prune_launch(s, d.theta, d.radius, d.rel_excl, st);
         if (rc) break;
@@ -668,7 +778,7 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
         const size_t base = s.obs.size() - nsteps;
         for (int n = 0; n < nsteps; ++n) {
             const double na_before = (double)s.obs[base + n - 1].n_active;
-            s.timing.coef += na_before * d.K;
+            s.timing.coef += na_before * (rk4 ? 4 : d.K);
         }
         s.timing.ev_start.clear();
         s.timing.ev_stop.clear();

@@ -485,6 +485,10 @@ pq_status pvb_observe_current(State& s, double theta, cudaStream_t st) {
 }
 
 pq_status pvb_propagate(State& s, const pq_prop_desc& d, int nsteps, cudaStream_t st) {
+    if (d.integrator != PQ_SIL) {
+        set_error("pvB propagation provides SIL only");
+        return PQ_ENOTSUP;
+    }
     pq_status rc = ensure_krylov(s, d.K);
     if (rc) return rc;
     const double tol = s.prec == PQ_FP64 ? 1e-13 : 1e-6;

@@ -150,3 +150,31 @@ def test_double_well_steps(prec):
         assert np.linalg.norm(psi - r["a"]) <= 1e-10 * np.linalg.norm(r["a"])
     else:
         assert np.max(np.abs(o["C"] - _series(r, "C"))) < 1e-5
+
+
+@pytest.mark.parametrize("name,dt,n,prec", [("morse2d", 2.0, 20, 0), ("hh4d", 0.01, 10, 0),
+                                            ("hh4d", 0.01, 10, 1)])
+def test_rk4_matches_oracle(name, dt, n, prec):
+    # the fourth-order Runge-Kutta stepper (not in the paper; the alternative
+    # integrator): FP64 identical active sets and C(t) within 1e-10 of the
+    # oracle's RK4, FP32-mix within 1e-5
+    from oracle import propagate
+    pq = lib()
+    cfg = W.CONFIGS[name]
+    prob = propagate.problem_from_config(cfg)
+    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], cfg["K"], dt, n,
+                      integrator="rk4")
+    b = pq.build_model(cfg)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=prec)
+    s.propagate(cfg["K"], dt, cfg["theta"], n, integrator=pq.RK4)
+    o = s.observables()
+    C = _series(r, "C")
+    if prec == 0:
+        np.testing.assert_array_equal(o["n_active"], _series(r, "n_active"))
+        assert np.max(np.abs(o["C"] - C)) < 1e-10
+        E = _series(r, "E")
+        assert np.max(np.abs(o["energy"] - E)) < 1e-10 * np.abs(E).max()
+        A, psi = s.read()
+        np.testing.assert_array_equal(A, r["A"])
+    else:
+        assert np.max(np.abs(o["C"] - C)) < 1e-5

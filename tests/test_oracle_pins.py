@@ -300,6 +300,25 @@ def test_sil_full_krylov_is_exact_exponential():
         np.testing.assert_allclose(out, ref, rtol=1e-11, atol=1e-11)
 
 
+def test_rk4_is_fourth_order():
+    # against the exact exponential: the one-step error falls as dt^5 and the
+    # error over a fixed time as dt^4 (catches a wrong stage weight or sign).
+    rng = np.random.default_rng(9)
+    n = 12
+    M = rng.standard_normal((n, n)); H = (M + M.T) / 2
+    psi = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    errs = []
+    for dt in (0.02, 0.01):
+        a = psi.copy()
+        for _ in range(int(round(0.4 / dt))):
+            a = sil.rk4_step(a, lambda v: H @ v, dt)
+        errs.append(np.linalg.norm(a - scipy.linalg.expm(-1j * H * 0.4) @ psi))
+    assert 14.0 < errs[0] / errs[1] < 18.0
+    one = [np.linalg.norm(sil.rk4_step(psi, lambda v: H @ v, dt)
+                          - scipy.linalg.expm(-1j * H * dt) @ psi) for dt in (0.02, 0.01)]
+    assert 28.0 < one[0] / one[1] < 36.0
+
+
 def test_sil_conserves_norm_and_energy():
     rng = np.random.default_rng(8)
     n = 40
