@@ -224,6 +224,9 @@ typedef struct pq_prop_desc {
     int reorth;      /* 1 = full re-orthogonalisation, 0 = three-term         */
     double rel_excl; /* relative exclusion threshold of the adaption (0: none) */
     int integrator;  /* pq_integrator: PQ_SIL (order K) or PQ_RK4             */
+    double sil_tol;  /* SIL only: > 0 makes the order error-controlled, up to K:
+                        a step stops after k + 1 vectors once
+                        beta_k |[exp(-i T_{k+1} dt) e_1]_k| <= sil_tol         */
 } pq_prop_desc;
 
 /* Time steppers of pq_propagate.  PQ_RK4 is the classical fourth-order

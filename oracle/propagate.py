@@ -163,12 +163,13 @@ def observables(prob, A, psi, factors, theta, vd=None):
 
 
 def run(prob, q0, p0, width, theta, K, dt, nsteps, radius=1,
-        record_sets=False, state=None, rel_excl=0.0, integrator="sil"):
+        record_sets=False, state=None, rel_excl=0.0, integrator="sil", sil_tol=0.0):
     """Propagate ``nsteps`` steps.  Returns a dict with per-step observables
     (index 0 = t = 0 after the initial prune), the final (A, a) and, when
     asked, the active set after each step.  ``radius`` is the neighbour rule
     and ``rel_excl`` the relative exclusion threshold of the adaption;
-    ``integrator`` is "sil" (order K) or "rk4"."""
+    ``integrator`` is "sil" (order K, error-controlled below K when
+    sil_tol > 0) or "rk4"."""
     if state is None:
         A, a, f = initial_state(prob, q0, p0, width, theta, radius)
     else:
@@ -180,7 +181,7 @@ def run(prob, q0, p0, width, theta, K, dt, nsteps, radius=1,
         if integrator == "rk4":
             a = sil.rk4_step(a, lambda v: prob.apply(A, v, vd), dt)
         else:
-            a = sil.sil_step(a, lambda v: prob.apply(A, v, vd), K, dt)
+            a = sil.sil_step(a, lambda v: prob.apply(A, v, vd), K, dt, tol=sil_tol)
         A, a = pruned.prune(A, a, prob.axes, theta, radius, rel_excl)
         obs.append(observables(prob, A, a, f, theta))
         if record_sets:

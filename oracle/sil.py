@@ -35,8 +35,13 @@ def tridiag_exp_e1(alpha, beta, dt):
     return Z @ (np.exp(-1j * lam * dt) * Z[0, :])
 
 
-def sil_step(psi, apply, K, dt, return_info=False):
-    """One SIL step of order K; ``apply(v)`` is the (pruned) H.v."""
+def sil_step(psi, apply, K, dt, return_info=False, tol=0.0):
+    """One SIL step of order K; ``apply(v)`` is the (pruned) H.v.  With
+    tol > 0 the order is error-controlled (the adaptive-order reading of
+    Sec. 3.1's Arnoldi): after Lanczos step k the estimate
+    beta_k |[exp(-i T_{k+1} dt) e_1]_k| of the relative error of stopping
+    with k + 1 vectors is formed, and the step stops once it is <= tol
+    (K stays the maximum)."""
     psi = np.asarray(psi, dtype=np.complex128)
     beta0 = np.linalg.norm(psi)
     if beta0 == 0.0 or len(psi) == 0:
@@ -57,6 +62,11 @@ def sil_step(psi, apply, K, dt, return_info=False):
         if b <= BREAKDOWN_REL * hn:
             break
         beta.append(float(b))
+        if tol > 0.0:
+            ck = tridiag_exp_e1(alpha, beta, dt)[k]
+            if b * abs(ck) <= tol:
+                beta.pop()
+                break
         V.append(w / b)
     c = tridiag_exp_e1(alpha, beta, dt)
     out = beta0 * sum(ci * v for ci, v in zip(c, V))

@@ -58,7 +58,8 @@ class SopTerm(C.Structure):
 
 class PropDesc(C.Structure):
     _fields_ = [("K", C.c_int), ("dt", C.c_double), ("theta", C.c_double), ("radius", C.c_int),
-                ("reorth", C.c_int), ("rel_excl", C.c_double), ("integrator", C.c_int)]
+                ("reorth", C.c_int), ("rel_excl", C.c_double), ("integrator", C.c_int),
+                ("sil_tol", C.c_double)]
 
 
 class Observables(C.Structure):
@@ -287,9 +288,9 @@ class State:
                              _vp(stream or 0)))
 
     def propagate(self, K, dt, theta, nsteps, reorth=1, radius=1, rel_excl=0.0, integrator=0,
-                  stream=None):
+                  sil_tol=0.0, stream=None):
         d = PropDesc(int(K), float(dt), float(theta), int(radius), int(reorth), float(rel_excl),
-                     int(integrator))
+                     int(integrator), float(sil_tol))
         _check(_lib.pq_propagate(self._h, C.byref(d), int(nsteps), _vp(stream or 0)))
 
     def observables(self) -> dict:

@@ -189,8 +189,10 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
         pq_status nrc = check_neighbour_rule(s.lat, d.radius);
         if (nrc) return nrc;
     }
-    if (d.integrator != PQ_SIL) {
-        set_error("the adjoint gradient provides SIL only");
+    if (d.integrator != PQ_SIL || d.sil_tol != 0.0) {
+        // an error-controlled order makes each step depend on the state: the
+        // forward map is then not linear on the frozen sets
+        set_error("the adjoint gradient provides fixed-order SIL only");
         return PQ_ENOTSUP;
     }
     // ---- parameter tables

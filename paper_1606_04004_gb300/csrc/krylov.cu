@@ -314,11 +314,12 @@ constexpr double kChebR = 2000.0;
 constexpr int kChebN = 2304;   // > kChebR + 16 kChebR^(1/3) + 40
 constexpr int kChebSub = 64;
 
-__global__ void __launch_bounds__(32) k_tridiag_exp(KrylovScalars* ks, double dt, int64_t* err) {
-    __shared__ double J[kChebN + 2];
-    const int n = ks->keff;
-    const int r = threadIdx.x;
-    if (n <= 0) return;
+// Lane r < n receives [exp(-i T_n dt) e_1]_r for the leading n x n block of
+// the Lanczos tridiagonal; false when g |dt| exceeds the sub-step limit.
+// Every lane of the warp must call it (shuffles); J: kChebN + 2 shared doubles.
+__device__ bool tridiag_exp_lanes(const KrylovScalars* ks, int n, double dt, double* J,
+                                  double& out_re, double& out_im) {
+    const int r = threadIdx.x & 31;
     const bool on = r < n;
     const double al = on ? ks->alpha[r] : 0.0;
     const double bu0 = (on && r + 1 < n) ? ks->beta[r] : 0.0;            // T[r][r+1]
@@ -335,14 +336,9 @@ __global__ void __launch_bounds__(32) k_tridiag_exp(KrylovScalars* ks, double dt
     for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
     const double Rtot = g * fabs(dt);
     double vr = r == 0 ? 1.0 : 0.0, vi = 0.0;
-    if (!(Rtot <= kChebR * kChebSub)) {   // also NaN
-        if (r == 0) *err |= 2;
-        if (on) {
-            ks->coef[2 * r] = 0.0;
-            ks->coef[2 * r + 1] = 0.0;
-        }
-        return;
-    }
+    out_re = 0.0;
+    out_im = 0.0;
+    if (!(Rtot <= kChebR * kChebSub)) return false;   // also NaN
     if (Rtot > 1e-300) {
         const int nsub = (int)ceil(Rtot / kChebR);
         const double R = Rtot / nsub;
@@ -403,13 +399,39 @@ __global__ void __launch_bounds__(32) k_tridiag_exp(KrylovScalars* ks, double dt
             vi = ai;
         }
     }
-    if (on) {
-        double sn, cs;
-        sincos(-mu * dt, &sn, &cs);   // exp(-i mu dt)
-        const double fb = ks->beta0 * ks->sigma[r];
-        ks->coef[2 * r] = (cs * vr - sn * vi) * fb;
-        ks->coef[2 * r + 1] = (cs * vi + sn * vr) * fb;
+    double sn, cs;
+    sincos(-mu * dt, &sn, &cs);   // exp(-i mu dt)
+    out_re = cs * vr - sn * vi;
+    out_im = cs * vi + sn * vr;
+    return true;
+}
+
+__global__ void __launch_bounds__(32) k_tridiag_exp(KrylovScalars* ks, double dt, int64_t* err) {
+    __shared__ double J[kChebN + 2];
+    const int n = ks->keff;
+    const int r = threadIdx.x;
+    if (n <= 0) return;
+    double vr, vi;
+    const bool ok = tridiag_exp_lanes(ks, n, dt, J, vr, vi);
+    if (!ok && r == 0) *err |= 2;
+    if (r < n) {
+        const double f = ok ? ks->beta0 * ks->sigma[r] : 0.0;
+        ks->coef[2 * r] = vr * f;
+        ks->coef[2 * r + 1] = vi * f;
     }
+}
+
+// Error-controlled Krylov order: after Lanczos step k (beta_k known), the
+// estimate beta_k |[exp(-i T_{k+1} dt) e_1]_k| of the relative error of the
+// order-(k+1) step; at or below tol the step stops at k + 1 vectors.
+__global__ void __launch_bounds__(32) k_sil_errcheck(KrylovScalars* ks, int k, double dt,
+                                                     double tol) {
+    __shared__ double J[kChebN + 2];
+    if (ks->keff <= k + 1) return;   // already stopped
+    double vr, vi;
+    const bool ok = tridiag_exp_lanes(ks, k + 1, dt, J, vr, vi);
+    const double ck = __shfl_sync(0xffffffffu, sqrt(vr * vr + vi * vi), k);
+    if (threadIdx.x == 0 && ok && ks->beta[k] * ck <= tol) ks->keff = k + 1;
 }
 
 // psi <- sum_{j < keff} coef_j V_j  (V_0 is psi itself: read before write).
@@ -575,6 +597,10 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
         }
         k_update_done<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks, k, s.cnt + CNT_ERR);
         PQ_CHECK_LAUNCH();
+        if (d.sil_tol > 0.0) {
+            k_sil_errcheck<<<1, 32, 0, st>>>(s.ks, k, d.dt, d.sil_tol);
+            PQ_CHECK_LAUNCH();
+        }
     }
     k_tridiag_exp<<<1, 32, 0, st>>>(s.ks, d.dt, s.cnt + CNT_ERR);
     PQ_CHECK_LAUNCH();
@@ -718,6 +744,10 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
         return PQ_EINVAL;
     }
     const bool rk4 = d.integrator == PQ_RK4;
+    if (!(d.sil_tol >= 0) || !std::isfinite(d.sil_tol)) {
+        set_error("sil_tol must be finite and >= 0");
+        return PQ_EINVAL;
+    }
     pq_status erc = check_neighbour_rule(s.lat, d.radius);
     if (erc) return erc;
     erc = ensure_krylov(s, rk4 ? std::max(d.K, 3) : d.K);

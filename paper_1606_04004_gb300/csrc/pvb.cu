@@ -485,8 +485,8 @@ pq_status pvb_observe_current(State& s, double theta, cudaStream_t st) {
 }
 
 pq_status pvb_propagate(State& s, const pq_prop_desc& d, int nsteps, cudaStream_t st) {
-    if (d.integrator != PQ_SIL) {
-        set_error("pvB propagation provides SIL only");
+    if (d.integrator != PQ_SIL || d.sil_tol != 0.0) {
+        set_error("pvB propagation provides fixed-order SIL only");
         return PQ_ENOTSUP;
     }
     pq_status rc = ensure_krylov(s, d.K);

@@ -178,3 +178,22 @@ def test_rk4_matches_oracle(name, dt, n, prec):
         np.testing.assert_array_equal(A, r["A"])
     else:
         assert np.max(np.abs(o["C"] - C)) < 1e-5
+
+
+@pytest.mark.parametrize("tol", [1e-8, 1e-12])
+def test_sil_error_control_matches_oracle(tol):
+    # error-controlled SIL order (K = 16 at most): identical active sets and
+    # C(t) within 1e-10 of the oracle's error-controlled SIL (FP64)
+    from oracle import propagate
+    pq = lib()
+    cfg = W.HH4D
+    n = 10
+    prob = propagate.problem_from_config(cfg)
+    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], 16, cfg["dt"], n,
+                      sil_tol=tol)
+    b = pq.build_model(cfg)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP64)
+    s.propagate(16, cfg["dt"], cfg["theta"], n, sil_tol=tol)
+    o = s.observables()
+    np.testing.assert_array_equal(o["n_active"], _series(r, "n_active"))
+    assert np.max(np.abs(o["C"] - _series(r, "C"))) < 1e-10

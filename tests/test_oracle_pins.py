@@ -319,6 +319,24 @@ def test_rk4_is_fourth_order():
     assert 28.0 < one[0] / one[1] < 36.0
 
 
+def test_sil_error_control_meets_tolerance():
+    # error-controlled order: the step stops early and its error against the
+    # exact exponential stays at the level of the requested tolerance, while
+    # tol = 0 keeps the full order (catches an estimate taken at the wrong index)
+    rng = np.random.default_rng(10)
+    n = 60
+    M = rng.standard_normal((n, n)); H = (M + M.T) / 2
+    psi = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    psi /= np.linalg.norm(psi)
+    ref = scipy.linalg.expm(-1j * H * 0.05) @ psi
+    for tol in (1e-6, 1e-10):
+        out, info = sil.sil_step(psi, lambda v: H @ v, 30, 0.05, return_info=True, tol=tol)
+        assert info["K"] < 30
+        assert np.linalg.norm(out - ref) < 10 * tol
+    _, info = sil.sil_step(psi, lambda v: H @ v, 30, 0.05, return_info=True)
+    assert info["K"] == 30
+
+
 def test_sil_conserves_norm_and_energy():
     rng = np.random.default_rng(8)
     n = 40
