@@ -1423,12 +1423,19 @@ static size_t smem_inner_ep(int n2, int nl) {
 // of A, so the global loads and stores of an item touch consecutive addresses.
 
 constexpr int kQWarps = kApplyThreads / 32;
-// Last-mode points per work item (build-time; 4, 6 or 8).  On the 6D 24^6 ellipsoid
-// (9.97e6 points) one H.psi took 749 us with 4, 717 us with 6 and 1082 us with 8.
-#ifndef PQ_QW
-#define PQ_QW 6
+// Last-mode points per work item (build-time; 4, 6 or 8), for the inner and
+// the outer passes.  On the 6D 24^6 ellipsoid (9.97e6 points) one H.psi took
+// 749 us with 4 / 4, 717 us with 6 / 6 and 1082 us with 8 / 8; under ncu the
+// inner pass ran 213 us with 4 and 231 us with 6 (its larger code waits for
+// instructions), the outer passes 131 us with 4 and 119 us with 6.
+#ifndef PQ_QW_INNER
+#define PQ_QW_INNER 4
 #endif
-constexpr int kQW = PQ_QW;
+#ifndef PQ_QW_OUTER
+#define PQ_QW_OUTER 6
+#endif
+constexpr int kQWInner = PQ_QW_INNER;
+constexpr int kQWOuter = PQ_QW_OUTER;
 
 struct __align__(16) QuadMeta {   // per warp, per fibre
     uint32_t rst[32];           // first position in A of compact row u
@@ -1948,17 +1955,17 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         const int n2 = L.n[L.D - 2], nl = L.nlast;
         const int nboth = s.nterms - (s.ngroup[0] + s.ngroup[1] + s.ngroup[2]);
         if (sizeof(R) == 4 && n2 <= 32 && nl <= 32 &&
-            smem_inner_q<R, kQW>(n2, nl, nboth) <= kSmemBudget) {
+            smem_inner_q<R, kQWInner>(n2, nl, nboth) <= kSmemBudget) {
             static bool q_attr[2] = {false, false};
             if (!q_attr[pi]) {
-                PQ_CUDA_TRY(cudaFuncSetAttribute(k_inner_q<R, kQW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                PQ_CUDA_TRY(cudaFuncSetAttribute(k_inner_q<R, kQWInner>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kSmemBudget));
                 q_attr[pi] = true;
             }
-            const size_t sm = smem_inner_q<R, kQW>(n2, nl, nboth);
+            const size_t sm = smem_inner_q<R, kQWInner>(n2, nl, nboth);
             int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inner_q<R, kQW>, kApplyThreads, sm);
-            k_inner_q<R, kQW><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inner_q<R, kQWInner>, kApplyThreads, sm);
+            k_inner_q<R, kQWInner><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
             PQ_CHECK_LAUNCH();
         } else if (n2 <= 32 && nl <= 32 && smem_inner_ep<R>(n2, nl) <= kSmemBudget) {
             static bool ep_attr[2] = {false, false};
@@ -2003,17 +2010,17 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         int wpb = kApplyThreads / 32;
         const int nk = L.n[k];
         if (sizeof(R) == 4 && L.nlast <= 32 && nk <= 32 &&
-            smem_outer_q<R, kQW>(nk, L.nlast) <= kSmemBudget) {
+            smem_outer_q<R, kQWOuter>(nk, L.nlast) <= kSmemBudget) {
             static bool q_attr[2] = {false, false};
             if (!q_attr[pi]) {
-                PQ_CUDA_TRY(cudaFuncSetAttribute(k_outer_q<R, kQW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                PQ_CUDA_TRY(cudaFuncSetAttribute(k_outer_q<R, kQWOuter>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kSmemBudget));
                 q_attr[pi] = true;
             }
-            const size_t sm = smem_outer_q<R, kQW>(nk, L.nlast);
+            const size_t sm = smem_outer_q<R, kQWOuter>(nk, L.nlast);
             int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_outer_q<R, kQW>, kApplyThreads, sm);
-            k_outer_q<R, kQW><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_outer_q<R, kQWOuter>, kApplyThreads, sm);
+            k_outer_q<R, kQWOuter><<<G * (per_sm > 0 ? per_sm : 1), kApplyThreads, sm, st>>>(a);
             PQ_CHECK_LAUNCH();
             continue;
         }
