@@ -53,6 +53,16 @@ __device__ __forceinline__ void bit_set(uint64_t* bits, uint32_t b) {
     atomicOr(reinterpret_cast<unsigned long long*>(bits + (b >> 6)), 1ull << (b & 63));
 }
 
+// bit_set for a bitmap that only gains bits while it is being marked: a plain
+// read first skips the atomic when the bit is already set (a stale read only
+// costs the atomic it would have done anyway).
+__device__ __forceinline__ void bit_mark(uint64_t* bits, uint32_t b) {
+    const uint64_t m = 1ull << (b & 63);
+    uint64_t* w = bits + (b >> 6);
+    if (!(*reinterpret_cast<volatile uint64_t*>(w) & m))
+        atomicOr(reinterpret_cast<unsigned long long*>(w), m);
+}
+
 // Bounds checks of the self-checking build (-DPQ_BOUNDS_CHECK): the first
 // out-of-range index is recorded in cnt[CNT_FAULT..+2] and the access is
 // skipped.  In the normal build the check compiles to `true`.

@@ -285,13 +285,13 @@ pq_status rebuild_from_bits(State& s, bool remap, cudaStream_t st) {
 // number of axes (3^k - 1).  Neighbours outside the lattice are dropped.
 __device__ __forceinline__ void mark_with_neighbours(uint64_t* bits, uint32_t key,
                                                      const Lattice& L, int rule) {
-    bit_set(bits, key);
+    bit_mark(bits, key);
     int dg[2 * kMaxD];
     for (int a = 0; a < L.naxes; ++a) dg[a] = (int)((key / L.axis_stride[a]) % (uint32_t)L.axis_n[a]);
     for (int a = 0; a < L.naxes; ++a) {
         const uint32_t sa = L.axis_stride[a];
-        if (dg[a] > 0) bit_set(bits, key - sa);
-        if (dg[a] + 1 < L.axis_n[a]) bit_set(bits, key + sa);
+        if (dg[a] > 0) bit_mark(bits, key - sa);
+        if (dg[a] + 1 < L.axis_n[a]) bit_mark(bits, key + sa);
     }
     if (rule == PQ_RADIUS_SQRT2) {
         for (int a = 0; a < L.naxes; ++a)
@@ -300,7 +300,7 @@ __device__ __forceinline__ void mark_with_neighbours(uint64_t* bits, uint32_t ke
                     for (int sb = -1; sb <= 1; sb += 2) {
                         const int da = dg[a] + sa, db = dg[b] + sb;
                         if (da < 0 || da >= L.axis_n[a] || db < 0 || db >= L.axis_n[b]) continue;
-                        bit_set(bits, key + (uint32_t)(sa * (int64_t)L.axis_stride[a] +
+                        bit_mark(bits, key + (uint32_t)(sa * (int64_t)L.axis_stride[a] +
                                                        sb * (int64_t)L.axis_stride[b]));
                     }
     } else if (rule == PQ_RADIUS_2) {
@@ -320,7 +320,7 @@ __device__ __forceinline__ void mark_with_neighbours(uint64_t* bits, uint32_t ke
                     delta += o * (int64_t)L.axis_stride[a];
                 }
             }
-            if (ok && moved >= 2) bit_set(bits, (uint32_t)((int64_t)key + delta));
+            if (ok && moved >= 2) bit_mark(bits, (uint32_t)((int64_t)key + delta));
             int a = 0;   // next offset
             while (a < L.naxes && c[a] == 2) c[a++] = 0;
             if (a == L.naxes) break;
