@@ -123,6 +123,20 @@ def _dist():
     return ws, rank, local
 
 
+def aggregate_replicas(ms, coef, dist, device):
+    """Replica aggregation of the timed region: the slowest rank's time and the
+    coefficients all ranks applied (value = their ratio).  dist is
+    torch.distributed or None (one process)."""
+    if dist is None:
+        return ms, coef
+    import torch
+    t = torch.tensor([ms, coef], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def oracle_sample_rate(cfg, A, psi, n_sample, seed=0):
     """The FP64 oracle's pruned H.psi on n_sample output points of (A, psi):
     returns (coefficients per second, seconds, sample size)."""
@@ -209,14 +223,7 @@ def run_ours(args, cfg):
     na = obs["n_active"]
     coef = float(np.sum(na[n_before - 1:n_before - 1 + args.steps])) * K
     tm = s.timing()
-    if dist:
-        t = torch.tensor([ms, coef], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max, coef_all = float(tmax[0]), float(t[1])
-    else:
-        ms_max, coef_all = ms, coef
+    ms_max, coef_all = aggregate_replicas(ms, coef, dist, "cuda")
     value = coef_all / (ms_max * 1e-3) / 1e9
 
     # roofline of the pruned H.psi (all passes), timed with CUDA events on
