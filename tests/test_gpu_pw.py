@@ -127,3 +127,54 @@ def test_pw_double_well_propagation_fp64():
     np.testing.assert_array_equal(A, r["A"])
     assert np.linalg.norm(psi - r["a"]) <= 1e-10 * np.linalg.norm(r["a"])
     assert np.max(np.abs(o["C"] - np.array([x["C"] for x in r["obs"]]))) < 1e-10
+
+
+def _mixed_problem():
+    """Mode 0 in projected Weylets (16 = 4 x 4 on a sine DVR), mode 1 a plain
+    sine DVR (16 points): the library basis and the oracle's problem."""
+    from oracle import bases, propagate
+    pq = lib()
+    cfg = W.MORSE3D
+    n, lo, hi, m = 16, cfg["xmin"], cfg["xmax"], cfg["mass"]
+    b = pq.Basis([dict(kind=pq.PW, n=n, xmin=lo, xmax=hi, mass=m, nx_lattice=4, np_lattice=4),
+                  dict(kind=pq.SINE_DVR, n=n, xmin=lo, xmax=hi, mass=m)])
+    grids = [b.grid(k)[0] for k in range(2)]
+    b.set_sop(pq.coupled_morse_terms(grids, cfg["morse_D"], cfg["morse_a"], cfg["morse_qe"],
+                                     cfg["coupling"]))
+    x, w, T, Wm = bases.pw_basis(n, lo, hi, m, 4, 4)
+    terms = propagate.morse_sop_terms([x, x], cfg["morse_D"], cfg["morse_a"], cfg["morse_qe"],
+                                      cfg["coupling"])
+    prob = propagate.PWProblem([x, x], [w, w], [T, T], [Wm, np.eye(n)], [(4, 4), (n,)], terms)
+    return b, prob
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mixed_pw_and_dvr_modes(prec):
+    # a pW mode next to a DVR mode (SoP factors of the DVR mode used as they
+    # are): H.psi parity on a random set, then 5 propagation steps with
+    # identical active sets on the mixed lattice (axes 4, 4, 16)
+    import torch
+    from oracle import propagate, pruned
+    pq = lib()
+    b, prob = _mixed_problem()
+    dims = (16, 16)
+    A = W.random_active_set(dims, 0.5, seed=21)
+    psi = W.random_psi(len(A), 22).astype(np.complex128 if prec == 0 else np.complex64)
+    s = _state_with(b, A, psi, prec)
+    x = torch.from_numpy(psi).to("cuda")
+    y = torch.empty_like(x)
+    s.apply_H(x, y)
+    torch.cuda.synchronize()
+    ref = prob.apply(A, psi.astype(np.complex128))
+    absterms = [(abs(c), {k: np.abs(h) for k, h in f.items()}) for c, f in prob.terms]
+    bound = pruned.apply_H_sop(A, np.abs(psi).astype(np.complex128), dims, absterms).real
+    tol = 1e-12 if prec == 0 else 2e-5
+    assert np.all(np.abs(y.cpu().numpy() - ref) <= tol * bound + 1e-300)
+    if prec == 0:
+        q0, p0, wd = (2.2, 2.35), (0.0, 0.0), (0.2, 0.2)
+        r = propagate.run(prob, q0, p0, wd, 1e-6, 10, 10.0, 5)
+        s2 = pq.State(b, q0, p0, wd, 1e-6, precision=pq.FP64)
+        s2.propagate(10, 10.0, 1e-6, 5)
+        o = s2.observables()
+        np.testing.assert_array_equal(o["n_active"], [v["n_active"] for v in r["obs"]])
+        assert np.max(np.abs(o["C"] - np.array([v["C"] for v in r["obs"]]))) < 1e-10
