@@ -143,6 +143,14 @@ typedef struct pq_sop_term {
 
 pq_status pq_set_sop(pq_basis* basis, const pq_sop_term* terms, int nterms);
 
+/* A diagonal potential given as a table over the whole lattice (not in SoP
+ * form; Sec. 2.1: in a DVR the potential is diagonal, V_II = V(x_I)), added to
+ * the SoP potential: n values, row-major over the modes (the last mode
+ * fastest), copied.  States created afterwards use it.  V = NULL removes it.
+ * Errors: PQ_EINVAL (n is not the lattice size, a value not finite),
+ * PQ_ENOTSUP (pW or pvB bases). */
+pq_status pq_set_potential_grid(pq_basis* basis, const double* V, int64_t n);
+
 /* Create a state holding a product Gaussian packet
  *   psi(q) = prod_k (2 pi w_k^2)^(-1/4) exp(-(q_k-q0_k)^2/(4 w_k^2) + i p0_k (q_k-q0_k))
  * projected on the DVR (a_I = prod_k sqrt(w_{i_k}) psi_k(x_{i_k}), each mode

@@ -95,6 +95,7 @@ _SIGS = {
     "pq_apply_H": [_vp, _vp, _vp, C.c_int, _vp],
     "pq_apply_H_host": [_vp, _vp, _vp, C.c_int, _vp],
     "pq_prune": [_vp, C.c_double, C.c_int, C.c_double, _vp],
+    "pq_set_potential_grid": [_vp, _vp, C.c_int64],
     "pq_propagate": [_vp, C.POINTER(PropDesc), C.c_int, _vp],
     "pq_observables_get": [_vp, C.POINTER(Observables)],
     "pq_set_timing": [_vp, C.c_int],
@@ -175,6 +176,16 @@ class Basis:
         Wm = np.zeros((n, n))
         _check(_lib.pq_basis_transform(self._h, mode, _dptr(Wm)))
         return Wm
+
+    def set_potential_grid(self, V):
+        """A tabulated diagonal potential over the whole lattice (array of the
+        lattice's shape or flat, row-major), added to the SoP potential;
+        None removes it (pq_set_potential_grid)."""
+        if V is None:
+            _check(_lib.pq_set_potential_grid(self._h, None, 0))
+            return
+        v = np.ascontiguousarray(np.asarray(V, dtype=np.float64).ravel())
+        _check(_lib.pq_set_potential_grid(self._h, _dptr(v), int(v.size)))
 
     def set_sop(self, terms):
         """terms: list of (coef, [factor per mode]) with factor None (identity),

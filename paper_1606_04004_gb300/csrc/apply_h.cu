@@ -2067,6 +2067,41 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
     return PQ_OK;
 }
 
+// out_I += V_grid(I) in_I for a tabulated (non-SoP) diagonal potential
+// (Sec. 2.1: the DVR potential is diagonal): one thread per active point.
+template <typename R>
+__global__ void k_add_grid_potential(const uint32_t* __restrict__ keys, const int64_t* na,
+                                     int64_t cap, const R* __restrict__ vgrid,
+                                     const typename Cx<R>::T* __restrict__ in,
+                                     typename Cx<R>::T* out, const double* in_scale,
+                                     const int* skip, int skip_k) {
+    using V = typename Cx<R>::T;
+    if (skip && *skip <= skip_k) return;
+    const int64_t n = min(*na, cap);
+    const R scale = in_scale ? (R)(*in_scale) : (R)1;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const R v = vgrid[keys[p]] * scale;
+        const V x = in[p];
+        V o = out[p];
+        o.x += v * x.x;
+        o.y += v * x.y;
+        out[p] = o;
+    }
+}
+
+template <typename R>
+static pq_status add_grid_potential(const State& s, const void* in, void* out,
+                                    const double* in_scale, const int* skip, int skip_k,
+                                    cudaStream_t st) {
+    k_add_grid_potential<R><<<grid_size() * 8, 256, 0, st>>>(
+        s.keys, s.cnt + CNT_NA, (int64_t)s.cap,
+        sizeof(R) == 8 ? (const R*)s.vgrid64 : (const R*)s.vgrid32,
+        (const typename Cx<R>::T*)in, (typename Cx<R>::T*)out, in_scale, skip, skip_k);
+    PQ_CHECK_LAUNCH();
+    return PQ_OK;
+}
+
 pq_status apply_H_launch(const State& s, const void* in, void* out, int prec,
                          const double* in_scale, const int* skip, int skip_k, cudaStream_t st) {
     if (s.pvb) {   // H_AA on the full grid (pvb.cu); called only from the C ABI
@@ -2076,8 +2111,16 @@ pq_status apply_H_launch(const State& s, const void* in, void* out, int prec,
         }
         return pvb_apply(const_cast<State&>(s), in, out, prec, st);
     }
-    if (prec == PQ_FP64) return launch_all<double>(s, in, out, in_scale, skip, skip_k, st);
-    if (prec == PQ_FP32MIX) return launch_all<float>(s, in, out, in_scale, skip, skip_k, st);
+    if (prec == PQ_FP64) {
+        pq_status rc = launch_all<double>(s, in, out, in_scale, skip, skip_k, st);
+        if (rc || !s.vgrid64) return rc;
+        return add_grid_potential<double>(s, in, out, in_scale, skip, skip_k, st);
+    }
+    if (prec == PQ_FP32MIX) {
+        pq_status rc = launch_all<float>(s, in, out, in_scale, skip, skip_k, st);
+        if (rc || !s.vgrid32) return rc;
+        return add_grid_potential<float>(s, in, out, in_scale, skip, skip_k, st);
+    }
     set_error("unknown precision %d", prec);
     return PQ_EINVAL;
 }

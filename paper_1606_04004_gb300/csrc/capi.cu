@@ -34,6 +34,8 @@ static void free_state(State* s) {
         for (void* p : pv)
             if (p) cudaFree(p);
     }
+    if (s->vgrid64) cudaFree(s->vgrid64);
+    if (s->vgrid32) cudaFree(s->vgrid32);
     if (s->gmat64) cudaFree(s->gmat64);
     if (s->gmat32) cudaFree(s->gmat32);
     if (s->gtmp) cudaFree(s->gtmp);
@@ -328,6 +330,16 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
         free_state(s);
         return rc;
     }
+    if (!basis->vgrid.empty()) {   // tabulated diagonal potential (DVR bases only)
+        const size_t nv = basis->vgrid.size();
+        std::vector<float> v32(basis->vgrid.begin(), basis->vgrid.end());
+        if ((rc = dalloc(&s->vgrid64, nv * 8)) || (rc = dalloc(&s->vgrid32, nv * 4))) {
+            free_state(s);
+            return rc;
+        }
+        cudaMemcpy(s->vgrid64, basis->vgrid.data(), nv * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(s->vgrid32, v32.data(), nv * 4, cudaMemcpyHostToDevice);
+    }
     *out = s;
     return PQ_OK;
 }
@@ -450,6 +462,37 @@ PQ_API pq_status pq_basis_transform(const pq_basis* basis_, int mode, double* Wo
             for (int j = 0; j < n; ++j) Wout[(size_t)i * n + j] = i == j ? 1.0 : 0.0;
     else
         memcpy(Wout, b->W[mode].data(), (size_t)n * n * sizeof(double));
+    return PQ_OK;
+}
+
+PQ_API pq_status pq_set_potential_grid(pq_basis* basis_, const double* V, int64_t n) {
+    clear_error();
+    Basis* b = reinterpret_cast<Basis*>(basis_);
+    if (!b) {
+        set_error("null basis");
+        return PQ_EINVAL;
+    }
+    if (b->generic || b->pvb) {
+        set_error("a tabulated potential is provided for DVR bases only");
+        return PQ_ENOTSUP;
+    }
+    if (!V) {
+        b->vgrid.clear();
+        return PQ_OK;
+    }
+    double full = 1;
+    for (int k = 0; k < b->D_user; ++k) full *= b->modes[k].n;
+    if ((double)n != full) {
+        set_error("tabulated potential of %lld values for a lattice of %.0f points", (long long)n,
+                  full);
+        return PQ_EINVAL;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(V[i])) {
+            set_error("tabulated potential value %lld is not finite", (long long)i);
+            return PQ_EINVAL;
+        }
+    b->vgrid.assign(V, V + n);
     return PQ_OK;
 }
 

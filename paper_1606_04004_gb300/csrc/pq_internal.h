@@ -102,6 +102,8 @@ struct Basis {
         std::vector<std::vector<double>> values;
     };
     std::vector<GTerm> gterms;
+    // tabulated diagonal potential on the whole lattice (empty: none)
+    std::vector<double> vgrid;
 };
 
 pq_status build_dvr_mode(const pq_mode_desc& m, std::vector<double>& x,
@@ -190,6 +192,7 @@ struct State {
     // Hamiltonian tables (device), both precisions
     double* T64 = nullptr;  float* T32 = nullptr;      // [D][kMaxN][kMaxN]
     double* pot64 = nullptr; float* pot32 = nullptr;   // [nterms][D][kMaxN]
+    double* vgrid64 = nullptr; float* vgrid32 = nullptr;   // tabulated V on the lattice, or null
     int nterms = 0;
     int ngroup[4] = {0, 0, 0, 0};  // potential terms by the tile modes they touch (see apply_h.cu)
     // generic SoP (phase-space bases): dense 1D matrices and the pass plan

@@ -92,6 +92,24 @@ def test_pvb_on_fgh_matches_oracle():
     assert e.value.status == pq.EINVAL
 
 
+def test_tabulated_potential_errors():
+    pq = _lib()
+    b = pq.Basis(pq.modes_of(W.MORSE2D))
+    with pytest.raises(pq.PQError) as e:
+        b.set_potential_grid(np.zeros(31 * 32))
+    assert e.value.status == pq.EINVAL
+    with pytest.raises(pq.PQError) as e:
+        b.set_potential_grid(np.full(32 * 32, np.nan))
+    assert e.value.status == pq.EINVAL
+    b.set_potential_grid(np.zeros((32, 32)))
+    b.set_potential_grid(None)
+    cfg = W.scaled(W.MORSE3D, D=2, n=16, nx_lattice=4, np_lattice=4)
+    bw = pq.Basis(pq.modes_of(cfg))
+    with pytest.raises(pq.PQError) as e:
+        bw.set_potential_grid(np.zeros(16 * 16))
+    assert e.value.status == pq.ENOTSUP
+
+
 def test_argument_errors():
     pq = _lib()
     with pytest.raises(pq.PQError) as e:

@@ -138,3 +138,49 @@ BIG = [((165, 81), 0.3), ((70, 9), 0.5), ((100, 3, 5), 0.4), ((9, 130), 0.5), ((
 def test_apply_long_modes(dims, frac, prec):
     A = W.random_active_set(dims, frac, seed=len(dims) * 3 + int(frac * 10))
     _run(dims, A, 7, prec, problem=fgh_problem, tol={0: 1e-13, 1: 1e-5})
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_tabulated_potential(prec):
+    # a diagonal potential given as a table over the lattice (not SoP),
+    # added to the SoP part: parity with the oracle on a random set
+    import torch
+    from oracle import pruned
+    pq = lib()
+    dims = (7, 6, 5)
+    b, Ts, pot = ho_problem(dims, 11)
+    rng = np.random.default_rng(12)
+    Vg = rng.uniform(-1, 1, int(np.prod(dims)))
+    b.set_potential_grid(Vg.reshape(dims))
+    A = W.random_active_set(dims, 0.5, seed=13)
+    psi = W.random_psi(len(A), 14).astype(np.complex128 if prec == 0 else np.complex64)
+    s = state_with(b, A, psi, prec)
+    x = torch.from_numpy(psi).to("cuda")
+    y = torch.empty_like(x)
+    s.apply_H(x, y)
+    torch.cuda.synchronize()
+    vd = vdiag_of(pot, A, dims) + Vg[A]
+    ref = pruned.apply_H(A, psi.astype(np.complex128), dims, Ts, vd)
+    bound = rel_bound(Ts, A, psi, dims, vd)
+    err = np.abs(y.cpu().numpy().astype(np.complex128) - ref)
+    assert np.all(err <= TOL[prec] * bound + 1e-300), (err / np.maximum(bound, 1e-300)).max()
+
+
+def test_tabulated_coupling_reproduces_sop_run():
+    # the 2D Morse coupling 0.005 q1 q2 moved from the SoP form into a table:
+    # the propagation (FP64) gives the oracle's active sets and C(t)
+    from oracle import propagate
+    pq = lib()
+    cfg = W.MORSE2D
+    n = 20
+    prob = propagate.problem_from_config(cfg)
+    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], cfg["K"], cfg["dt"], n)
+    b = pq.Basis(pq.modes_of(cfg))
+    g = [b.grid(k)[0] for k in range(2)]
+    b.set_sop(pq.coupled_morse_terms(g, cfg["morse_D"], cfg["morse_a"], cfg["morse_qe"], 0.0))
+    b.set_potential_grid(cfg["coupling"] * np.outer(g[0], g[1]))
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP64)
+    s.propagate(cfg["K"], cfg["dt"], cfg["theta"], n)
+    o = s.observables()
+    np.testing.assert_array_equal(o["n_active"], [v["n_active"] for v in r["obs"]])
+    assert np.max(np.abs(o["C"] - np.array([v["C"] for v in r["obs"]]))) < 1e-10
