@@ -355,6 +355,48 @@ def run_apply(args, cfg):
                       "peak_kind": kind, "reps": args.reps}), flush=True)
 
 
+def run_snapshots(args, cfg):
+    """H.psi microbenchmark on the propagation's own active sets: the hh6d run
+    (FP32-mix) is stopped at the listed steps and the H.psi of its current
+    (A, psi) is timed there (median of --reps, L2 flushed between launches)."""
+    import torch
+    import paper_1606_04004_gb300 as pq
+    prec = pq.FP32MIX if args.precision == "fp32mix" else pq.FP64
+    b = pq.build_model(cfg)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=prec, capacity=0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    tdt = torch.complex64 if prec == pq.FP32MIX else torch.complex128
+    peak, kind = _peaks()
+    bpc = BYTES_PER_COEF[args.precision]
+    done = 0
+    for step in sorted(int(v) for v in args.snapshots.split(",")):
+        if step > done:
+            s.propagate(cfg["K"], cfg["dt"], cfg["theta"], step - done)
+            done = step
+        n = s.size()
+        x = torch.empty(n, dtype=tdt, device="cuda")
+        x.copy_(torch.from_numpy(s.read()[1]).to("cuda"))
+        y = torch.empty_like(x)
+        for _ in range(3):
+            s.apply_H(x, y)
+        times = []
+        for _ in range(args.reps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.apply_H(x, y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        med = statistics.median(times) * 1e-3
+        print(json.dumps({"mode": "snapshot", "workload": cfg["name"], "precision": args.precision,
+                          "step": step, "n_active": int(n), "median_us": med * 1e6,
+                          "gcoef_s": n / med / 1e9, "frac_hbm": n * bpc / med / 1e9 / peak,
+                          "peak": peak, "peak_kind": kind, "reps": args.reps}), flush=True)
+        del x, y
+
+
 def run_dwell(args):
     """Accuracy study on the paper's 2D double well (Sec. 3.2; the comparisons
     of its neighbour-radius and basis figures): the pruned FGH DVR and the
@@ -413,9 +455,10 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "apply", "dwell"])
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "dwell", "snapshot"])
     ap.add_argument("--radius", type=float, default=11.2)
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--snapshots", default="0,20,50,100")   # steps of --mode snapshot
     ap.add_argument("--dwell-bases", default="")   # comma list of fgh,pw,pvb (default fgh,pw)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -425,6 +468,8 @@ def main():
         run_apply(args, cfg)
     elif args.mode == "dwell":
         run_dwell(args)
+    elif args.mode == "snapshot":
+        run_snapshots(args, cfg)
     elif args.impl == "reference":
         run_reference(args, cfg)
     else:
