@@ -19,6 +19,15 @@
 //    per mode, so there are no races).
 // Zero-filled tiles give exactly the pruned product: inactive inputs
 // contribute nothing and only active outputs are written.
+//
+// Kernel families, chosen per pass by launch_all:
+//  * item-blocked (k_inner_q, k_outer_q): FP32, n[k] and n[D-1] <= 32;
+//  * element-parallel (k_inner_ep, k_outer_ep): FP64, the same sizes;
+//  * register-blocked, compact and generic tiles: other lengths up to 64;
+//  * point-parallel (k_apply_point, k_pass_point): any mode longer than 64;
+//  * generic single-mode passes (k_pass_row, k_pass_fibre): projected Weylets.
+// A tabulated (non-SoP) diagonal potential is added per active point after
+// the passes (k_add_grid_potential).
 #include "device_util.cuh"
 
 namespace pq {
@@ -1076,19 +1085,18 @@ static pq_status launch_generic(const State& s, ApplyArgs<R> a, const void* in, 
 }
 
 // ------------------------------------------------------------------------
-// Element-parallel fibre kernels (n[k] <= 32, n[D-1] <= 32).  The tiles of a
-// pruned set are sparse, so per-warp fibre processing leaves most lanes idle
-// and serialises long chains of dependent loads.  Here a CTA takes a batch of
-// kEpBatch fibres (or planes) at a time: phase 1, one warp per fibre compacts
-// its active rows (ballot) and the element offsets of those rows; phase 2, all
-// threads of the CTA gather the batch's active coefficients, one thread per
-// coefficient, into a shared-memory tile; phase 3, one thread per active
-// output forms its dot products over the fibre's active rows (and, in the
-// inner pass, over the row's active points and the potential) and writes or
-// accumulates it.  Every phase is bulk-parallel, so the CTA keeps many loads
-// in flight instead of one dependent chain per warp.
+// Element-parallel fibre kernels (n[k] <= 32, n[D-1] <= 32), the FP64 path.
+// One warp per fibre (or plane): the warp compacts the fibre's active rows
+// with a ballot, the lanes gather the fibre's active coefficients (lane e takes
+// elements e, e + 32, ..., located by a monotone walk over the row offsets)
+// into a zero-filled shared-memory tile, and each lane then forms the outputs
+// of its elements over the fibre's active rows (and, in the inner pass, over
+// the row's span and the potential).  Every output costs one FMA pair per
+// active term, the fewest FP64 operations of the tiled kernels, which is what
+// counts at GB300's FP64 rate; the FP32 path uses the item-blocked kernels
+// below.
 
-constexpr int kEpBatch = 8;          // fibres per batch (one per warp of 256 threads)
+constexpr int kEpBatch = 8;          // warps per CTA, one fibre each
 
 // position of the n-th (0-based) set bit of b
 __device__ __forceinline__ int nth_set_bit(uint32_t b, int n) {
@@ -1117,24 +1125,6 @@ struct EpMeta {
     int roff[kEpBatch][33];
 };
 
-// Locate batch element e: fibre f, compact row u, last-mode point s, position.
-__device__ __forceinline__ void ep_locate(const EpMeta& m, int e, int& f, int& u, int& s,
-                                          uint32_t& pos) {
-    f = 0;
-    while (f + 1 < kEpBatch && m.eoff[f + 1] <= e) ++f;
-    const int el = e - m.eoff[f];
-    int lo = 0, hi = m.na[f] - 1;   // largest u with roff[f][u] <= el
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (m.roff[f][mid] <= el) lo = mid;
-        else hi = mid - 1;
-    }
-    u = lo;
-    const int kth = el - m.roff[f][u];
-    s = nth_set_bit(m.rbt[f][u], kth);
-    pos = m.rst[f][u] + (uint32_t)kth;
-}
-
 // Phase 1 for warp f: compact the active rows (given per lane j < n) and
 // their element offsets.
 __device__ __forceinline__ void ep_compact(EpMeta& m, int f, int lane, int j, uint32_t b,
@@ -1159,21 +1149,6 @@ __device__ __forceinline__ void ep_compact(EpMeta& m, int f, int lane, int j, ui
         m.na[f] = __popc(act);
         m.roff[f][__popc(act)] = total;
     }
-}
-
-// Locate element el of fibre f: compact row u, last-mode point s, position.
-__device__ __forceinline__ void ep_locate_f(const EpMeta& m, int f, int el, int& u, int& s,
-                                            uint32_t& pos) {
-    int lo = 0, hi = m.na[f] - 1;   // largest u with roff[f][u] <= el
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (m.roff[f][mid] <= el) lo = mid;
-        else hi = mid - 1;
-    }
-    u = lo;
-    const int kth = el - m.roff[f][u];
-    s = nth_set_bit(m.rbt[f][u], kth);
-    pos = m.rst[f][u] + (uint32_t)kth;
 }
 
 // Element e of the warp's fibre, located from the lane's previous row:
