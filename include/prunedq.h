@@ -100,8 +100,9 @@ typedef struct pq_state pq_state;
 /* Build the per-mode 1D bases (Sec. 2.1 direct-product expansion; DVR grid
  * points x_j, weights w_j with a_j = sqrt(w_j) psi(x_j), and kinetic matrices).
  * Host-only FP64 work.  *out is owned by the library: free with pq_basis_free.
- * Errors: PQ_EINVAL for D outside 1..8, n outside 2..64, a lattice of 2^32
- * points or more, or a kind this build does not provide (PQ_ENOTSUP). */
+ * Errors: PQ_EINVAL for D outside 1..7, n outside 2..256, a lattice of 2^32
+ * points or more, or an unknown kind; PQ_ENOTSUP for pvB modes mixed with
+ * other kinds. */
 pq_status pq_build_basis(const pq_mode_desc* modes, int D, pq_basis** out);
 void pq_basis_free(pq_basis* basis);
 
