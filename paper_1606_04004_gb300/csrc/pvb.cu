@@ -183,6 +183,59 @@ __global__ void k_lincomb(typename Cx<R>::T* out, double a1r, double a1i,
     }
 }
 
+// Conjugate-gradient scalars on the device (slots of a small double array),
+// so that an iteration needs no host round trip.
+enum { kCgRR = 0, kCgY2, kCgAlpha, kCgBeta, kCgDone, kCgFail, kCgIt, kCgSlots };
+
+// Sum of the real parts of partials[G][2] (fixed order), then the CG update of
+// `mode`: 0 = start (rr = <y, y>), 1 = after <p, S p> (alpha), 2 = after the
+// new <r, r> (beta, convergence).
+__global__ void k_cg_scalar(const double* partials, int G, double* cg, int mode, double tol2) {
+    const int lane = threadIdx.x;
+    double acc = 0.0;
+    for (int b = lane; b < G; b += 32) acc += partials[2 * b];
+    acc = warp_sum(acc);
+    if (lane != 0) return;
+    if (mode == 0) {
+        cg[kCgRR] = acc;
+        cg[kCgY2] = fmax(acc, 1e-300);
+        cg[kCgDone] = acc <= tol2 * cg[kCgY2] ? 1.0 : 0.0;
+        cg[kCgFail] = 0.0;
+        cg[kCgIt] = 0.0;
+        return;
+    }
+    if (cg[kCgDone] != 0.0) return;
+    if (mode == 1) {
+        const double al = cg[kCgRR] / acc;
+        if (!isfinite(al)) {
+            cg[kCgFail] = 1.0;
+            cg[kCgDone] = 1.0;
+            return;
+        }
+        cg[kCgAlpha] = al;
+    } else {
+        cg[kCgBeta] = acc / cg[kCgRR];
+        cg[kCgRR] = acc;
+        cg[kCgIt] += 1.0;
+        if (acc <= tol2 * cg[kCgY2]) cg[kCgDone] = 1.0;
+    }
+}
+
+// out = x1 + sign * cg[slot] * x2 (real coefficient), nothing once CG is done.
+template <typename R>
+__global__ void k_cg_axpy(typename Cx<R>::T* out, const typename Cx<R>::T* x1,
+                          const typename Cx<R>::T* x2, int64_t n, const double* cg, int slot,
+                          double sign) {
+    if (cg[kCgDone] != 0.0) return;
+    const double c = sign * cg[slot];
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const auto u = x1[p];
+        const auto v = x2[p];
+        out[p] = cmake<R>((R)(u.x + c * v.x), (R)(u.y + c * v.y));
+    }
+}
+
 template <typename R>
 __global__ void k_packet_bra(const uint32_t* __restrict__ keys, const int64_t* na, int64_t cap,
                              Lattice L, const double2* __restrict__ fac, typename Cx<R>::T* out) {
@@ -327,33 +380,50 @@ struct Pvb {
         return PQ_OK;
     }
     void* vec(int i) { return (char*)s.pvb_vec + (size_t)i * s.cap * sizeof(V); }
-    // x = S_AA^{-1} y by conjugate gradients (x, y distinct)
+    // x = S_AA^{-1} y by conjugate gradients (x, y distinct).  The scalars
+    // live on the device; the host looks at the convergence flag once every
+    // kCgBatch iterations (iterations after convergence change nothing).
     pq_status solve(const void* y, void* x, double tol) {
         void* r = vec(0);
         void* p = vec(1);
         void* Sp = vec(2);
+        double* cg = s.red_tmp + 8192;
+        constexpr int kCgBatch = 4;
+        const int maxit = 2000;
+        const double tol2 = tol * tol;
         pq_status rc;
         PQ_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(V), st));
         if ((rc = lin(r, 1.0, y)) || (rc = lin(p, 1.0, y))) return rc;
-        cd rr, yy;
-        if ((rc = dot(r, r, &rr))) return rc;
-        yy = rr;
-        const double y2 = std::max(yy.real(), 1e-300);
-        const int maxit = 2000;
-        for (int it = 0; it < maxit; ++it) {
-            if (rr.real() <= tol * tol * y2) return PQ_OK;
-            cd pSp;
-            if ((rc = S(p, Sp)) || (rc = dot(p, Sp, &pSp))) return rc;
-            const double al = rr.real() / pSp.real();
-            if (!std::isfinite(al)) {
+        auto dot_into = [&](const void* a, const void* b, int mode) -> pq_status {
+            k_cdot<R><<<G, kPvbThreads, 0, st>>>((const V*)a, (const V*)b, n, part);
+            PQ_CHECK_LAUNCH();
+            k_cg_scalar<<<1, 32, 0, st>>>(part, G, cg, mode, tol2);
+            PQ_CHECK_LAUNCH();
+            return PQ_OK;
+        };
+        auto axpy = [&](void* out, const void* x1, const void* x2, int slot, double sign) -> pq_status {
+            k_cg_axpy<R><<<G, kPvbThreads, 0, st>>>((V*)out, (const V*)x1, (const V*)x2, n, cg, slot,
+                                                    sign);
+            PQ_CHECK_LAUNCH();
+            return PQ_OK;
+        };
+        if ((rc = dot_into(r, r, 0))) return rc;
+        double flags[2];
+        for (int it = 0;; it += kCgBatch) {
+            PQ_CUDA_TRY(cudaMemcpyAsync(flags, cg + kCgDone, sizeof(flags), cudaMemcpyDeviceToHost, st));
+            PQ_CUDA_TRY(cudaStreamSynchronize(st));
+            if (flags[1] != 0.0) {
                 set_error("pvB: conjugate gradients broke down");
                 return PQ_ENUMERIC;
             }
-            cd rr2;
-            if ((rc = lin(x, 1.0, x, al, p)) || (rc = lin(r, 1.0, r, -al, Sp)) || (rc = dot(r, r, &rr2)))
-                return rc;
-            if ((rc = lin(p, 1.0, r, rr2.real() / rr.real(), p))) return rc;
-            rr = rr2;
+            if (flags[0] != 0.0) return PQ_OK;
+            if (it >= maxit) break;
+            for (int b = 0; b < kCgBatch; ++b) {
+                if ((rc = S(p, Sp)) || (rc = dot_into(p, Sp, 1)) ||
+                    (rc = axpy(x, x, p, kCgAlpha, 1.0)) || (rc = axpy(r, r, Sp, kCgAlpha, -1.0)) ||
+                    (rc = dot_into(r, r, 2)) || (rc = axpy(p, r, p, kCgBeta, 1.0)))
+                    return rc;
+            }
         }
         set_error("pvB: conjugate gradients did not converge in %d iterations", maxit);
         return PQ_ENUMERIC;
