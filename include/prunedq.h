@@ -325,6 +325,20 @@ pq_status pq_survival_grad(pq_state* state, const pq_prop_desc* desc, int nsteps
  * state's active set outgrew its capacity. */
 pq_status pq_observe_noalloc(const pq_state* state, double theta, double* out, void* stream);
 
+/* Device memory through the caller's allocator (no counterpart in the paper):
+ * every device buffer the library takes (state buffers, the Krylov space,
+ * temporaries of a propagation) is then obtained as alloc(bytes, stream, ctx)
+ * and returned as free(ptr, stream, ctx), `stream` being the cudaStream_t the
+ * buffer is used on (0 for long-lived buffers).  This lets a framework such as
+ * PyTorch keep all device memory in its caching allocator.  alloc = free =
+ * NULL restores cudaMalloc.  Host memory (one small pinned counter block per
+ * state) and the fixed scratch of pq_observe_noalloc are not affected.
+ * PQ_EINVAL while any state exists (a state must free with the allocator it
+ * allocated with) or when only one of the two functions is given. */
+typedef void* (*pq_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*pq_free_fn)(void* ptr, void* stream, void* ctx);
+pq_status pq_set_allocator(pq_alloc_fn alloc, pq_free_fn free_fn, void* ctx);
+
 /* Number of kernels the library has launched since load (all states). */
 int64_t pq_launch_count(void);
 

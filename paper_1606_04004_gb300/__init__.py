@@ -78,7 +78,11 @@ class ParamDesc(C.Structure):
 PARAM_POTENTIAL, PARAM_CENTRE = 0, 1
 
 _vp = C.c_void_p
+#: pq_alloc_fn / pq_free_fn of the C ABI
+ALLOC_FN = C.CFUNCTYPE(_vp, C.c_size_t, _vp, _vp)
+FREE_FN = C.CFUNCTYPE(None, _vp, _vp, _vp)
 _SIGS = {
+    "pq_set_allocator": [ALLOC_FN, FREE_FN, _vp],
     "pq_build_basis": [C.POINTER(ModeDesc), C.c_int, C.POINTER(_vp)],
     "pq_basis_free": [_vp],
     "pq_basis_grid": [_vp, C.c_int, _vp, _vp],
@@ -126,6 +130,35 @@ def _check(rc):
 
 def launch_count() -> int:
     return int(_lib.pq_launch_count())
+
+
+_allocator = []   # keeps the ctypes callbacks alive while the library holds them
+
+
+def set_allocator(alloc=None, free=None):
+    """Route the library's device memory through alloc(bytes, stream, ctx) ->
+    pointer and free(pointer, stream, ctx) (pq_set_allocator); no arguments
+    restore cudaMalloc.  Only while no state exists."""
+    if alloc is None:
+        _check(_lib.pq_set_allocator(ALLOC_FN(), FREE_FN(), None))
+        _allocator.clear()
+        return
+    fa, ff = ALLOC_FN(alloc), FREE_FN(free)
+    _check(_lib.pq_set_allocator(fa, ff, None))
+    _allocator[:] = [fa, ff]
+
+
+def use_torch_allocator():
+    """Let PyTorch's caching allocator own all of the library's device memory."""
+    import torch
+
+    def _alloc(n, stream, ctx):
+        return torch.cuda.caching_allocator_alloc(int(n), stream=int(stream or 0))
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    set_allocator(_alloc, _free)
 
 
 def lib_path() -> str:

@@ -143,14 +143,18 @@ namespace {
 struct DevBuf {
     void* p = nullptr;
     ~DevBuf() {
-        if (p) cudaFree(p);
+        if (p) {
+            cudaDeviceSynchronize();   // the gradient's kernels may still use it
+            dev_free(p, 0, false);
+        }
     }
 };
 
 pq_status dmalloc(DevBuf& b, size_t bytes) {
-    cudaError_t e = cudaMalloc(&b.p, bytes ? bytes : 16);
-    if (e != cudaSuccess) {
-        set_error("cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    b.p = dev_alloc(bytes, 0, false);
+    if (!b.p) {
+        cudaGetLastError();
+        set_error("device allocation of %zu bytes failed", bytes);
         return PQ_ENOMEM;
     }
     return PQ_OK;

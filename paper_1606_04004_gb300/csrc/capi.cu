@@ -25,37 +25,64 @@ void set_error(const char* fmt, ...) {
 }
 void clear_error() { g_err.clear(); }
 
+// caller's allocator (pq_set_allocator) and the number of live states
+static pq_alloc_fn g_user_alloc = nullptr;
+static pq_free_fn g_user_free = nullptr;
+static void* g_user_ctx = nullptr;
+static std::atomic<int64_t> g_live_states{0};
+
+void* dev_alloc(size_t bytes, cudaStream_t st, bool async) {
+    if (bytes == 0) bytes = 16;
+    if (g_user_alloc) return g_user_alloc(bytes, (void*)st, g_user_ctx);
+    void* p = nullptr;
+    const cudaError_t e = async ? cudaMallocAsync(&p, bytes, st) : cudaMalloc(&p, bytes);
+    return e == cudaSuccess ? p : nullptr;
+}
+
+void dev_free(void* p, cudaStream_t st, bool async) {
+    if (!p) return;
+    if (g_user_free) {
+        g_user_free(p, (void*)st, g_user_ctx);
+        return;
+    }
+    if (async) cudaFreeAsync(p, st);
+    else cudaFree(p);
+}
+
 static void free_state(State* s) {
     if (!s) return;
-    if (s->rowinfo) cudaFree(s->rowinfo);
+    // a caller's allocator may hand the memory out again at once: let the
+    // device finish with it first (cudaFree synchronises by itself)
+    if (g_user_free) cudaDeviceSynchronize();
+    if (s->rowinfo) dev_free(s->rowinfo, 0, false);
     {
         void* pv[] = {s->pvbB64, s->pvbB32, s->pvbBh64, s->pvbBh32, s->pvbS64, s->pvbS32,
                       s->pvbT64, s->pvbT32, s->pvb_grid, s->pvb_vec, s->fac_bra64};
         for (void* p : pv)
-            if (p) cudaFree(p);
+            dev_free(p, 0, false);
     }
-    if (s->vgrid64) cudaFree(s->vgrid64);
-    if (s->vgrid32) cudaFree(s->vgrid32);
-    if (s->gmat64) cudaFree(s->gmat64);
-    if (s->gmat32) cudaFree(s->gmat32);
-    if (s->gtmp) cudaFree(s->gtmp);
+    dev_free(s->vgrid64, 0, false);
+    dev_free(s->vgrid32, 0, false);
+    dev_free(s->gmat64, 0, false);
+    dev_free(s->gmat32, 0, false);
+    dev_free(s->gtmp, 0, false);
     void* ptrs[] = {s->keys,   s->psi,     s->psi_alt, s->bits,  s->bits_alt, s->off,
                     s->off_alt, s->rows,   s->planes,  s->leaders, s->cnt,    s->scan_tmp,
                     s->red_tmp, s->ks,     s->V,       s->T64,   s->T32,     s->pot64,
                     s->pot32,  s->fac64,   s->fac32,   s->io_in, s->io_out};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        dev_free(p, 0, false);
     if (s->h_cnt) cudaFreeHost(s->h_cnt);
     delete s;
+    g_live_states.fetch_sub(1);
 }
 
 template <typename T>
 static pq_status dalloc(T** p, size_t bytes) {
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc((void**)p, bytes);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        set_error("cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    *p = static_cast<T*>(dev_alloc(bytes, 0, false));
+    if (!*p) {
+        cudaGetLastError();   // clear a sticky allocation error
+        set_error("device allocation of %zu bytes failed", bytes);
         return PQ_ENOMEM;
     }
     return PQ_OK;
@@ -265,6 +292,7 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
         return PQ_EINVAL;
     }
     State* s = new State();
+    g_live_states.fetch_add(1);
     s->basis = basis;
     s->prec = precision;
     s->esize = precision == PQ_FP64 ? 16 : 8;
@@ -368,6 +396,23 @@ using namespace pq;
 #define PQ_API extern "C" __attribute__((visibility("default")))
 
 PQ_API const char* pq_last_error(void) { return g_err.c_str(); }
+
+PQ_API pq_status pq_set_allocator(pq_alloc_fn alloc, pq_free_fn free_fn, void* ctx) {
+    clear_error();
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        set_error("give both an allocation and a release function, or neither");
+        return PQ_EINVAL;
+    }
+    if (g_live_states.load() != 0) {
+        set_error("the allocator cannot change while %lld state(s) exist",
+                  (long long)g_live_states.load());
+        return PQ_EINVAL;
+    }
+    g_user_alloc = alloc;
+    g_user_free = free_fn;
+    g_user_ctx = alloc ? ctx : nullptr;
+    return PQ_OK;
+}
 PQ_API int64_t pq_launch_count(void) { return g_launches.load(); }
 
 PQ_API pq_status pq_build_basis(const pq_mode_desc* modes, int D, pq_basis** out) {
@@ -702,7 +747,7 @@ PQ_API pq_status pq_state_load(pq_state* state, const int64_t* idx, int64_t n, c
     cudaMemcpy(dk, k32.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
     rc = load_set(*s, dk, n, 0);
     cudaDeviceSynchronize();
-    cudaFree(dk);
+    dev_free(dk, 0, false);
     if (rc) return rc;
     if (psi)
         PQ_CUDA_TRY(cudaMemcpy(s->psi, psi, (size_t)n * s->esize, cudaMemcpyHostToDevice));

@@ -711,13 +711,16 @@ static pq_status rk4_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
 
 pq_status ensure_krylov(State& s, int K) {
     if (s.V_K >= K) return PQ_OK;
-    if (s.V) cudaFree(s.V);
+    if (s.V) {
+        cudaDeviceSynchronize();   // the old space may still be in use on some stream
+        dev_free(s.V, 0, false);
+    }
     s.V = nullptr;
     s.V_K = 0;
-    cudaError_t e = cudaMalloc(&s.V, (size_t)K * s.cap * s.esize);
-    if (e != cudaSuccess) {
-        set_error("cannot allocate the Krylov space (%zu bytes): %s", (size_t)K * s.cap * s.esize,
-                  cudaGetErrorString(e));
+    s.V = dev_alloc((size_t)K * s.cap * s.esize, 0, false);
+    if (!s.V) {
+        cudaGetLastError();
+        set_error("cannot allocate the Krylov space (%zu bytes)", (size_t)K * s.cap * s.esize);
         return PQ_ENOMEM;
     }
     s.V_K = K;
@@ -754,7 +757,11 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
     if (erc) return erc;
     if (nsteps == 0) return PQ_OK;
     double* recs = nullptr;
-    PQ_CUDA_TRY(cudaMallocAsync((void**)&recs, (size_t)(nsteps + 1) * 8 * sizeof(double), st));
+    recs = (double*)dev_alloc((size_t)(nsteps + 1) * 8 * sizeof(double), st, true);
+    if (!recs) {
+        set_error("device allocation of the step records failed");
+        return PQ_ENOMEM;
+    }
     PQ_CUDA_TRY(cudaMemsetAsync(recs, 0, (size_t)(nsteps + 1) * 8 * sizeof(double), st));
     // Slot 0 receives E of the record already on the host (alpha_0 of step 1).
     pq_status rc = PQ_OK;
@@ -776,7 +783,7 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
     cudaError_t e2 = cudaMemcpyAsync(s.h_cnt, s.cnt, CNT_SIZE * sizeof(int64_t),
                                      cudaMemcpyDeviceToHost, st);
     cudaError_t e3 = cudaStreamSynchronize(st);
-    cudaFreeAsync(recs, st);
+    dev_free(recs, st, true);
     if (rc) return rc;
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
         set_error("propagate: %s", cudaGetErrorString(e3 != cudaSuccess ? e3 : (e1 ? e1 : e2)));
@@ -833,12 +840,16 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
 
 pq_status observe_launch(State& s, double theta, cudaStream_t st) {
     double* rec = nullptr;
-    PQ_CUDA_TRY(cudaMallocAsync((void**)&rec, 8 * sizeof(double), st));
+    rec = (double*)dev_alloc(8 * sizeof(double), st, true);
+    if (!rec) {
+        set_error("device allocation failed");
+        return PQ_ENOMEM;
+    }
     pq_status rc = observe_rec(s, theta, rec, st);
     double h[8] = {0};
     cudaMemcpyAsync(h, rec, sizeof(h), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
-    cudaFreeAsync(rec, st);
+    dev_free(rec, st, true);
     if (rc) return rc;
     if (e != cudaSuccess) {
         set_error("observe: %s", cudaGetErrorString(e));
@@ -855,7 +866,11 @@ static pq_status energy_t(State& s, double* E, cudaStream_t st) {
     using V = typename Cx<R>::T;
     const int G = red_blocks();
     void* W = nullptr;
-    PQ_CUDA_TRY(cudaMallocAsync(&W, s.cap * s.esize > 0 ? s.cap * s.esize : 16, st));
+    W = dev_alloc(s.cap * s.esize, st, true);
+    if (!W) {
+        set_error("device allocation failed");
+        return PQ_ENOMEM;
+    }
     k_norm2<R><<<G, kRedThreads, 0, st>>>((const V*)s.psi, s.cnt + CNT_NA, (int64_t)s.cap, s.red_tmp);
     PQ_CHECK_LAUNCH();
     k_start_step<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks, 1, s.cnt + CNT_ERR);
@@ -863,22 +878,27 @@ static pq_status energy_t(State& s, double* E, cudaStream_t st) {
     // W = H (psi / ||psi||); <psi/||psi||, W> is then E
     pq_status rc = apply_H_launch(s, s.psi, W, s.prec, &s.ks->sigma[0], nullptr, 0, st);
     if (rc) {
-        cudaFreeAsync(W, st);
+        dev_free(W, st, true);
         return rc;
     }
     k_dots<R, 1><<<G, kRedThreads, 0, st>>>(s.psi, s.V, s.cap, (const V*)W, s.cnt + CNT_NA, 0,
                                             s.ks, 0, s.red_tmp);
     PQ_CHECK_LAUNCH();
     double* dE = nullptr;
-    PQ_CUDA_TRY(cudaMallocAsync((void**)&dE, sizeof(double), st));
+    dE = (double*)dev_alloc(sizeof(double), st, true);
+    if (!dE) {
+        dev_free(W, st, true);
+        set_error("device allocation failed");
+        return PQ_ENOMEM;
+    }
     PQ_CUDA_TRY(cudaMemsetAsync(dE, 0, sizeof(double), st));
     k_dots_done<<<1, 256, 0, st>>>(s.red_tmp, G, 0, 1, s.ks, 0, dE, s.cnt + CNT_ERR);
     PQ_CHECK_LAUNCH();
     double h = 0.0;
     cudaMemcpyAsync(&h, dE, sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
-    cudaFreeAsync(dE, st);
-    cudaFreeAsync(W, st);
+    dev_free(dE, st, true);
+    dev_free(W, st, true);
     if (e != cudaSuccess) {
         set_error("energy: %s", cudaGetErrorString(e));
         return PQ_ECUDA;

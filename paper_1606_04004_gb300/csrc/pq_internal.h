@@ -236,6 +236,10 @@ pq_status rebuild_from_bits(State& s, bool remap, cudaStream_t st);
 // Neighbour rules (pq_neighbour_rule) and the relative exclusion threshold
 // of the adaption; radius 2 (the full box) needs at most kMaxBoxAxes axes.
 constexpr int kMaxBoxAxes = 8;
+// Device memory through the caller's allocator when one is set
+// (pq_set_allocator), else cudaMalloc / cudaMallocAsync (`async`: stream-ordered).
+void* dev_alloc(size_t bytes, cudaStream_t st, bool async);
+void dev_free(void* p, cudaStream_t st, bool async);
 pq_status check_neighbour_rule(const Lattice& L, int radius);
 pq_status prune_launch(State& s, double theta, int radius, double rel_excl, cudaStream_t st);
 pq_status init_bits_from_packet(State& s, double theta, cudaStream_t st);

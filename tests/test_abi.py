@@ -92,6 +92,20 @@ def test_pvb_on_fgh_matches_oracle():
     assert e.value.status == pq.EINVAL
 
 
+def test_set_allocator_arguments():
+    import ctypes
+    pq = _lib()
+    lib = ctypes.CDLL(pq.lib_path())
+    alloc = pq.ALLOC_FN(lambda n, st, ctx: None)
+    # one function without the other
+    assert lib.pq_set_allocator(alloc, pq.FREE_FN(), None) == pq.EINVAL
+    # set and restore while no state exists (host-only basis objects do not count)
+    b = pq.Basis(pq.modes_of(W.MORSE2D))
+    pq.set_allocator(lambda n, st, ctx: None, lambda p, st, ctx: None)
+    pq.set_allocator()
+    del b
+
+
 def test_tabulated_potential_errors():
     pq = _lib()
     b = pq.Basis(pq.modes_of(W.MORSE2D))
