@@ -197,3 +197,19 @@ def test_sil_error_control_matches_oracle(tol):
     o = s.observables()
     np.testing.assert_array_equal(o["n_active"], _series(r, "n_active"))
     assert np.max(np.abs(o["C"] - _series(r, "C"))) < 1e-10
+
+
+def test_sil_error_control_fp32():
+    # error-controlled order on the FP32-mix path: C(t) within 1e-5 of the oracle
+    from oracle import propagate
+    pq = lib()
+    cfg = W.HH4D
+    n = 10
+    prob = propagate.problem_from_config(cfg)
+    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], 16, cfg["dt"], n,
+                      sil_tol=1e-8)
+    b = pq.build_model(cfg)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP32MIX)
+    s.propagate(16, cfg["dt"], cfg["theta"], n, sil_tol=1e-8)
+    o = s.observables()
+    assert np.max(np.abs(o["C"] - _series(r, "C"))) < 1e-5

@@ -178,3 +178,46 @@ def test_mixed_pw_and_dvr_modes(prec):
         o = s2.observables()
         np.testing.assert_array_equal(o["n_active"], [v["n_active"] for v in r["obs"]])
         assert np.max(np.abs(o["C"] - np.array([v["C"] for v in r["obs"]]))) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pw_double_well_apply(prec):
+    # the point-parallel generic passes (165- and 81-function modes) on a
+    # random subset of the double-well pW lattice
+    import torch
+    from oracle import propagate, pruned
+    pq = lib()
+    cfg = W.DWELL2D_PW
+    b = pq.build_model(cfg)
+    prob = propagate.problem_from_config(cfg)
+    dims = prob.dims
+    A = W.random_active_set(dims, 0.2, seed=31)
+    psi = W.random_psi(len(A), 32).astype(np.complex128 if prec == 0 else np.complex64)
+    s = _state_with(b, A, psi, prec)
+    x = torch.from_numpy(psi).to("cuda")
+    y = torch.empty_like(x)
+    s.apply_H(x, y)
+    torch.cuda.synchronize()
+    ref = prob.apply(A, psi.astype(np.complex128))
+    absterms = [(abs(c), {k: np.abs(h) for k, h in f.items()}) for c, f in prob.terms]
+    bound = pruned.apply_H_sop(A, np.abs(psi).astype(np.complex128), dims, absterms).real
+    tol = 1e-12 if prec == 0 else 5e-5
+    err = np.abs(y.cpu().numpy() - ref)
+    assert np.all(err <= tol * bound + 1e-300), (err / np.maximum(bound, 1e-300)).max()
+
+
+def test_pw_rk4_small():
+    # RK4 through the generic pW passes (FP64) against the oracle's RK4
+    from oracle import propagate
+    pq = lib()
+    cfg = _pw_cfg(2, 16, 4, 4)
+    b = pq.build_model(cfg)
+    prob = propagate.problem_from_config(cfg)
+    n, dt = 8, 2.0
+    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], cfg["K"], dt, n,
+                      integrator="rk4")
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP64)
+    s.propagate(cfg["K"], dt, cfg["theta"], n, integrator=pq.RK4)
+    o = s.observables()
+    np.testing.assert_array_equal(o["n_active"], [v["n_active"] for v in r["obs"]])
+    assert np.max(np.abs(o["C"] - np.array([v["C"] for v in r["obs"]]))) < 1e-10
