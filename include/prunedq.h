@@ -287,8 +287,9 @@ pq_status pq_timing_get(pq_state* state, double* apply_ms, int64_t* n_apply,
  *   PQ_PARAM_POTENTIAL  dH/dtheta as diagonal SoP terms on the DVR grid
  *                       (PQ_FACTOR_DIAG / PQ_FACTOR_IDENTITY factors);
  *   PQ_PARAM_CENTRE     the packet centre q0 of `mode`.
- * grad_out: nparams doubles (host); P_out (nullable): P.  DVR bases only
- * (PQ_ENOTSUP otherwise), at most 16 parameters.  The state is left at its
+ * grad_out: nparams doubles (host); P_out (nullable): P.  DVR bases and
+ * fixed-order SIL only (PQ_ENOTSUP otherwise: pW / pvB, PQ_RK4, sil_tol > 0),
+ * at most 16 parameters.  The state is left at its
  * initial packet; its recorded observables are not changed.  Synchronises.
  * Allocates device memory for the recorded sets and checkpoints. */
 typedef enum pq_param_kind { PQ_PARAM_POTENTIAL = 0, PQ_PARAM_CENTRE = 1 } pq_param_kind;
@@ -334,7 +335,8 @@ pq_status pq_observe_noalloc(const pq_state* state, double theta, double* out, v
  * NULL restores cudaMalloc.  Host memory (one small pinned counter block per
  * state) and the fixed scratch of pq_observe_noalloc are not affected.
  * PQ_EINVAL while any state exists (a state must free with the allocator it
- * allocated with) or when only one of the two functions is given. */
+ * allocated with) or when only one of the two functions is given.  Not to be
+ * called concurrently with other library calls. */
 typedef void* (*pq_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*pq_free_fn)(void* ptr, void* stream, void* ctx);
 pq_status pq_set_allocator(pq_alloc_fn alloc, pq_free_fn free_fn, void* ctx);
