@@ -13,14 +13,18 @@ and ``numpy.searchsorted`` (sorting / lookup), matrix products.
 
 Modules
 -------
-bases      1D primitive bases: sine DVR, HO (Gauss-Hermite) DVR; von Neumann
-           and momentum-symmetrised Gaussians projected on a DVR (pvB, pW).
-models     potentials written as plain functions of the coordinates and the
-           initial Gaussian packet.
+bases      1D primitive bases: sine, HO (Gauss-Hermite) and FGH DVRs; von
+           Neumann and momentum-symmetrised Gaussians projected on a DVR (pvB, pW).
+models     potentials written as plain functions of the coordinates (including
+           the paper's double well) and the initial Gaussian packet.
 pruned     the pruned H.a on an active set, the adaption (prune + add) set
-           function, observables.
-sil        short-iterative Lanczos step with full re-orthogonalisation.
-propagate  the whole run: initial prune, then SIL -> prune -> observables.
+           function with its neighbour rules and relative exclusion, observables.
+sil        short-iterative Lanczos step with full re-orthogonalisation (fixed or
+           error-controlled order) and the RK4 step.
+propagate  the whole run: initial prune, then step -> prune -> observables.
+pvb        pvB dynamics: H_AA on the full grid, CG on S_AA, Lanczos in the S
+           inner product.
+adjoint    frozen-set replay, survival probability, finite differences.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against closed forms, brute force or a dense reference (see tests/).
