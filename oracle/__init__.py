@@ -8,7 +8,7 @@ code with the CUDA library (``paper_1606_04004_gb300``) and never imports it;
 the only common module is ``workloads`` (seeded inputs, no method arithmetic).
 
 Everything is numpy float64 / complex128.  Library primitives used as single
-steps: ``numpy.linalg.eigh`` (symmetric eigendecomposition), ``numpy.unique``
+steps: ``numpy.linalg.eigh`` (symmetric eigendecomposition), ``numpy.fft.fft`` (FGH kinetic matrix), ``numpy.unique``
 and ``numpy.searchsorted`` (sorting / lookup), matrix products.
 
 Modules
