@@ -89,22 +89,18 @@ def ho_dvr(n: int, mass: float = 1.0, omega: float = 1.0):
     return x, w, T
 
 
-def pw_basis(n, xmin, xmax, mass, nx, np_, dvr="sine"):
-    """Projected Weylets on a sine DVR, or on an FGH DVR with dvr="fgh" (Sec. 2.4;
-    Sec. 3.2 uses the FGH grid).
+def pw_functions(x, w, xmin, xmax, nx, np_):
+    """The momentum-symmetrised Gaussians of Eq. sG_def projected on a DVR with
+    points x and weights w (Sec. 2.4), before orthogonalisation.
 
-    Momentum-symmetrised Gaussians (Eq. sG_def) on a doubly dense phase-space
-    lattice (Delta x Delta p = pi, p_l > 0): x_a = xmin + (a + 1/2) Dx with
-    Dx = L / nx, p_b = (b + 1/2) Dp with Dp = pi / Dx, alpha = Dp / (2 Dx),
+    Doubly dense phase-space lattice (Delta x Delta p = pi, p_l > 0):
+    x_a = xmin + (a + 1/2) Dx with Dx = (xmax - xmin) / nx, p_b = (b + 1/2) Dp
+    with Dp = pi / Dx, alpha = Dp / (2 Dx),
         phi_ab(x) = (8 alpha / pi)^(1/4) exp(-alpha (x - x_a)^2)
-                    sin(p_b (x - x_a - sqrt(pi / (8 alpha)))).
-    Projected on the DVR, Phi_ji = sqrt(w_j) phi_i(x_j) with i = a np + b
-    (x index slow, p index fast), and orthogonalised symmetrically (Loewdin):
-    W = Phi S^(-1/2), S = Phi^T Phi.  Needs n = nx np.
-    Returns (x, w, T, W) where x, w, T are the underlying DVR's."""
-    if nx * np_ != n:
-        raise ValueError("the phase-space lattice must have as many functions as DVR points")
-    x, w, T = (fgh_dvr if dvr == "fgh" else sine_dvr)(n, xmin, xmax, mass)
+                    sin(p_b (x - x_a - sqrt(pi / (8 alpha)))),
+    and Phi_ji = sqrt(w_j) phi_i(x_j) with i = a np + b (x index slow, p index
+    fast).  Returns Phi, shape (len(x), nx np)."""
+    x = np.asarray(x, dtype=np.float64)
     L = xmax - xmin
     dx = L / nx
     dp = np.pi / dx
@@ -112,12 +108,27 @@ def pw_basis(n, xmin, xmax, mass, nx, np_, dvr="sine"):
     xa = xmin + (np.arange(nx) + 0.5) * dx
     pb = (np.arange(np_) + 0.5) * dp
     shift = np.sqrt(np.pi / (8.0 * alpha))
-    Phi = np.zeros((n, n))
+    Phi = np.zeros((len(x), nx * np_))
     for a in range(nx):
         for b in range(np_):
             g = (8.0 * alpha / np.pi) ** 0.25 * np.exp(-alpha * (x - xa[a]) ** 2) \
                 * np.sin(pb[b] * (x - xa[a] - shift))
             Phi[:, a * np_ + b] = np.sqrt(w) * g
+    return Phi
+
+
+def pw_basis(n, xmin, xmax, mass, nx, np_, dvr="sine"):
+    """Projected Weylets on a sine DVR, or on an FGH DVR with dvr="fgh" (Sec. 2.4;
+    Sec. 3.2 uses the FGH grid).
+
+    The projected symmetrised Gaussians Phi (``pw_functions``, Eq. sG_def) are
+    orthogonalised symmetrically (Loewdin): W = Phi S^(-1/2), S = Phi^T Phi.
+    Needs n = nx np.  Returns (x, w, T, W) where x, w, T are the underlying
+    DVR's."""
+    if nx * np_ != n:
+        raise ValueError("the phase-space lattice must have as many functions as DVR points")
+    x, w, T = (fgh_dvr if dvr == "fgh" else sine_dvr)(n, xmin, xmax, mass)
+    Phi = pw_functions(x, w, xmin, xmax, nx, np_)
     S = Phi.T @ Phi
     lam, U = np.linalg.eigh(S)
     W = Phi @ (U @ np.diag(lam ** -0.5) @ U.T)

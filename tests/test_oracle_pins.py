@@ -483,26 +483,82 @@ def test_pw_orthonormal_and_similar():
                                rtol=1e-10, atol=1e-14)
 
 
-def test_pw_functions_follow_eq_sG():
-    # brute force of Eq. sG_def at the DVR points for one lattice function:
-    # Phi = W S^(1/2); its column (a, b) is sqrt(w) times the symmetrised
-    # Gaussian with phase shift sqrt(pi / (8 alpha)) on the doubly dense lattice.
-    n, lo, hi, nx, np_ = 16, 0.5, 6.0, 4, 4
-    x, w, T, W = bases.pw_basis(n, lo, hi, 1.0, nx, np_)
-    lam, U = np.linalg.eigh(W.T @ W)   # = 1; Phi = W S^(1/2) needs S:
+def _moments(x, w, T, mass, col):
+    """Norm, position centroid and <p^2> of a function given by its DVR
+    coefficients col_j = sqrt(w_j) f(x_j): quadrature for the first two,
+    the DVR kinetic matrix (<p^2> = 2 m <f|T|f>) for the third."""
+    nrm = np.vdot(col, col).real
+    xc = np.sum(x * np.abs(col) ** 2) / nrm
+    p2 = 2.0 * mass * np.vdot(col, T @ col).real / nrm
+    return nrm, xc, p2
+
+
+@pytest.mark.parametrize("dvr", ["sine", "fgh"])
+def test_pw_functions_closed_form_moments(dvr):
+    # Eq. sG_def on the doubly dense lattice (Dx Dp = pi, alpha = Dp / 2 Dx):
+    # in momentum space phi_ab is two Gaussians of variance alpha at +-p_b plus
+    # a cross term proportional to cos(2 p_b s); the shift s = sqrt(pi / 8 alpha)
+    # makes 2 p_b s = (2b + 1) pi / 2, so the cross term vanishes and, exactly,
+    #   ||phi|| = 1,  <p^2> = p_b^2 + alpha,
+    #   <x> - x_a = -(-1)^b (p_b / 2 alpha) exp(-p_b^2 / 2 alpha).
+    # Checked by DVR quadrature and the DVR kinetic matrix for functions away
+    # from the box edges and the DVR's top momentum (catches a wrong alpha,
+    # Dp, shift or its sign, normalisation, or centre).
+    n, lo, hi, m, nx, np_ = 96, 0.0, 12.0, 2.0, 12, 8
+    x, w, T = (bases.fgh_dvr if dvr == "fgh" else bases.sine_dvr)(n, lo, hi, m)
+    Phi = bases.pw_functions(x, w, lo, hi, nx, np_)
     dx = (hi - lo) / nx
-    dp = np.pi / dx                       # doubly dense: dx dp = pi
+    dp = np.pi / dx
     alpha = dp / (2 * dx)
-    a, b = 2, 3
-    xa = lo + (a + 0.5) * dx
-    pb = (b + 0.5) * dp
-    g = (8 * alpha / np.pi) ** 0.25 * np.exp(-alpha * (x - xa) ** 2) \
-        * np.sin(pb * (x - xa - np.sqrt(np.pi / (8 * alpha))))
-    Phi_col = np.sqrt(w) * g
-    # W spans the same space as Phi: the column lies in span(W) and
-    # W W^T Phi_col = Phi_col
-    np.testing.assert_allclose(W @ (W.T @ Phi_col), Phi_col, atol=1e-12)
-    assert pb > 0 and abs(dx * dp - np.pi) < 1e-12
+    for a in range(2, nx - 2):
+        xa = lo + (a + 0.5) * dx
+        for b in range(np_ - 2):
+            pb = (b + 0.5) * dp
+            nrm, xc, p2 = _moments(x, w, T, m, Phi[:, a * np_ + b])
+            assert abs(nrm - 1.0) < 1e-8, (a, b, nrm)
+            assert abs(p2 - (pb * pb + alpha)) < 1e-6 * (pb * pb + alpha), (a, b, p2)
+            shift = -((-1) ** b) * pb / (2 * alpha) * np.exp(-pb * pb / (2 * alpha))
+            assert abs(xc - xa - shift) < 1e-8, (a, b, xc - xa, shift)
+
+
+def test_pw_is_loewdin_orthogonalisation():
+    # Sec. 2.4: W is the symmetric (Loewdin) orthogonalisation of Phi.  Polar
+    # decomposition: W orthogonal and W^T Phi symmetric positive definite fix W
+    # uniquely (catches Gram-Schmidt / QR, a transposed U or S^(+1/2)).
+    for dvr, (n, lo, hi, nx, np_) in (("sine", (16, 0.5, 6.0, 4, 4)),
+                                      ("fgh", (165, -0.5, 3.7, 15, 11))):
+        x, w, T, Wm = bases.pw_basis(n, lo, hi, 200.0, nx, np_, dvr)
+        Phi = bases.pw_functions(x, w, lo, hi, nx, np_)
+        np.testing.assert_allclose(Wm.T @ Wm, np.eye(n), atol=1e-10)
+        M = Wm.T @ Phi
+        np.testing.assert_allclose(M, M.T, atol=1e-10)
+        assert np.linalg.eigvalsh((M + M.T) / 2).min() > 0
+
+
+@pytest.mark.parametrize("dvr", ["sine", "fgh"])
+def test_pvb_functions_closed_form_moments(dvr):
+    # Sec. 2.2 von Neumann lattice (Dx Dp = 2 pi, alpha = Dp / 2 Dx, momenta
+    # centred on zero): each projected Gaussian has, exactly, ||g|| = 1,
+    # <x> = x_a, <p^2> = p_b^2 + alpha and <p> = p_b.  <p> is taken from the
+    # discrete Fourier transform of the grid values (a route independent of the
+    # DVR); the others as for pW.  Interior functions only.
+    n, lo, hi, m, nx, np_ = 96, 0.0, 12.0, 2.0, 12, 8
+    x, w, T, G, B = bases.pvb_basis(n, lo, hi, m, nx, np_, dvr)
+    dx = (hi - lo) / nx
+    dp = 2 * np.pi / dx
+    alpha = dp / (2 * dx)
+    k = 2 * np.pi * np.fft.fftfreq(n, d=x[1] - x[0])
+    for a in range(2, nx - 2):
+        xa = lo + (a + 0.5) * dx
+        for b in range(1, np_ - 1):
+            pb = -np_ * dp / 2 + (b + 0.5) * dp
+            col = G[:, a * np_ + b]
+            nrm, xc, p2 = _moments(x, w, T, m, col)
+            assert abs(nrm - 1.0) < 1e-8, (a, b, nrm)
+            assert abs(xc - xa) < 1e-8, (a, b, xc, xa)
+            assert abs(p2 - (pb * pb + alpha)) < 1e-7 * (pb * pb + alpha), (a, b, p2)
+            F = np.abs(np.fft.fft(col / np.sqrt(w))) ** 2
+            assert abs(np.sum(k * F) / np.sum(F) - pb) < 1e-6 * dp, (a, b)
 
 
 def test_pvb_biorthogonal():
@@ -642,3 +698,97 @@ def test_pvb_theta0_matches_dvr_dynamics():
         assert abs(o1["C"] - o2["C"]) < 1e-9, (o1["C"], o2["C"])
         assert abs(o1["norm2"] - o2["norm2"]) < 1e-9
         assert abs(o1["E"] - o2["E"]) < 1e-9 * abs(o2["E"])
+
+
+# ---------------------------------------------------------------- adjoint
+
+def test_adjoint_frozen_replay_equals_dense_products():
+    # The frozen-set map: psi_{n+1} = R_n exp(-i H_{A_n A_n} dt) psi_n with R_n
+    # carrying coefficients from A_n to A_{n+1} (kept where the point stays,
+    # zero where it is new), and C = sum_{I in A_N} conj(a0_I) psi_N,I.  With
+    # K >= |A_n| the SIL step is the exact exponential, so the replay must equal
+    # dense products of principal-submatrix exponentials and 0/1 carry matrices
+    # (catches a carry taken in the wrong direction, a set used one step off,
+    # or a bra on the wrong set).
+    from oracle import adjoint
+    cfg = W.scaled(W.HH4D, D=2, n=8, dt=0.3)
+    params = np.array([0.111803, 1.0, 1.2, 1.4, 1.1])
+    prob = propagate.problem_from_config(cfg, omegas=params[1:3], lam=params[0])
+    H = _dense_problem_H(prob)
+    sets = [W.random_active_set(prob.dims, 0.7, s) for s in range(1, 6)]
+    a_init = W.random_psi(len(sets[0]), 3)
+    AN, aN = adjoint.run_frozen(prob, sets[0], a_init, sets, 64, cfg["dt"])
+    a = a_init.copy()
+    for A, An in zip(sets[:-1], sets[1:]):
+        a = scipy.linalg.expm(-1j * H[np.ix_(A, A)] * cfg["dt"]) @ a
+        R = (An[:, None] == A[None, :]).astype(float)
+        a = R @ a
+    np.testing.assert_array_equal(AN, sets[-1])
+    np.testing.assert_allclose(aN, a, rtol=1e-11, atol=1e-12)
+
+    f = prob.factors(params[3:5], cfg["p0"], cfg["width"])
+    P, C = adjoint.survival(cfg, params, sets, K=64)
+    b = pruned.product_on(sets[0], prob.dims, f)
+    for A, An in zip(sets[:-1], sets[1:]):
+        b = (An[:, None] == A[None, :]).astype(float) @ (
+            scipy.linalg.expm(-1j * H[np.ix_(A, A)] * cfg["dt"]) @ b)
+    Cref = np.vdot(pruned.product_on(sets[-1], prob.dims, f), b)
+    assert abs(C - Cref) < 1e-12 and abs(P - abs(Cref) ** 2) < 1e-12
+
+
+def test_adjoint_finite_differences_equal_analytic_gradient():
+    # On the full lattice P(theta) = |a0^T exp(-i H T) a0|^2 (a0 real, unit).
+    # Analytic gradient by a different route: for a potential parameter the
+    # derivative of exp(-i H T) is the Daleckii-Krein formula in the eigenbasis
+    # of H, Q (Gamma o (Q^T dH Q)) Q^T with the divided differences
+    # Gamma_mn = -i T exp(-i (E_m + E_n) T / 2) sinc((E_m - E_n) T / 2); for a
+    # packet centre q0_k the derivative of the normalised Gaussian factor,
+    # df = dv/|v| - v (v.dv)/|v|^3 with dv = v (x - q0) / (2 s^2).  H is linear
+    # in lambda and quadratic in omega_k, so dH comes from the model itself.
+    # The oracle's central differences (h = 1e-4) must match to O(h^2)
+    # (catches a sign, a parameter-slot mix-up or a one-sided difference).
+    from oracle import adjoint
+    cfg = W.scaled(W.HH4D, D=2, n=16, K=16, dt=0.1, nsteps=10)
+    params = np.array([0.111803, 1.0, 1.3, 1.2, 0.8])
+    D = 2
+    prob = propagate.problem_from_config(cfg, omegas=params[1:3], lam=params[0])
+    full = np.arange(int(np.prod(prob.dims)), dtype=np.int64)
+    sets = [full] * (cfg["nsteps"] + 1)
+    Ttot = cfg["dt"] * cfg["nsteps"]
+    H = _dense_problem_H(prob)
+    E, Q = np.linalg.eigh(H)
+    U = (Q * np.exp(-1j * E * Ttot)) @ Q.T
+    Gam = -1j * Ttot * np.exp(-0.5j * np.add.outer(E, E) * Ttot) \
+        * np.sinc(np.subtract.outer(E, E) * Ttot / (2 * np.pi))
+    f = prob.factors(params[3:5], cfg["p0"], cfg["width"])
+    a0 = pruned.product_on(full, prob.dims, f)
+    C = np.vdot(a0, U @ a0)
+
+    def vd(lam, om):
+        return propagate.problem_from_config(cfg, omegas=om, lam=lam).vdiag(full)
+
+    om = params[1:3]
+    dHs = [vd(1.0, om) - vd(0.0, om)]
+    for k in range(D):
+        om0 = om.copy(); om0[k] = 0.0
+        dHs.append(2.0 * (vd(params[0], om) - vd(params[0], om0)) / om[k])
+    grad = []
+    for dh in dHs:
+        dU = Q @ (Gam * (Q.T @ (dh[:, None] * Q))) @ Q.T
+        grad.append(2.0 * np.real(np.conj(C) * np.vdot(a0, dU @ a0)))
+    s = cfg["width"][0]
+    for k in range(D):
+        x = prob.grids[k]
+        v = np.sqrt(prob.weights[k]) * models.gaussian_1d(x, params[3 + k], 0.0, s).real
+        dv = v * (x - params[3 + k]) / (2 * s * s)
+        nv = np.linalg.norm(v)
+        df = dv / nv - v * (v @ dv) / nv ** 3
+        fk = list(f); fk[k] = df
+        da0 = pruned.product_on(full, prob.dims, fk)
+        dC = np.vdot(da0, U @ a0) + np.vdot(a0, U @ da0)
+        grad.append(2.0 * np.real(np.conj(C) * dC))
+    P, Cor = adjoint.survival(cfg, params, sets)
+    assert abs(Cor - C) < 1e-10 and abs(P - abs(C) ** 2) < 1e-10
+    g = adjoint.fd_gradient(cfg, params, sets, h=1e-4)
+    np.testing.assert_allclose(g, grad, rtol=1e-6, atol=1e-7)
+    assert np.min(np.abs(grad)) > 1e-3          # every slot carries a signal
