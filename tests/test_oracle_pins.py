@@ -110,6 +110,23 @@ def test_henon_heiles_saddle():
         assert abs(models.henon_heiles(qs, lam) - 1 / (6 * lam ** 2)) < 1e-9
 
 
+def test_gaussian_packet_moments():
+    # The packet is fixed by its moments: unit norm, <x> = q0, variance s^2,
+    # and <p> = p0 (from the DFT of the grid values; a real Hamiltonian's C(t)
+    # cannot tell p0 from -p0, so the sign is pinned here).
+    x = np.linspace(-20.0, 20.0, 4096, endpoint=False)
+    dx = x[1] - x[0]
+    k = 2 * np.pi * np.fft.fftfreq(len(x), d=dx)
+    for q0, p0, s in ((0.3, 2.5, 0.7), (-1.0, -4.0, 1.3), (2.0, 0.0, 0.5 ** 0.5)):
+        g = models.gaussian_1d(x, q0, p0, s)
+        rho = np.abs(g) ** 2 * dx
+        assert abs(rho.sum() - 1.0) < 1e-12
+        assert abs((x * rho).sum() - q0) < 1e-12
+        assert abs(((x - q0) ** 2 * rho).sum() - s * s) < 1e-12
+        F = np.abs(np.fft.fft(g)) ** 2
+        assert abs((k * F).sum() / F.sum() - p0) < 1e-10
+
+
 # ------------------------------------------------------------ pruned H.a
 
 def _dense_H(dims, Ts, vfull):
@@ -370,15 +387,17 @@ def _dense_problem_H(prob):
     return _dense_H(dims, prob.Ts, prob.vdiag(full))
 
 
-def test_theta0_is_unpruned_exact_dynamics():
+@pytest.mark.parametrize("p0", [(0.0, 0.0), (0.0, 6.0)])
+def test_theta0_is_unpruned_exact_dynamics(p0):
     # theta = 0: the active set is the full lattice at all times and the pruned
     # run is the exact direct-product propagation (Sec. 3.1: at 100 % basis
     # all methods agree).  K = dim makes SIL exact, so the run must equal
-    # exp(-i H t) a(0) by dense exponential.
+    # exp(-i H t) a(0) by dense exponential.  The moving packet (p0 != 0) has
+    # complex coefficients, so C(t) also checks the conjugated bra of Eq. acorr.
     cfg = W.scaled(W.MORSE2D, n=6)
     prob = propagate.problem_from_config(cfg)
     N = 36
-    r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], 0.0, N, 10.0, 5)
+    r = propagate.run(prob, cfg["q0"], p0, cfg["width"], 0.0, N, 10.0, 5)
     assert all(o["n_active"] == N for o in r["obs"])
     H = _dense_problem_H(prob)
     a0 = pruned.product_on(np.arange(N), prob.dims, r["factors"])
@@ -439,6 +458,26 @@ def test_hh_lambda0_coherent_state_closed_form():
             ref = np.prod([np.exp(-0.5j * t) * np.exp(-(q * q / 2) * (1 - np.exp(-1j * t)))
                            for q in q0])
             assert abs(o["C"] - ref) < tol, (K, s, o["C"], ref)
+            # coherent-state energy: sum_k (q0_k^2 + 1) / 2, conserved
+            assert abs(o["E"] - sum((q * q + 1) / 2 for q in q0)) < 1e-10
+
+
+def test_observables_are_scale_invariant_and_count_wasted():
+    # E is the Rayleigh quotient <a|H|a> / <a|a> (independent of the scale of
+    # a), norm2 = <a|a>, and the wasted count is the number of active
+    # coefficients below theta (brute-force count on a pruned state).
+    cfg = W.scaled(W.MORSE2D, n=16)
+    prob = propagate.problem_from_config(cfg)
+    A, a, f = propagate.initial_state(prob, cfg["q0"], cfg["p0"], cfg["width"], 1e-3)
+    a = sil.sil_step(a, lambda v: prob.apply(A, v), 8, 10.0)
+    o1 = propagate.observables(prob, A, a, f, 1e-3)
+    o2 = propagate.observables(prob, A, 2.0 * a, f, 1e-3)
+    H = _dense_problem_H(prob)[np.ix_(A, A)]
+    assert abs(o1["E"] - np.vdot(a, H @ a).real / np.vdot(a, a).real) < 1e-14
+    assert abs(o2["E"] - o1["E"]) < 1e-14 and abs(o2["norm2"] - 4 * o1["norm2"]) < 1e-13
+    assert abs(o1["norm2"] - sum(abs(complex(v)) ** 2 for v in a)) < 1e-13
+    assert o1["n_wasted"] == sum(1 for v in a if abs(complex(v)) < 1e-3) > 0
+    assert o1["n_active"] == len(A)
 
 
 def test_initial_state_chunked_equals_full_prune():
@@ -450,6 +489,29 @@ def test_initial_state_chunked_equals_full_prune():
     np.testing.assert_array_equal(A, Af)
     np.testing.assert_array_equal(a, af)
     assert abs(np.sum(np.abs(pruned.product_on(full, prob.dims, f)) ** 2) - 1) < 1e-13
+
+
+@pytest.mark.parametrize("radius", [1, 2])
+def test_run_sets_are_adaption_fixed_points(radius):
+    # After every adaption (Sec. 2.5) the members of S = {|a| >= theta} keep
+    # their coefficients and the added neighbours are below theta (zero or
+    # carried), so the significant set of the adapted state is S again and the
+    # active set must be exactly S plus its neighbours under the run's rule.
+    # Checked on the recorded state of every step of a pruned run.
+    cfg = W.scaled(W.MORSE2D, n=16)
+    prob = propagate.problem_from_config(cfg)
+    theta = 1e-4
+    A, a, f = propagate.initial_state(prob, cfg["q0"], cfg["p0"], cfg["width"], theta, radius)
+    state = (A, a, f)
+    for step in range(6):
+        A, a, _ = state
+        np.testing.assert_array_equal(
+            A, pruned.adapt_set(A[pruned.significant(a, theta)], prob.axes, radius))
+        r = propagate.run(prob, cfg["q0"], cfg["p0"], cfg["width"], theta, 8, 10.0, 3,
+                          radius=radius, state=state)
+        assert r["obs"][-1]["n_active"] == len(r["A"])
+        state = (r["A"], r["a"], f)
+    assert 0 < len(state[0]) < 16 * 16
 
 
 def test_pruned_infidelity_decreases_with_theta():
