@@ -164,3 +164,16 @@ def test_host_pw_basis_matches_oracle():
         pq.Basis([dict(kind=pq.PW, n=16, xmin=0.5, xmax=6.0, mass=1.0, nx_lattice=4, np_lattice=3)])
     assert e.value.status == pq.EINVAL
     b.set_sop(pq.coupled_morse_terms([xl, xl], 0.1, 1.0, 2.0, 0.005))
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # no CPU fallback: with the shared library absent the package refuses to
+    # import (checked in a child process so this one keeps its library)
+    import subprocess
+    import sys
+    code = ("import paper_1606_04004_gb300\n")
+    env = dict(os.environ, PQ_LIBRARY=str(tmp_path / "absent" / "libprunedq.so"))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "is missing" in r.stderr
