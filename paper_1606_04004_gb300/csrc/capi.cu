@@ -77,6 +77,14 @@ static void free_state(State* s) {
     g_live_states.fetch_sub(1);
 }
 
+// Status of a CUDA call made while an object is being built (the caller
+// frees what it built so far).
+static pq_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return PQ_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return PQ_ECUDA;
+}
+
 template <typename T>
 static pq_status dalloc(T** p, size_t bytes) {
     *p = static_cast<T*>(dev_alloc(bytes, 0, false));
@@ -338,21 +346,25 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
         return rc;
     }
     if (L.nlast <= 32 && L.nrows <= (1u << 28)) {
-        if ((rc = dalloc(&s->rowinfo, (size_t)L.nrows * sizeof(uint2)))) {
+        if ((rc = dalloc(&s->rowinfo, (size_t)L.nrows * sizeof(uint2))) ||
+            (rc = cuda_status(cudaMemset(s->rowinfo, 0, (size_t)L.nrows * sizeof(uint2)),
+                              "clearing the row table"))) {
             free_state(s);
             return rc;
         }
-        cudaMemset(s->rowinfo, 0, (size_t)L.nrows * sizeof(uint2));
     }
     if (cudaMallocHost((void**)&s->h_cnt, CNT_SIZE * 8) != cudaSuccess) {
         set_error("cudaMallocHost failed");
         free_state(s);
         return PQ_ENOMEM;
     }
-    cudaMemset(s->cnt, 0, CNT_SIZE * 8);
-    cudaMemset(s->bits, 0, nw * 8);
-    cudaMemset(s->off, 0, (nw + 1) * 4);
-    cudaMemset(s->ks, 0, sizeof(KrylovScalars));
+    if ((rc = cuda_status(cudaMemset(s->cnt, 0, CNT_SIZE * 8), "clearing the counters")) ||
+        (rc = cuda_status(cudaMemset(s->bits, 0, nw * 8), "clearing the bitmap")) ||
+        (rc = cuda_status(cudaMemset(s->off, 0, (nw + 1) * 4), "clearing the rank table")) ||
+        (rc = cuda_status(cudaMemset(s->ks, 0, sizeof(KrylovScalars)), "clearing the scalars"))) {
+        free_state(s);
+        return rc;
+    }
     if ((rc = basis->generic ? upload_generic(*s) : upload_hamiltonian(*s)) ||
         (basis->pvb && (rc = upload_pvb(*s)))) {
         free_state(s);
@@ -361,12 +373,14 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
     if (!basis->vgrid.empty()) {   // tabulated diagonal potential (DVR bases only)
         const size_t nv = basis->vgrid.size();
         std::vector<float> v32(basis->vgrid.begin(), basis->vgrid.end());
-        if ((rc = dalloc(&s->vgrid64, nv * 8)) || (rc = dalloc(&s->vgrid32, nv * 4))) {
+        if ((rc = dalloc(&s->vgrid64, nv * 8)) || (rc = dalloc(&s->vgrid32, nv * 4)) ||
+            (rc = cuda_status(cudaMemcpy(s->vgrid64, basis->vgrid.data(), nv * 8,
+                                         cudaMemcpyHostToDevice), "uploading the potential")) ||
+            (rc = cuda_status(cudaMemcpy(s->vgrid32, v32.data(), nv * 4, cudaMemcpyHostToDevice),
+                              "uploading the potential"))) {
             free_state(s);
             return rc;
         }
-        cudaMemcpy(s->vgrid64, basis->vgrid.data(), nv * 8, cudaMemcpyHostToDevice);
-        cudaMemcpy(s->vgrid32, v32.data(), nv * 4, cudaMemcpyHostToDevice);
     }
     *out = s;
     return PQ_OK;
@@ -684,22 +698,25 @@ PQ_API pq_status pq_init_packet(const pq_basis* basis_, const double* q0, const 
     std::vector<double> fac;
     packet_factors(*b, q0, p0, width, fac, s->lead_virtual);
     std::vector<float> fac32(fac.begin(), fac.end());
-    if ((rc = dalloc(&s->fac64, fac.size() * 8)) || (rc = dalloc(&s->fac32, fac32.size() * 4))) {
+    if ((rc = dalloc(&s->fac64, fac.size() * 8)) || (rc = dalloc(&s->fac32, fac32.size() * 4)) ||
+        (rc = cuda_status(cudaMemcpy(s->fac64, fac.data(), fac.size() * 8, cudaMemcpyHostToDevice),
+                          "uploading the packet")) ||
+        (rc = cuda_status(cudaMemcpy(s->fac32, fac32.data(), fac32.size() * 4,
+                                     cudaMemcpyHostToDevice), "uploading the packet"))) {
         free_state(s);
         return rc;
     }
-    cudaMemcpy(s->fac64, fac.data(), fac.size() * 8, cudaMemcpyHostToDevice);
-    cudaMemcpy(s->fac32, fac32.data(), fac32.size() * 4, cudaMemcpyHostToDevice);
     if (b->pvb) {   // bra of the autocorrelation: B^dagger f per mode
         std::vector<double> bra;
         Basis tmp = *b;
         tmp.Gc = b->Bc;
         packet_factors(tmp, q0, p0, width, bra, s->lead_virtual);
-        if ((rc = dalloc(&s->fac_bra64, bra.size() * 8))) {
+        if ((rc = dalloc(&s->fac_bra64, bra.size() * 8)) ||
+            (rc = cuda_status(cudaMemcpy(s->fac_bra64, bra.data(), bra.size() * 8,
+                                         cudaMemcpyHostToDevice), "uploading the packet bra"))) {
             free_state(s);
             return rc;
         }
-        cudaMemcpy(s->fac_bra64, bra.data(), bra.size() * 8, cudaMemcpyHostToDevice);
     }
     s->theta = theta;
     s->radius = radius;
@@ -744,8 +761,9 @@ PQ_API pq_status pq_state_load(pq_state* state, const int64_t* idx, int64_t n, c
     uint32_t* dk = nullptr;
     pq_status rc = dalloc(&dk, (size_t)n * 4);
     if (rc) return rc;
-    cudaMemcpy(dk, k32.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
-    rc = load_set(*s, dk, n, 0);
+    rc = cuda_status(cudaMemcpy(dk, k32.data(), (size_t)n * 4, cudaMemcpyHostToDevice),
+                     "uploading the index list");
+    if (!rc) rc = load_set(*s, dk, n, 0);
     cudaDeviceSynchronize();
     dev_free(dk, 0, false);
     if (rc) return rc;
