@@ -102,7 +102,25 @@ MUTANTS = [
     ("pvb_biorthogonal_no_conjugate", "oracle.bases", "pvb_basis",
      "B = np.linalg.inv(G).conj().T", "B = np.linalg.inv(G).T",
      [P.test_pvb_biorthogonal]),
+    ("sine_dvr_weight", "oracle.bases", "sine_dvr",
+     "w = np.full(n, L / (n + 1))", "w = np.full(n, L / n)",
+     [lambda: P.test_pvb_functions_closed_form_moments("sine")]),
+    ("fgh_weight", "oracle.bases", "fgh_dvr",
+     "w = np.full(n, L / n)", "w = np.full(n, L / (n + 1))",
+     [P.test_fgh_free_particle_spectrum]),
+    ("ho_sign_convention_dropped", "oracle.bases", "ho_dvr",
+     "U = U * np.sign(U[0, :])[None, :]", "U = U",
+     [P.test_hh_lambda0_coherent_state_closed_form]),
+    ("pvb_alpha", "oracle.bases", "pvb_basis",
+     "alpha = dp / (2.0 * dx)", "alpha = dp / dx",
+     [lambda: P.test_pvb_functions_closed_form_moments("sine")]),
     # ----------------------------------------------------------- models
+    ("hh_harmonic_half_dropped", "oracle.models", "henon_heiles",
+     "v = 0.5 * np.sum((om * q) ** 2, axis=-1)", "v = np.sum((om * q) ** 2, axis=-1)",
+     [P.test_henon_heiles_saddle]),
+    ("morse_coupling_sign", "oracle.models", "coupled_morse",
+     "v = v + coupling * q[..., i] * q[..., j]", "v = v - coupling * q[..., i] * q[..., j]",
+     [P.test_pw_theta0_matches_dvr_dynamics]),
     ("hh_cubic_sign", "oracle.models", "henon_heiles",
      "(a * a * b - b ** 3 / 3.0)", "(a * a * b + b ** 3 / 3.0)",
      [P.test_henon_heiles_saddle]),
@@ -119,6 +137,22 @@ MUTANTS = [
      "+ 1j * p0 * (x - q0)", "- 1j * p0 * (x - q0)",
      [P.test_gaussian_packet_moments]),
     # ----------------------------------------------------------- pruned
+    ("digits_column_major", "oracle.pruned", "digits",
+     "np.unravel_index(np.asarray(A, dtype=np.int64), dims)",
+     "np.unravel_index(np.asarray(A, dtype=np.int64), dims, order=\"F\")",
+     [lambda: P.test_lattice_helpers_match_library_constructions((4, 4, 4))]),
+    ("potential_modes_reversed", "oracle.pruned", "potential_diag",
+     "np.asarray(grids[k])[dg[k]]", "np.asarray(grids[k])[dg[len(dims) - 1 - k]]",
+     [lambda: P.test_lattice_helpers_match_library_constructions((4, 4, 4))]),
+    ("product_modes_reversed", "oracle.pruned", "product_on",
+     "np.asarray(factors[k])[dg[k]]", "np.asarray(factors[k])[dg[len(dims) - 1 - k]]",
+     [lambda: P.test_lattice_helpers_match_library_constructions((4, 4, 4))]),
+    ("lookup_without_key_check", "oracle.pruned", "lookup",
+     "found = (pos < len(A)) & (A[pos_c] == keys)", "found = (pos < len(A))",
+     [P.test_pruned_apply_at_sample_equals_full]),
+    ("adapt_offset_sign_dropped", "oracle.pruned", "adapt_set",
+     "delta += d * st[a]", "delta += st[a]",
+     [lambda: P.test_prune_bruteforce((4, 3, 5), 1)]),
     ("strides_wrong_extent", "oracle.pruned", "strides_of",
      "s[k] = s[k + 1] * int(dims[k + 1])", "s[k] = s[k + 1] * int(dims[k])",
      [lambda: P.test_pruned_apply_equals_PHP((4, 5, 3), 0.4, 2)]),
@@ -225,6 +259,15 @@ MUTANTS = [
      "terms.append((2.0 * coupling, {i: grids[i], j: grids[j]}))",
      [P.test_pw_theta0_matches_dvr_dynamics]),
     # -------------------------------------------------------------- pvb
+    ("pvb_lanczos_euclidean_norm", "oracle.pvb", "sil_step_S",
+     "b = np.sqrt(max(np.vdot(w, prob.S_AA(A, w)).real, 0.0))", "b = np.linalg.norm(w)",
+     [P.test_pvb_theta0_matches_dvr_dynamics]),
+    ("pvb_start_euclidean_norm", "oracle.pvb", "sil_step_S",
+     "beta0 = np.sqrt(max(np.vdot(a, Sa).real, 0.0))", "beta0 = np.linalg.norm(a)",
+     [P.test_pvb_theta0_matches_dvr_dynamics]),
+    ("pvb_norm_without_overlap", "oracle.pvb", "run",
+     "n2 = float(np.vdot(a, prob.S_AA(A, a)).real)", "n2 = float(np.vdot(a, a).real)",
+     [P.test_pvb_theta0_matches_dvr_dynamics]),
     ("pvb_H_no_conjugate", "oracle.pvb", "PVBProblem.H_AA",
      "self.Bs[k].conj().T", "self.Bs[k].T",
      [P.test_pvb_theta0_matches_dvr_dynamics]),
@@ -241,6 +284,12 @@ MUTANTS = [
      "c = [np.vdot(v, Sw) for v in V]", "c = [np.vdot(v, w) for v in V]",
      [P.test_pvb_theta0_matches_dvr_dynamics]),
     # ---------------------------------------------------------- adjoint
+    ("adjoint_carry_conjugated", "oracle.adjoint", "run_frozen",
+     "b[found] = a[pos[found]]", "b[found] = a[pos[found]].conj()",
+     [P.test_adjoint_frozen_replay_equals_dense_products]),
+    ("sil_beta_squared", "oracle.sil", "sil_step",
+     "b = np.linalg.norm(w)", "b = np.linalg.norm(w) ** 2",
+     [P.test_sil_full_krylov_is_exact_exponential]),
     ("adjoint_set_one_step_off", "oracle.adjoint", "run_frozen",
      "An = np.asarray(sets[n + 1], dtype=np.int64)", "An = np.asarray(sets[n], dtype=np.int64)",
      [P.test_adjoint_frozen_replay_equals_dense_products]),

@@ -180,6 +180,34 @@ def test_pruned_apply_at_sample_equals_full():
                                rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4), (3, 5, 4)])
+def test_lattice_helpers_match_library_constructions(dims):
+    # Row-major lattice bookkeeping against numpy's own constructions:
+    # strides and digits (ravel_multi_index / indices by another route), V on
+    # the full lattice against meshgrid(indexing="ij"), and the product packet
+    # against a chain of Kronecker products.  Equal mode sizes make a reversed
+    # mode order give wrong numbers rather than an index error; an asymmetric
+    # V and distinct factors make it visible.
+    N = int(np.prod(dims))
+    full = np.arange(N, dtype=np.int64)
+    st = pruned.strides_of(dims)
+    for e in itertools.product(*[range(d) for d in dims]):
+        assert sum(i * s for i, s in zip(e, st)) == np.ravel_multi_index(e, dims)
+    np.testing.assert_array_equal(pruned.digits(full, dims),
+                                  np.indices(dims).reshape(len(dims), -1))
+    rng = np.random.default_rng(21)
+    grids = [np.sort(rng.uniform(-1, 1, d)) for d in dims]
+    vf = lambda q: q[..., 0] + 10 * q[..., 1] ** 2 + 100 * q[..., 2] ** 3
+    mesh = np.stack(np.meshgrid(*grids, indexing="ij"), axis=-1)
+    np.testing.assert_allclose(pruned.potential_diag(full, dims, grids, vf),
+                               vf(mesh).ravel(), rtol=1e-15, atol=1e-15)
+    facs = [rng.standard_normal(d) + 1j * rng.standard_normal(d) for d in dims]
+    dense = np.kron(np.kron(facs[0], facs[1]), facs[2])
+    np.testing.assert_allclose(pruned.product_on(full, dims, facs), dense, rtol=1e-15)
+    A = W.random_active_set(dims, 0.5, 22)
+    np.testing.assert_allclose(pruned.product_on(A, dims, facs), dense[A], rtol=1e-15)
+
+
 def test_pruned_apply_empty():
     y = pruned.apply_H(np.zeros(0, np.int64), np.zeros(0, complex), (3, 4),
                        [np.eye(3), np.eye(4)], np.zeros(0))
