@@ -53,7 +53,7 @@ typedef enum pq_basis_kind {
     PQ_HO_DVR = 1,    /* harmonic-oscillator (Gauss-Hermite) DVR (Sec. 3.3)       */
     PQ_PVB = 2,       /* biorthogonal projected von Neumann basis (Sec. 2.2)      */
     PQ_PW = 3,        /* projected Weylets (Sec. 2.4)                             */
-    PQ_FGH_DVR = 4    /* Fourier grid DVR on a periodic box (Sec. 2.2, Sec. 3.2)  */
+    PQ_FGH_DVR = 4    /* Fourier grid DVR on a periodic box (Sec. 2.2, Sec. 3.1)  */
 } pq_basis_kind;
 
 typedef enum pq_precision {
@@ -82,7 +82,7 @@ typedef enum pq_neighbour_rule {
  *  omega  frequency of the HO-DVR's underlying oscillator (with `mass`).
  *  nx_lattice, np_lattice  phase-space lattice of pvB / pW modes (unused for DVRs).
  *  dvr    underlying DVR of a pvB / pW mode: PQ_SINE_DVR (0, default) or
- *         PQ_FGH_DVR (Sec. 3.2 builds both phase-space bases on the FGH grid).
+ *         PQ_FGH_DVR (Sec. 3.1 builds both phase-space bases on the FGH grid).
  */
 typedef struct pq_mode_desc {
     int kind;

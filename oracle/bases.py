@@ -37,7 +37,7 @@ def sine_dvr(n: int, xmin: float, xmax: float, mass: float):
 def fgh_dvr(n: int, xmin: float, xmax: float, mass: float):
     """Fourier grid Hamiltonian DVR on the periodic box [xmin, xmax) (Sec. 2.2:
     the FGH DVR, whose functions cover the same phase-space area as a
-    periodic lattice; the double-well grids of Sec. 3.2).
+    periodic lattice; the double-well grids of Sec. 3.1).
 
     Points x_j = xmin + j L/n, j = 0..n-1 (xmax is identified with xmin),
     weight w = L/n.  The kinetic matrix is p^2/2m in the discrete Fourier
@@ -91,7 +91,8 @@ def ho_dvr(n: int, mass: float = 1.0, omega: float = 1.0):
 
 def pw_functions(x, w, xmin, xmax, nx, np_):
     """The momentum-symmetrised Gaussians of Eq. sG_def projected on a DVR with
-    points x and weights w (Sec. 2.4), before orthogonalisation.
+    points x and weights w (Eq. sG_def of Sec. 2.3, projected as in Eq. psG_def of
+    Sec. 2.4), before orthogonalisation.
 
     Doubly dense phase-space lattice (Delta x Delta p = pi, p_l > 0):
     x_a = xmin + (a + 1/2) Dx with Dx = (xmax - xmin) / nx, p_b = (b + 1/2) Dp
@@ -119,7 +120,7 @@ def pw_functions(x, w, xmin, xmax, nx, np_):
 
 def pw_basis(n, xmin, xmax, mass, nx, np_, dvr="sine"):
     """Projected Weylets on a sine DVR, or on an FGH DVR with dvr="fgh" (Sec. 2.4;
-    Sec. 3.2 uses the FGH grid).
+    Sec. 3.1 uses the FGH grid).
 
     The projected symmetrised Gaussians Phi (``pw_functions``, Eq. sG_def) are
     orthogonalised symmetrically (Loewdin): W = Phi S^(-1/2), S = Phi^T Phi.
@@ -137,7 +138,7 @@ def pw_basis(n, xmin, xmax, mass, nx, np_, dvr="sine"):
 
 def pvb_basis(n, xmin, xmax, mass, nx, np_, dvr="sine"):
     """Biorthogonal projected von Neumann basis on a sine DVR, or on an FGH
-    DVR with dvr="fgh" (Sec. 2.2; Sec. 3.2 uses the FGH grid).
+    DVR with dvr="fgh" (Sec. 2.2; Sec. 3.1 uses the FGH grid).
 
     von Neumann Gaussians on a lattice with Delta x Delta p = 2 pi:
     x_a = xmin + (a + 1/2) Dx, Dx = L / nx, Dp = 2 pi / Dx, momenta

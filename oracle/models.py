@@ -3,7 +3,7 @@ coordinates (the oracle never uses a sum-of-products form for V: a DVR
 potential is diagonal, Sec. 2.1, so V_II = V(x_I) is all that is needed).
 
 The coupled Morse and Henon-Heiles models are synthetic stand-ins the
-workloads define; the double well is the paper's own model (Sec. 3.2).
+workloads define; the double well is the paper's own model (Sec. 3.1).
 """
 from __future__ import annotations
 
@@ -37,7 +37,7 @@ def coupled_morse(q: np.ndarray, De: float, a: float, qe: float,
 
 
 def double_well(q: np.ndarray, c1: float = 6.4, c2: float = 37.5, c3: float = 10.0) -> np.ndarray:
-    """The 2D double well of Sec. 3.2 (Eq. ex_dwell), q of shape (..., 2):
+    """The 2D double well of Sec. 3.1 (Eq. ex_dwell), q of shape (..., 2):
     V = c1 (x-1)^2 (x-2)^2 + c2 (y-2)^2 + c3 x^2 y."""
     q = np.asarray(q, dtype=np.float64)
     x, y = q[..., 0], q[..., 1]

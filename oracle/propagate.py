@@ -93,7 +93,7 @@ def pw_problem_from_config(cfg, n=None, nx=None, np_=None):
 
 
 def dwell_pw_problem(cfg):
-    """pW problem of the double well (Sec. 3.2): projected Weylets on the FGH
+    """pW problem of the double well (Sec. 3.1): projected Weylets on the FGH
     grids of each mode, the double-well SoP terms transformed by congruence."""
     xs, ws, Ts, Wm, lat = [], [], [], [], []
     for k in range(cfg["D"]):

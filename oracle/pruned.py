@@ -61,7 +61,7 @@ def lookup(A, keys):
 
 def potential_diag(A, dims, grids, vfunc):
     """V_II = V(x_I) at every active point (DVR potential is diagonal,
-    Sec. 2.1 and Sec. 2.4)."""
+    Sec. 2.1 and Sec. 2.5)."""
     dg = digits(A, dims)
     q = np.stack([np.asarray(grids[k])[dg[k]] for k in range(len(dims))], axis=-1)
     return vfunc(q)

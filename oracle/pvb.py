@@ -33,7 +33,7 @@ def mode_transform(X, M, k):
 class PVBProblem:
     """pvB problem of a workload record: the 3D coupled Morse on sine DVRs
     (uniform modes; n, nx, np may be overridden), or the double well of
-    Sec. 3.2 on its FGH grids (per-mode sizes, ``dvr="fgh"``)."""
+    Sec. 3.1 on its FGH grids (per-mode sizes, ``dvr="fgh"``)."""
 
     def __init__(self, cfg, n=None, nx=None, np_=None):
         self.cfg = cfg

@@ -1828,7 +1828,7 @@ static pq_status launch_outer_reg(ApplyArgs<R> a, int G, cudaStream_t st) {
 
 // ------------------------------------------------------------------------
 // Point-parallel pass for lattices with a mode longer than the tiled kernels
-// take (n > 64, e.g. the FGH grids of the double well, Sec. 3.2): one thread
+// take (n > 64, e.g. the FGH grids of the double well, Sec. 3.1): one thread
 // per active point forms the whole pruned product for its point, every mode's
 // fibre found by bitmap tests and rank queries on the fly, the SoP potential
 // evaluated from the per-mode tables.  Meant for small lattices.

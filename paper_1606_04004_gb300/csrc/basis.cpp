@@ -185,7 +185,7 @@ static int ho_dvr(int n, double mass, double omega, std::vector<double>& x,
 }
 
 // Projected Weylets (Sec. 2.4) on a sine or FGH DVR: momentum-symmetrised Gaussians
-// (Eq. sG_def) on the doubly dense lattice Dx Dp = pi (x_a cell-centred,
+// (Eq. sG_def, Sec. 2.3) on the doubly dense lattice Dx Dp = pi (x_a cell-centred,
 // p_b = (b + 1/2) Dp > 0, alpha = Dp / (2 Dx)), projected on the DVR
 // (Phi_ji = sqrt(w_j) phi_i(x_j), i = a np + b) and orthogonalised
 // symmetrically: W = Phi S^(-1/2), S = Phi^T Phi.  W (n x n, row-major) maps

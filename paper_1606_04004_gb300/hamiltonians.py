@@ -1,11 +1,11 @@
 """Sum-of-products forms of the model Hamiltonians, tabulated on the
-library's DVR grids (host set-up; Sec. 2.2.2 SoP form, Sec. 2.4: in a DVR the
-potential is a sum of products of diagonal factors).
+library's DVR grids (host set-up; Sec. 2.2.2 SoP form, Sec. 2.5: for a pruned DVR
+the potential is a sum of products of diagonal factors).
 
 Kinetic energy: one term per mode with the mode's kinetic factor.
 Henon-Heiles chain: sum_k 1/2 omega_k^2 q_k^2 + lam sum_{k<D} (q_k^2 q_{k+1} - q_{k+1}^3 / 3).
 Coupled Morse:      sum_k De (1 - exp(-a (q_k - qe)))^2 + c sum_{i<j} q_i q_j.
-Double well (Sec. 3.2, Eq. ex_dwell): c1 (x-1)^2 (x-2)^2 + c2 (y-2)^2 + c3 x^2 y.
+Double well (Sec. 3.1, Eq. ex_dwell): c1 (x-1)^2 (x-2)^2 + c2 (y-2)^2 + c3 x^2 y.
 """
 from __future__ import annotations
 

@@ -2,7 +2,6 @@
 (median SM clock, throttle reasons), the roofline peak lookup and the rule
 that the ncu traffic figure is reported only for the kernel source it was
 measured on."""
-import hashlib
 import json
 import os
 
@@ -51,20 +50,41 @@ def test_peak_is_the_measured_copy_bandwidth(tmp_path, monkeypatch):
     assert bench._peaks() == (6800.0, "fallback")
 
 
+def test_code_digest_ignores_comments_and_whitespace_only(tmp_path):
+    a = tmp_path / "a.cu"
+    a.write_text("// header\n__global__ void k(float* x) { x[0] = 1.0f; }  /* a\nb */\n")
+    b = tmp_path / "b.cu"
+    b.write_text("// another header\n__global__ void k(float* x)\n{\n    x[0] = 1.0f;   // set\n}\n")
+    c = tmp_path / "c.cu"
+    c.write_text("__global__ void k(float* x) { x[0] = 2.0f; }\n")
+    assert bench.code_digest(a) == bench.code_digest(b)
+    assert bench.code_digest(a) != bench.code_digest(c)
+
+
 def test_traffic_record_only_for_the_measured_source(tmp_path, monkeypatch):
     src = tmp_path / "paper_1606_04004_gb300" / "csrc"
     src.mkdir(parents=True)
     (tmp_path / "profiles").mkdir()
-    (src / "apply_h.cu").write_bytes(b"// kernel v1\n")
-    h = hashlib.sha256(b"// kernel v1\n").hexdigest()
-    rec = {"apply_h_sha256": h, "dram_bytes_per_coef": 100.0}
+    (src / "apply_h.cu").write_text("// kernel v1\nint k;\n")
+    rec = {"apply_h_code_sha256": bench.code_digest(src / "apply_h.cu"),
+           "dram_bytes_per_coef": 100.0}
     (tmp_path / "profiles" / "apply_h_hh6d_traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench._traffic_record()["dram_bytes_per_coef"] == 100.0
-    (src / "apply_h.cu").write_bytes(b"// kernel v2\n")      # source changed since
+    (src / "apply_h.cu").write_text("// kernel v1, comment edited\nint  k;\n")
+    assert bench._traffic_record()["dram_bytes_per_coef"] == 100.0
+    (src / "apply_h.cu").write_text("// kernel v2\nint k2;\n")      # code changed since
     assert bench._traffic_record() is None
     os.remove(tmp_path / "profiles" / "apply_h_hh6d_traffic.json")
     assert bench._traffic_record() is None
+
+
+def test_committed_traffic_record_matches_the_kernel_source():
+    # the committed counters were taken on the H.psi kernels as they are now
+    rec = bench._traffic_record()
+    assert rec is not None, ("apply_h.cu changed since the ncu traffic capture: re-take it, "
+                             "or the bench reports traffic as null")
+    assert 20 < rec["dram_bytes_per_coef"] < 200
 
 
 def test_algorithmic_bytes_per_coefficient():

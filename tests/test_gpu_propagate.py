@@ -134,7 +134,7 @@ def test_morse2d_fp64_neighbour_rules(rule, rho):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_double_well_steps(prec):
-    # the paper's double well (Sec. 3.2) on its FGH grids of 165 x 81 points:
+    # the paper's double well (Sec. 3.1) on its FGH grids of 165 x 81 points:
     # FP64 identical active sets and C(t) within 1e-10 of the oracle; FP32-mix
     # C(t) within 1e-5
     pq = lib()

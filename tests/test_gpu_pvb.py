@@ -100,7 +100,7 @@ def test_pvb_morse3d_initial_state_and_H():
 
 
 def test_pvb_double_well():
-    """The double well of Sec. 3.2 in pvB on its FGH grids (165- and
+    """The double well of Sec. 3.1 in pvB on its FGH grids (165- and
     81-function modes: the long-mode full-grid transforms): H_AA of the initial
     state and three propagation steps against the oracle (FP64)."""
     import torch

@@ -109,7 +109,7 @@ def test_pw_propagation_fp64(name, D, n, nx, np_, nsteps):
 
 
 def test_pw_double_well_propagation_fp64():
-    # the double well of Sec. 3.2 in projected Weylets on its FGH grids
+    # the double well of Sec. 3.1 in projected Weylets on its FGH grids
     # (165 and 81 functions per mode: point-parallel passes): identical active
     # sets on the (15 x 11) x (9 x 9) phase-space lattice, C(t) within 1e-10
     from oracle import propagate

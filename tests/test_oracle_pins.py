@@ -453,7 +453,7 @@ def test_autocorrelation_2t_identity():
 
 
 def test_double_well_autocorrelation_2t_identity():
-    # Eq. acorr on the paper's own double well (Sec. 3.2, real packet, real
+    # Eq. acorr on the paper's own double well (Sec. 3.1, real packet, real
     # FGH DVR, theta = 0): C(2t) = sum_I a_I(t)^2, at the full grid of 13365
     # points (catches a wrong potential sign or a complex-conjugation slip).
     cfg = W.DWELL2D
@@ -612,7 +612,7 @@ def test_pw_functions_closed_form_moments(dvr):
 
 
 def test_pw_is_loewdin_orthogonalisation():
-    # Sec. 2.4: W is the symmetric (Loewdin) orthogonalisation of Phi.  Polar
+    # Sec. 2.3-2.4: W is the symmetric (Loewdin) orthogonalisation of Phi.  Polar
     # decomposition: W orthogonal and W^T Phi symmetric positive definite fix W
     # uniquely (catches Gram-Schmidt / QR, a transposed U or S^(+1/2)).
     for dvr, (n, lo, hi, nx, np_) in (("sine", (16, 0.5, 6.0, 4, 4)),
@@ -730,7 +730,7 @@ def test_pw_theta0_matches_dvr_dynamics():
 
 
 def test_pw_on_fgh_theta0_matches_fgh_dynamics():
-    # Sec. 3.2 builds the projected Weylets on the FGH grid; at 100 % basis
+    # Sec. 3.1 builds the projected Weylets on the FGH grid; at 100 % basis
     # they reproduce the FGH DVR dynamics of the double well (small grids).
     cfg = W.scaled(W.DWELL2D, n=(20, 12))
     pcfg = W.scaled(W.DWELL2D_PW, n=(20, 12), nx_lattice=(5, 4), np_lattice=(4, 3))
@@ -760,7 +760,7 @@ def test_pvb_cg_solves_overlap():
 
 
 def test_pvb_on_fgh_theta0_matches_fgh_dynamics():
-    # Sec. 3.2 builds pvB on the FGH grid; at 100 % basis it reproduces the FGH
+    # Sec. 3.1 builds pvB on the FGH grid; at 100 % basis it reproduces the FGH
     # DVR dynamics of the double well (small grids, per-mode sizes).
     from oracle import pvb
     cfg = W.scaled(W.DWELL2D, n=(20, 12))

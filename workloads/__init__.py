@@ -19,7 +19,7 @@ Workloads (parameters in atomic units unless stated):
 * ``morse3d`` -- 3D coupled Morse (pairwise 0.005 q_i q_j), 64-point sine-DVR
   per mode, phase-space lattices of 8 x 8 per mode, seed-drawn packet centres.
 * ``adjoint4d`` -- the hh4d model, T = 20, checkpoint every 25 steps.
-* ``dwell2d`` -- the two-dimensional double well of Sec. 3.2 as printed there
+* ``dwell2d`` -- the two-dimensional double well of Sec. 3.1 as printed there
   (mass 200, potential coefficients 6.4, 37.5 and 10, packet centre (2.1, 2.05)
   with exponents 1/0.04 and 1/0.02, final time 24.6) on FGH grids of 165
   points on [-0.5, 3.7) and 81 points on [1.0, 2.9); SIL order 10, dt = 0.01
@@ -27,7 +27,7 @@ Workloads (parameters in atomic units unless stated):
   2460 steps.
 * ``dwell2d_pw`` / ``dwell2d_pvb`` -- the same double well in projected
   Weylets / in the biorthogonal projected von Neumann basis, built on those FGH
-  grids (Sec. 3.2): phase-space lattices 15 x 11 (x) and 9 x 9 (y).
+  grids (Sec. 3.1): phase-space lattices 15 x 11 (x) and 9 x 9 (y).
 """
 from __future__ import annotations
 
