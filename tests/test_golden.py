@@ -47,3 +47,35 @@ def test_neighbour_counts_in_phase_space():
         c = np.array([int(np.ravel_multi_index((2,) * (2 * D), axes))])
         assert len(pruned.adapt_set(c, axes, pruned.RADIUS_2)) - 1 == 3 ** (2 * D) - 1
         assert len(pruned.adapt_set(c, axes, pruned.RADIUS_1)) - 1 == 2 * (2 * D)
+
+
+def _printed(total, me):
+    """The total as the paper prints it, ~m x 10^e (digits truncated)."""
+    m, e = me
+    return int(total // 10 ** e) == m
+
+
+def test_printed_basis_sizes_are_consistent():
+    # the per-mode sizes of Table I multiply (times the two electronic states)
+    # to the printed total of about 322 x 10^6; the NO2 basis (two radial FGH
+    # modes of 13 x 13 and an angular 10 x 10) to about 285 x 10^4
+    py = GOLD["pyrazine_basis"]
+    n = [a * b for a, b in zip(py["nx"], py["np"])]
+    total = int(np.prod(n)) * py["electronic_states"]
+    assert _printed(total, py["total_printed_mantissa_exponent"])
+    no2 = GOLD["no2_basis"]
+    r = no2["radial_nx_np"][0] * no2["radial_nx_np"][1]
+    t = r ** no2["radial_coordinates"] * no2["angular_nx_np"][0] * no2["angular_nx_np"][1]
+    assert _printed(t, no2["total_printed_mantissa_exponent"])
+
+
+def test_hh6d_workload_is_pyrazine_sized():
+    # the 6D throughput workload stands in for the 6D pyrazine benchmark: six
+    # modes and a direct-product lattice within a factor 1.5 of pyrazine's
+    # per-electronic-state basis (24^6 = 1.91e8 against 1.61e8)
+    py = GOLD["pyrazine_basis"]
+    per_state = int(np.prod([a * b for a, b in zip(py["nx"], py["np"])]))
+    cfg = W.HH6D
+    assert cfg["D"] == len(py["modes"])
+    ratio = cfg["n"] ** cfg["D"] / per_state
+    assert 1 / 1.5 < ratio < 1.5
