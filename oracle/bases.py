@@ -1,12 +1,11 @@
 """1D primitive bases of the oracle (FP64).
 
-Sec. 2.1 (Eq. of the direct-product expansion and the DVR remarks): a DVR
-basis chi_j has grid points x_j and weights w_j such that the coefficient of a
-wavefunction is a_j = sqrt(w_j) psi(x_j); the potential is diagonal.
-Sec. 2.2 (Eq. pvN_def): "omega_j = W_j / omega(x_j)" -- the weight used in the
-projection is the quadrature weight divided by the weight function of the
-DVR polynomials; for both DVRs below it is the factor that turns grid values
-into coefficients.
+Sec. 2.1 (Eq. wavepacket_form): the wavefunction is expanded in direct
+products of DVR functions chi_j with grid points x_j, in which the potential is
+diagonal.  Sec. 2.2 (Eq. pvN_def): a function f projects onto chi_j with the
+coefficient sqrt(w_j) f(x_j), where w_j is the quadrature weight divided by the
+weight function of the DVR polynomials; for the DVRs below it is the weight
+returned with the grid.
 """
 from __future__ import annotations
 

@@ -136,7 +136,7 @@ def problem_from_config(cfg, omegas=None, lam=None):
 
 
 def initial_state(prob, q0, p0, width, theta, radius=1, chunk=1 << 22):
-    """Projected, normalised product packet (Sec. 2.1) and its initial prune
+    """Projected (Eq. pvN_def), normalised product packet and its initial prune
     (Sec. 2.5 applied to the full lattice).  Returns (A, a, factors) where the
     factors are the per-mode normalised packet vectors (the full-lattice packet
     used by C(t) is their product).  The full lattice is scanned in chunks of

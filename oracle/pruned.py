@@ -235,7 +235,7 @@ def prune(A, psi, axes, theta, radius=RADIUS_1, rel_excl=0.0):
 
 def packet_factors(grids, weights, q0, p0, width, gfunc):
     """Per-mode coefficient vectors of a product packet, a^k_i =
-    sqrt(w_i) g_k(x_i) (DVR projection, Sec. 2.1), each normalised; the
+    sqrt(w_i) g_k(x_i) (DVR projection, Eq. pvN_def of Sec. 2.2), each normalised; the
     normalised full-lattice packet is their direct product."""
     out = []
     for k in range(len(grids)):

@@ -1,7 +1,7 @@
 // Host-side (FP64) construction of the 1D primitive bases and packet factors.
-// Sec. 2.1: a DVR basis chi_j has points x_j and weights w_j with coefficient
-// a_j = sqrt(w_j) psi(x_j); Sec. 2.2 (Eq. pvN_def) uses the same weights to
-// project functions onto the DVR.
+// Sec. 2.1: the wavefunction is expanded in direct products of DVR functions
+// chi_j (points x_j, weights w_j); Sec. 2.2 (Eq. pvN_def): a function f
+// projects onto chi_j with the coefficient sqrt(w_j) f(x_j).
 #include <math.h>
 #include <string.h>
 
