@@ -313,7 +313,7 @@ def test_prune_ball_rules_bruteforce(axes, seed, rule):
 
 def test_prune_relative_exclusion_bruteforce():
     # exclusion happens only when more than rel_excl * |A| members would
-    # leave; at exactly that many they stay (the paper's "larger than").
+    # leave; at exactly that many they stay (Sec. 2.5 excludes only above the fraction).
     axes = (6, 5)
     rng = np.random.default_rng(77)
     A = W.random_active_set(axes, 0.6, 77)
