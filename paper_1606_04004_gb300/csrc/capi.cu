@@ -761,8 +761,9 @@ PQ_API pq_status pq_state_load(pq_state* state, const int64_t* idx, int64_t n, c
     uint32_t* dk = nullptr;
     pq_status rc = dalloc(&dk, (size_t)n * 4);
     if (rc) return rc;
-    rc = cuda_status(cudaMemcpy(dk, k32.data(), (size_t)n * 4, cudaMemcpyHostToDevice),
-                     "uploading the index list");
+    if (n > 0)   // an empty list has no host data to copy
+        rc = cuda_status(cudaMemcpy(dk, k32.data(), (size_t)n * 4, cudaMemcpyHostToDevice),
+                         "uploading the index list");
     if (!rc) rc = load_set(*s, dk, n, 0);
     cudaDeviceSynchronize();
     dev_free(dk, 0, false);
