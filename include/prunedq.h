@@ -14,7 +14,9 @@
  *    the calling thread.
  *  - A lattice point is named by its row-major linear index (mode 0 slowest,
  *    mode D-1 contiguous).  A is kept sorted by that index.  The product of
- *    the mode sizes must be below 2^32 and every mode size at most 64.
+ *    the mode sizes must be below 2^32 and every mode size at most 256
+ *    (modes of up to 64 points take the tiled H.psi kernels, longer modes
+ *    the point-parallel ones).
  *  - Coefficient vectors are complex, interleaved (re, im): double pairs for
  *    PQ_FP64, float pairs for PQ_FP32MIX.  Vectors passed to the library as
  *    "device" pointers live in device memory of the current CUDA device and
@@ -321,9 +323,12 @@ pq_status pq_survival_grad(pq_state* state, const pq_prop_desc* desc, int nsteps
  * with the device current; make that first call before any stream capture.
  * The array is shared by all calls and keeps the last call's contents: calls
  * that overlap on the GPU (other streams, other host threads) race on it.
+ * DVR and projected-Weylet states only: a pvB state (Sec. 2.2) needs the
+ * bra factors B^dagger f and the norm a^dagger S_AA a, which take full-grid
+ * transforms, and is refused with PQ_ENOTSUP.
  * Errors: PQ_EINVAL for a null state or output, theta < 0, or more than
- * 268,435,456 active points (the scratch's limit); PQ_ECAPACITY if the
- * state's active set outgrew its capacity. */
+ * 268,435,456 active points (the scratch's limit); PQ_ENOTSUP for a pvB
+ * state; PQ_ECAPACITY if the state's active set outgrew its capacity. */
 pq_status pq_observe_noalloc(const pq_state* state, double theta, double* out, void* stream);
 
 /* Device memory through the caller's allocator (no counterpart in the paper):

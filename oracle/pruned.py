@@ -25,26 +25,26 @@ def digits(A, dims):
                     dtype=np.int64).reshape(len(dims), -1)
 
 
-DENSE_MAP_LIMIT = 1 << 26
+DENSE_MAP_LIMIT = 1 << 28
 
 
 class PositionMap:
     """Position of every lattice point in the sorted active set A (-1 when
     not active): the set semantics of the paper's hash set (Sec. 2.5) as a
-    dense table for lattices up to DENSE_MAP_LIMIT points, else a binary
-    search in A."""
+    dense table for lattices up to DENSE_MAP_LIMIT points (int32 entries, so
+    that a 24^6 lattice takes 0.8 GB), else a binary search in A."""
 
     def __init__(self, A, nfull):
         self.A = np.asarray(A, dtype=np.int64)
         self.dense = None
-        if nfull <= DENSE_MAP_LIMIT:
-            self.dense = np.full(int(nfull), -1, dtype=np.int64)
-            self.dense[self.A] = np.arange(len(self.A))
+        if nfull <= DENSE_MAP_LIMIT and len(self.A) < (1 << 31):
+            self.dense = np.full(int(nfull), -1, dtype=np.int32)
+            self.dense[self.A] = np.arange(len(self.A), dtype=np.int32)
 
     def __call__(self, keys):
         if self.dense is not None:
             ok = (keys >= 0) & (keys < len(self.dense))
-            p = np.where(ok, self.dense[np.where(ok, keys, 0)], -1)
+            p = np.where(ok, self.dense[np.where(ok, keys, 0)], -1).astype(np.int64)
             found = p >= 0
             return np.where(found, p, 0), found
         return lookup(self.A, keys)

@@ -231,26 +231,25 @@ class Basis:
 def _marshal_terms(dims, terms, keep):
     """SoP terms -> a ctypes pq_sop_term array (arrays kept alive in `keep`)."""
     D = len(dims)
-    if True:
-        carr = (SopTerm * max(1, len(terms)))()
-        for t, (coef, facs) in enumerate(terms):
-            if len(facs) != D:
-                raise ValueError("one factor per mode")
-            fa = (Factor * D)()
-            for k, f in enumerate(facs):
-                if f is None:
-                    fa[k] = Factor(FACTOR_IDENTITY, None)
-                elif isinstance(f, str) and f == "T":
-                    fa[k] = Factor(FACTOR_KINETIC, None)
-                else:
-                    v = np.ascontiguousarray(f, dtype=np.float64)
-                    if v.shape != (dims[k],):
-                        raise ValueError(f"factor of mode {k} needs {dims[k]} values")
-                    keep.append(v)
-                    fa[k] = Factor(FACTOR_DIAG, v.ctypes.data_as(C.POINTER(C.c_double)))
-            keep.append(fa)
-            carr[t] = SopTerm(float(coef), fa)
-        return carr
+    carr = (SopTerm * max(1, len(terms)))()
+    for t, (coef, facs) in enumerate(terms):
+        if len(facs) != D:
+            raise ValueError("one factor per mode")
+        fa = (Factor * D)()
+        for k, f in enumerate(facs):
+            if f is None:
+                fa[k] = Factor(FACTOR_IDENTITY, None)
+            elif isinstance(f, str) and f == "T":
+                fa[k] = Factor(FACTOR_KINETIC, None)
+            else:
+                v = np.ascontiguousarray(f, dtype=np.float64)
+                if v.shape != (dims[k],):
+                    raise ValueError(f"factor of mode {k} needs {dims[k]} values")
+                keep.append(v)
+                fa[k] = Factor(FACTOR_DIAG, v.ctypes.data_as(C.POINTER(C.c_double)))
+        keep.append(fa)
+        carr[t] = SopTerm(float(coef), fa)
+    return carr
 
 
 # ------------------------------------------------------------------ state

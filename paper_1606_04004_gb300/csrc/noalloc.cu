@@ -116,6 +116,12 @@ extern "C" __attribute__((visibility("default"))) pq_status pq_observe_noalloc(
         set_error("null state or output, or theta < 0");
         return PQ_EINVAL;
     }
+    if (s->pvb) {
+        // pvB needs the bra factors B^dagger f and the norm a^dagger S_AA a
+        // (Sec. 2.2), which take full-grid transforms and their buffers
+        set_error("pq_observe_noalloc does not provide pvB states; use pq_observables_get");
+        return PQ_ENOTSUP;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     double* scratch = nullptr;
     pq_status rc = noalloc_scratch(&scratch);

@@ -50,3 +50,19 @@ def test_observe_noalloc_empty_state():
     s.load(np.zeros(0, np.int64))
     got = s.observe_noalloc(1e-6)
     assert got["C"] == 0 and got["norm2"] == 0 and got["n_wasted"] == 0
+
+
+def test_observe_noalloc_refuses_pvb_states():
+    """A pvB state's C and norm take the bra factors B^dagger f and
+    a^dagger S_AA a (Sec. 2.2); the fixed-scratch reduction does not form them,
+    so the call refuses such a state instead of returning DVR-form sums."""
+    pq = lib()
+    cfg = W.scaled(W.MORSE3D, basis="pvb", D=2, n=16, nx_lattice=4, np_lattice=4,
+                   q0=W.morse3d_centres()[:2], p0=(0.0,) * 2, width=(0.2,) * 2)
+    b = pq.build_model(cfg)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP64)
+    with pytest.raises(pq.PQError) as e:
+        s.observe_noalloc(cfg["theta"])
+    assert e.value.status == pq.ENOTSUP
+    # the refusal leaves the state usable
+    assert s.observables()["norm2"][-1] > 0
