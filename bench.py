@@ -63,19 +63,59 @@ def code_digest(path):
     return hashlib.sha256(txt.encode()).hexdigest()
 
 
+APPLY_SOURCES = ("apply_h.cu",)
+
+
+def apply_digest(root=None):
+    """Code digest of the DVR H.psi kernel sources (APPLY_SOURCES), each
+    digested by code_digest, then the digests hashed together."""
+    root = ROOT if root is None else root
+    h = hashlib.sha256()
+    for name in APPLY_SOURCES:
+        p = os.path.join(root, "paper_1606_04004_gb300", "csrc", name)
+        h.update((code_digest(p) if os.path.exists(p) else "absent").encode())
+    return h.hexdigest()
+
+
 def _traffic_record():
     """DRAM bytes per active coefficient of the H.psi kernels from the committed
-    ncu summary, if it was taken on the current kernel source (same code
-    digest of apply_h.cu)."""
+    ncu summary, if it was taken on the current kernel sources (same digest)."""
     p = os.path.join(ROOT, "profiles", "apply_h_hh6d_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         rec = json.load(f)
-    src = os.path.join(ROOT, "paper_1606_04004_gb300", "csrc", "apply_h.cu")
-    if rec.get("apply_h_code_sha256") != code_digest(src):
+    if rec.get("apply_code_sha256") != apply_digest():
         return None
     return rec
+
+
+def fibre_flops_per_coef(A, dims):
+    """Algorithmic FP32 operations of one pruned DVR H.psi per active
+    coefficient: 4 per active member of each of the point's D fibres (a real
+    matrix element times a complex coefficient, Sec. 2.2.2) plus 4 for the
+    diagonal potential times the coefficient.  Host bookkeeping on the active
+    set (numpy), not part of the timed work."""
+    dims = tuple(int(d) for d in dims)
+    if len(A) == 0:
+        return 0.0
+    m = np.zeros(int(np.prod(dims)), dtype=bool)
+    m[np.asarray(A, dtype=np.int64)] = True
+    m = m.reshape(dims)
+    total = 0
+    for k in range(len(dims)):
+        cnt = m.sum(axis=k, keepdims=True, dtype=np.int64)
+        total += int((np.broadcast_to(cnt, m.shape) * m).sum(dtype=np.int64))
+    return 4.0 * total / len(A) + 4.0
+
+
+def fp32_peak_tflops():
+    """FP32 FMA rate of this GPU, measured now (scalar and packed two-lane
+    FMA chains, the larger of the two)."""
+    import paper_1606_04004_gb300 as pq
+    r1 = pq.measure_peak(pq.PEAK_FP32)
+    r2 = pq.measure_peak(pq.PEAK_FP32X2)
+    return max(r1["tflops"], r2["tflops"]), {"fp32_ffma": r1["tflops"], "fp32_ffma2": r2["tflops"]}
 
 
 class ClockSampler:
@@ -218,6 +258,8 @@ def run_ours(args, cfg):
     # warm-up steps (untimed)
     s.propagate(K, dt, th, args.warmup, stream=sptr)
     n_before = len(s.observables()["n_active"])
+    dims = (cfg["n"],) * cfg["D"]
+    fpc_first = fibre_flops_per_coef(s.read()[0], dims) if prec == pq.FP32MIX else None
     s.set_timing(True)
     launches0 = pq.launch_count()
     if dist:
@@ -250,6 +292,19 @@ def run_ours(args, cfg):
     traffic = None
     if trec and args.precision == "fp32mix" and cfg["name"] == trec.get("workload"):
         traffic = trec["dram_bytes_per_coef"] * tm["coef_applied"] / max(tm["n_apply"], 1)
+    alu = None
+    if fpc_first is not None and apply_s > 0:
+        # FP32 ALU roofline of the same launches: algorithmic flops per coefficient
+        # of the first and the last timed set, weighted by their sizes (the set
+        # grows over the window)
+        na_first, na_last = float(na[n_before - 1]), float(na[-1])
+        fpc_last = fibre_flops_per_coef(s.read()[0], dims)
+        fpc = (fpc_first * na_first + fpc_last * na_last) / (na_first + na_last)
+        alu_peak, alu_parts = fp32_peak_tflops()
+        alu_ach = tm["coef_applied"] * fpc / apply_s / 1e12
+        alu = {"achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
+               "flop_per_coef": fpc, "flop_per_coef_first_last": [fpc_first, fpc_last],
+               "peak_kind": "measured in this run (FP32 FMA chains)", **alu_parts}
 
     # e2e: the host-buffer C-ABI call on the final state
     A_n = s.size()
@@ -290,7 +345,8 @@ def run_ours(args, cfg):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "pruned H.psi (inner + outer fibre passes)",
                      "bytes_per_coef": bpc, "peak_kind": peak_kind,
-                     "apply_gcoef_s": tm["coef_applied"] / apply_s / 1e9 if apply_s else None},
+                     "apply_gcoef_s": tm["coef_applied"] / apply_s / 1e9 if apply_s else None,
+                     "alu": alu, "alu_frac": alu["frac"] if alu else None},
         "clocks": clk.summary(),
         "e2e": e2e,
     }
@@ -362,11 +418,94 @@ def run_apply(args, cfg):
     med = statistics.median(times) * 1e-3
     peak, kind = _peaks()
     bpc = BYTES_PER_COEF[args.precision]
+    fpc = fibre_flops_per_coef(A, (cfg["n"],) * cfg["D"])
+    alu_peak, alu_parts = fp32_peak_tflops()
+    alu = len(A) * fpc / med / 1e12
     print(json.dumps({"mode": "apply", "workload": cfg["name"], "precision": args.precision,
                       "n_active": int(len(A)), "radius": r, "median_us": med * 1e6,
                       "gcoef_s": len(A) / med / 1e9, "achieved_gbs": len(A) * bpc / med / 1e9,
                       "frac_hbm": len(A) * bpc / med / 1e9 / peak, "peak": peak,
-                      "peak_kind": kind, "reps": args.reps}), flush=True)
+                      "peak_kind": kind, "flop_per_coef": fpc, "alu_tflops": alu,
+                      "alu_peak_tflops": alu_peak, "alu_frac": alu / alu_peak, **alu_parts,
+                      "reps": args.reps}), flush=True)
+
+
+TF32_NOMINAL_OVER_BF16 = 1.1 / 2.25   # dense tensor rates of the part, TF32 over BF16
+
+
+def run_apply_phase_space(args, cfg):
+    """H.psi microbenchmark of the 3D coupled Morse workload in projected
+    Weylets (pW: nine pruned single-mode passes of dense 64 x 64 factors) or
+    in pvB (H_AA on the full 64^3 grid: B, the kinetic matrix and B^dagger
+    along every mode), on the workload's initial state, FP32-mix (tensor
+    cores, split TF32).  Reports Gcoef/s and the tensor-core work: the MMA
+    flops the passes issue (split TF32 = 3 products, fibres zero-padded to 64)
+    against the TF32 dense peak (the measured BF16 peak x the nominal
+    TF32 / BF16 ratio of the part), and the useful (unpadded, single-product)
+    flops."""
+    import torch
+    import paper_1606_04004_gb300 as pq
+    basis = "pvb" if args.config == "morse3d_pvb" else "pw"
+    c = W.scaled(W.MORSE3D, basis=basis, q0=W.morse3d_centres(W.MORSE3D["seed"]))
+    b = pq.build_model(c)
+    s = pq.State(b, c["q0"], c["p0"], c["width"], c["theta"], precision=pq.FP32MIX)
+    A, psi = s.read()
+    x = torch.from_numpy(psi).to("cuda")
+    y = torch.empty_like(x)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        s.apply_H(x, y)
+    launches0 = pq.launch_count()
+    times = []
+    for _ in range(args.reps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.apply_H(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = (pq.launch_count() - launches0) / args.reps
+    med = statistics.median(times) * 1e-3
+    D, n = c["D"], c["n"]
+    dims = (n,) * D
+    m = np.zeros(n ** D, bool)
+    m[A] = True
+    m = m.reshape(dims)
+    if basis == "pw":
+        # passes per mode: the merged single-mode factor + two pair terms
+        passes = {k: 1 + (D - 1) for k in range(D)}
+        tiles, useful = 0, 0.0
+        for k in range(D):
+            L = np.broadcast_to(m.sum(axis=k, keepdims=True), m.shape)[m]
+            useful += passes[k] * 4.0 * float(L.sum())
+            if k == D - 1:
+                t = -(-int(m.any(axis=D - 1).sum()) // 64)          # active rows, 64 per tile
+            else:
+                t = int(m.any(axis=(k, D - 1)).sum())               # fibre planes
+            tiles += passes[k] * t
+        mma = tiles * 3 * 2.0 * 128 * 64 * 64
+    else:
+        ntile = (n ** D // n) // 64
+        cplx = 3 * 2.0 * 128 * 128 * 64 * ntile          # a complex transform, all tiles
+        real = 3 * 2.0 * 128 * 64 * 64 * ntile
+        mma = 2 * D * cplx + D * real
+        useful = 2 * D * 8.0 * n * n ** D + D * 4.0 * n * n ** D
+    bf16 = None
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+    tf32_peak = (bf16 if bf16 else 1900.0) * TF32_NOMINAL_OVER_BF16
+    print(json.dumps({"mode": "apply", "workload": f"morse3d ({basis})", "precision": "fp32mix",
+                      "n_active": int(len(A)), "median_us": med * 1e6,
+                      "gcoef_s": len(A) / med / 1e9, "launches_per_apply": launches,
+                      "tensor_mma_tflops": mma / med / 1e12, "useful_tflops": useful / med / 1e12,
+                      "tf32_peak_tflops": tf32_peak,
+                      "tf32_peak_kind": "measured BF16 burst x nominal TF32/BF16 (1.1/2.25)"
+                                        if bf16 else "fallback BF16 1.9 PF x nominal ratio",
+                      "tensor_frac": mma / med / 1e12 / tf32_peak, "reps": args.reps}), flush=True)
 
 
 def run_snapshots(args, cfg):
@@ -409,6 +548,23 @@ def run_snapshots(args, cfg):
                           "gcoef_s": n / med / 1e9, "frac_hbm": n * bpc / med / 1e9 / peak,
                           "peak": peak, "peak_kind": kind, "reps": args.reps}), flush=True)
         del x, y
+
+
+def run_peaks(args):
+    """Measured arithmetic peaks of this GPU: FP32 scalar and packed two-lane
+    FMA chains and FP64 FMA chains (pq_measure_peak), with the SM clock sampled
+    while they run."""
+    import paper_1606_04004_gb300 as pq
+    import torch
+    torch.cuda.init()
+    out = {"mode": "peaks"}
+    with ClockSampler(0) as clk:
+        for name, kind, iters in (("fp32_ffma", pq.PEAK_FP32, 8192), ("fp32_ffma2", pq.PEAK_FP32X2, 8192),
+                                  ("fp64_dfma", pq.PEAK_FP64, 512)):
+            best = max(pq.measure_peak(kind, iters)["tflops"] for _ in range(5))
+            out[name + "_tflops"] = best
+    out["clocks"] = clk.summary()
+    print(json.dumps(out), flush=True)
 
 
 def run_dwell(args):
@@ -469,7 +625,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "apply", "dwell", "snapshot"])
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "dwell", "snapshot", "peaks"])
     ap.add_argument("--radius", type=float, default=11.2)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--snapshots", default="0,20,50,100")   # steps of --mode snapshot
@@ -477,9 +633,16 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("need at least 3 warm-up steps")
+    if args.config in ("morse3d", "morse3d_pvb"):
+        if args.mode != "apply":
+            raise SystemExit("--config morse3d / morse3d_pvb: only --mode apply")
+        run_apply_phase_space(args, None)
+        return
     cfg = W.CONFIGS[args.config]
     if args.mode == "apply":
         run_apply(args, cfg)
+    elif args.mode == "peaks":
+        run_peaks(args)
     elif args.mode == "dwell":
         run_dwell(args)
     elif args.mode == "snapshot":

@@ -285,6 +285,11 @@ pq_status pq_timing_get(pq_state* state, double* apply_ms, int64_t* n_apply,
  * psi_n recomputed from checkpoints taken every `ckpt_every` steps; the
  * time integral of <lambda| dH/dtheta |psi> over each step by 5-point
  * Gauss-Legendre with SIL propagators (negative times for the adjoint).
+ * Precision: the forward run (sets, checkpoints, C, P) in the state's
+ * precision; for a PQ_FP32MIX state the backward sweep (adjoint kets, the
+ * recomputed kets from the exactly widened checkpoints, the integrands) runs
+ * on an internal FP64 copy of the state, so the gradient is that of the FP32
+ * run's frozen sets without FP32 rounding in the time integrals.
  * Parameters:
  *   PQ_PARAM_POTENTIAL  dH/dtheta as diagonal SoP terms on the DVR grid
  *                       (PQ_FACTOR_DIAG / PQ_FACTOR_IDENTITY factors);
@@ -345,6 +350,19 @@ pq_status pq_observe_noalloc(const pq_state* state, double theta, double* out, v
 typedef void* (*pq_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*pq_free_fn)(void* ptr, void* stream, void* ctx);
 pq_status pq_set_allocator(pq_alloc_fn alloc, pq_free_fn free_fn, void* ctx);
+
+/* Arithmetic peak of the current device, measured (no counterpart in the
+ * paper; the H.psi kernels are compared with it, next to the HBM bandwidth).
+ * kind: PQ_PEAK_FP32 (scalar fused multiply-add), PQ_PEAK_FP32X2 (packed
+ * two-lane FP32 FMA, sm_100 and later), PQ_PEAK_FP64.  The device runs
+ * dependent FMA chains (8 per thread, `iters` FMAs each, 2048 threads per SM)
+ * once untimed and once timed with CUDA events on the legacy default stream;
+ * *ms_out receives the timed run's milliseconds and *flop_out its floating-
+ * point operations (2 per FMA and lane).  Synchronises the device; allocates
+ * a small device buffer.  Errors: PQ_EINVAL for an unknown kind, iters < 1 or
+ * a null output; PQ_ECUDA. */
+typedef enum pq_peak_kind { PQ_PEAK_FP32 = 0, PQ_PEAK_FP32X2 = 1, PQ_PEAK_FP64 = 2 } pq_peak_kind;
+pq_status pq_measure_peak(int kind, int iters, double* ms_out, double* flop_out);
 
 /* Number of kernels the library has launched since load (all states). */
 int64_t pq_launch_count(void);

@@ -107,6 +107,7 @@ _SIGS = {
     "pq_observe_noalloc": [_vp, C.c_double, _vp, _vp],
     "pq_survival_grad": [_vp, C.POINTER(PropDesc), C.c_int, C.c_int, C.POINTER(ParamDesc), C.c_int,
                          _vp, _vp, _vp],
+    "pq_measure_peak": [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "pq_launch_count": [],
     "pq_last_error": [],
 }
@@ -130,6 +131,17 @@ def _check(rc):
 
 def launch_count() -> int:
     return int(_lib.pq_launch_count())
+
+
+PEAK_FP32, PEAK_FP32X2, PEAK_FP64 = range(3)
+
+
+def measure_peak(kind: int, iters: int = 4096) -> dict:
+    """Measured arithmetic rate of the current device (pq_measure_peak):
+    milliseconds, floating-point operations and TFLOP/s of one timed run."""
+    ms, fl = C.c_double(), C.c_double()
+    _check(_lib.pq_measure_peak(int(kind), int(iters), C.byref(ms), C.byref(fl)))
+    return dict(ms=ms.value, flop=fl.value, tflops=fl.value / (ms.value * 1e-3) / 1e12)
 
 
 _allocator = []   # keeps the ctypes callbacks alive while the library holds them

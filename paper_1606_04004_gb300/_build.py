@@ -15,7 +15,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
               "--expt-relaxed-constexpr"]
-SOURCES = ["basis.cpp", "lattice.cu", "apply_h.cu", "krylov.cu", "capi.cu", "noalloc.cu", "adjoint.cu", "pvb.cu"]
+SOURCES = ["basis.cpp", "lattice.cu", "apply_h.cu", "krylov.cu", "capi.cu", "noalloc.cu", "adjoint.cu", "pvb.cu", "peaks.cu", "tc_fibre.cu"]
 
 
 def _nvcc() -> str:

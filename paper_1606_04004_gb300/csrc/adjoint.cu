@@ -138,6 +138,13 @@ __global__ void __launch_bounds__(kAdjThreads) k_packet_dots(
     }
 }
 
+// FP32 coefficients widened exactly to FP64.
+__global__ void k_widen(const float2* __restrict__ x, double2* __restrict__ y, int64_t n) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        y[p] = make_double2((double)x[p].x, (double)x[p].y);
+}
+
 namespace {
 
 struct DevBuf {
@@ -299,15 +306,16 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
         *n = std::min<int64_t>(s.h_cnt[CNT_NA], (int64_t)s.cap);
         return PQ_OK;
     };
-    auto packet_dots = [&](const void* x, std::vector<std::complex<double>>& out) -> pq_status {
+    auto packet_dots_on = [&](const State& S, const void* x,
+                              std::vector<std::complex<double>>& out) -> pq_status {
         const int nq = 1 + ncen;
-        if (s.prec == PQ_FP64)
+        if (S.prec == PQ_FP64)
             k_packet_dots<double><<<G, kAdjThreads, 0, st>>>(
-                s.keys, (const double2*)x, s.cnt + CNT_NA, (int64_t)s.cap, L, (const double2*)s.fac64,
+                S.keys, (const double2*)x, S.cnt + CNT_NA, (int64_t)S.cap, L, (const double2*)S.fac64,
                 (const double2*)d_dfac.p, (const int*)d_modes.p, nq, (double*)d_part.p);
         else
             k_packet_dots<float><<<G, kAdjThreads, 0, st>>>(
-                s.keys, (const float2*)x, s.cnt + CNT_NA, (int64_t)s.cap, L, (const double2*)s.fac64,
+                S.keys, (const float2*)x, S.cnt + CNT_NA, (int64_t)S.cap, L, (const double2*)S.fac64,
                 (const double2*)d_dfac.p, (const int*)d_modes.p, nq, (double*)d_part.p);
         PQ_CHECK_LAUNCH();
         std::vector<double> h;
@@ -348,62 +356,94 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
             return rc;
     }
     std::vector<std::complex<double>> pd;
-    if ((rc = packet_dots(s.psi, pd))) return rc;
+    if ((rc = packet_dots_on(s, s.psi, pd))) return rc;
     const std::complex<double> C = pd[0];
     std::vector<std::complex<double>> dC(np, 0.0);
     for (int c = 0; c < ncen; ++c) dC[cen_idx[c]] += pd[1 + c];   // <d a0 | psi_N>
 
-    // ---- backward sweep
+    // ---- backward sweep.  An FP32 forward run's sweep runs on an FP64 twin of
+    // the state (same basis, capacity and packet): the recorded sets are the
+    // FP32 run's, its checkpoints are widened exactly, and the adjoint kets,
+    // the recomputed kets and the Gauss-Legendre integrands are FP64.  The
+    // products of P's gradient over the integral have no FP32 cancellation
+    // floor, while P, C and the sets are those of the FP32 forward run.
+    struct Twin {
+        State* t = nullptr;
+        ~Twin() {
+            if (t) free_twin(t);
+        }
+    } twin;
+    const bool widen = s.prec != PQ_FP64;
+    if (widen && (rc = make_fp64_twin(s, &twin.t))) return rc;
+    State& B = widen ? *twin.t : s;
+    const size_t besz = B.esize;
+    if ((rc = ensure_krylov(B, d.K))) return rc;
+    auto bcopy = [&](void* dst, const void* src, int64_t n) -> pq_status {
+        if (n > 0) PQ_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)n * besz, cudaMemcpyDeviceToDevice, st));
+        return PQ_OK;
+    };
+    // checkpoint (forward precision) -> B's coefficients
+    auto restore = [&](void* dst, const void* ckp, int64_t n) -> pq_status {
+        if (n <= 0) return PQ_OK;
+        if (!widen) return bcopy(dst, ckp, n);
+        k_widen<<<G * 4, kAdjThreads, 0, st>>>((const float2*)ckp, (double2*)dst, n);
+        PQ_CHECK_LAUNCH();
+        return PQ_OK;
+    };
     DevBuf lam_b, mu_b, psig_b, seg_b;
     size_t vmax = 0;
     for (int64_t v : na) vmax = std::max<size_t>(vmax, (size_t)v);
-    if ((rc = dmalloc(lam_b, vmax * esz)) || (rc = dmalloc(mu_b, vmax * esz)) ||
-        (rc = dmalloc(psig_b, vmax * esz)) || (rc = dmalloc(seg_b, (size_t)ckpt * vmax * esz)))
+    if ((rc = dmalloc(lam_b, vmax * besz)) || (rc = dmalloc(mu_b, vmax * besz)) ||
+        (rc = dmalloc(psig_b, vmax * besz)) || (rc = dmalloc(seg_b, (size_t)ckpt * vmax * besz)))
         return rc;
     std::vector<double> gx, gw;
     gauss_legendre(5, gx, gw);
-    if ((rc = set_psi_from_packet(s, st))) return rc;   // lambda_N = a0 on A_N
+    // lambda_N = a0 on A_N
+    if ((widen && (rc = load_set(B, (const uint32_t*)sets[nsteps].p, na[nsteps], st))) ||
+        (rc = set_psi_from_packet(B, st)))
+        return rc;
     pq_prop_desc dd = d;
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int c = sg * ckpt, e = std::min(nsteps, c + ckpt);
-        if ((rc = copy(lam_b.p, s.psi, na[e]))) return rc;
+        if ((rc = bcopy(lam_b.p, B.psi, na[e]))) return rc;
         // recompute psi_c .. psi_{e-1} on their recorded sets
-        if ((rc = load_set(s, (const uint32_t*)sets[c].p, na[c], st)) || (rc = copy(s.psi, ck[sg].p, na[c])))
+        if ((rc = load_set(B, (const uint32_t*)sets[c].p, na[c], st)) ||
+            (rc = restore(B.psi, ck[sg].p, na[c])))
             return rc;
         for (int n = c; n < e; ++n) {
-            if ((rc = copy((char*)seg_b.p + (size_t)(n - c) * vmax * esz, s.psi, na[n]))) return rc;
+            if ((rc = bcopy((char*)seg_b.p + (size_t)(n - c) * vmax * besz, B.psi, na[n]))) return rc;
             if (n + 1 < e) {
                 dd.dt = d.dt;
-                if ((rc = sil_only(s, dd, st)) ||
-                    (rc = load_set(s, (const uint32_t*)sets[n + 1].p, na[n + 1], st, true)))
+                if ((rc = sil_only(B, dd, st)) ||
+                    (rc = load_set(B, (const uint32_t*)sets[n + 1].p, na[n + 1], st, true)))
                     return rc;
             }
         }
-        if ((rc = load_set(s, (const uint32_t*)sets[e].p, na[e], st)) || (rc = copy(s.psi, lam_b.p, na[e])))
+        if ((rc = load_set(B, (const uint32_t*)sets[e].p, na[e], st)) || (rc = bcopy(B.psi, lam_b.p, na[e])))
             return rc;
         for (int n = e - 1; n >= c; --n) {
             // mu = R_n^T lambda_{n+1} on A_n
-            if ((rc = load_set(s, (const uint32_t*)sets[n].p, na[n], st, true)) ||
-                (rc = copy(mu_b.p, s.psi, na[n])))
+            if ((rc = load_set(B, (const uint32_t*)sets[n].p, na[n], st, true)) ||
+                (rc = bcopy(mu_b.p, B.psi, na[n])))
                 return rc;
-            const void* psin = (char*)seg_b.p + (size_t)(n - c) * vmax * esz;
+            const void* psin = (char*)seg_b.p + (size_t)(n - c) * vmax * besz;
             for (size_t g = 0; g < gx.size() && npot > 0; ++g) {
                 const double sgn = d.dt * (1.0 + gx[g]) / 2.0, wg = gw[g] * d.dt / 2.0;
                 dd.dt = sgn;                                   // U(s) psi_n
-                if ((rc = copy(s.psi, psin, na[n])) || (rc = sil_only(s, dd, st)) ||
-                    (rc = copy(psig_b.p, s.psi, na[n])))
+                if ((rc = bcopy(B.psi, psin, na[n])) || (rc = sil_only(B, dd, st)) ||
+                    (rc = bcopy(psig_b.p, B.psi, na[n])))
                     return rc;
                 dd.dt = -(d.dt - sgn);                         // U(dt-s)^dagger mu
-                if ((rc = copy(s.psi, mu_b.p, na[n])) || (rc = sil_only(s, dd, st))) return rc;
-                if (s.prec == PQ_FP64)
+                if ((rc = bcopy(B.psi, mu_b.p, na[n])) || (rc = sil_only(B, dd, st))) return rc;
+                if (B.prec == PQ_FP64)
                     k_grad_dots<double><<<G, kAdjThreads, 0, st>>>(
-                        s.keys, (const double2*)s.psi, (const double2*)psig_b.p, s.cnt + CNT_NA,
-                        (int64_t)s.cap, L, (const double*)d_tab.p, (const double*)d_coef.p,
+                        B.keys, (const double2*)B.psi, (const double2*)psig_b.p, B.cnt + CNT_NA,
+                        (int64_t)B.cap, L, (const double*)d_tab.p, (const double*)d_coef.p,
                         (const int*)d_toff.p, npot, (double*)d_part.p);
                 else
                     k_grad_dots<float><<<G, kAdjThreads, 0, st>>>(
-                        s.keys, (const float2*)s.psi, (const float2*)psig_b.p, s.cnt + CNT_NA,
-                        (int64_t)s.cap, L, (const double*)d_tab.p, (const double*)d_coef.p,
+                        B.keys, (const float2*)B.psi, (const float2*)psig_b.p, B.cnt + CNT_NA,
+                        (int64_t)B.cap, L, (const double*)d_tab.p, (const double*)d_coef.p,
                         (const int*)d_toff.p, npot, (double*)d_part.p);
                 PQ_CHECK_LAUNCH();
                 std::vector<double> h;
@@ -412,12 +452,12 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
                     dC[pot_idx[q]] += std::complex<double>(0.0, -wg) * std::complex<double>(h[2 * q], h[2 * q + 1]);
             }
             dd.dt = -d.dt;                                     // lambda_n = U^dagger mu
-            if ((rc = copy(s.psi, mu_b.p, na[n])) || (rc = sil_only(s, dd, st))) return rc;
+            if ((rc = bcopy(B.psi, mu_b.p, na[n])) || (rc = sil_only(B, dd, st))) return rc;
         }
     }
     // <lambda_0 | d psi_0> for the packet centres (psi_0 = a0 on A_0)
     if (ncen > 0) {
-        if ((rc = packet_dots(s.psi, pd))) return rc;
+        if ((rc = packet_dots_on(B, B.psi, pd))) return rc;
         for (int c = 0; c < ncen; ++c) dC[cen_idx[c]] += std::conj(pd[1 + c]);
     }
     for (int q = 0; q < np; ++q) grad[q] = 2.0 * std::real(std::conj(C) * dC[q]);

@@ -1008,6 +1008,9 @@ static pq_status launch_pass(const State& s, ApplyArgs<R> a, int mode, int mat, 
         PQ_CHECK_LAUNCH();
         return PQ_OK;
     }
+    if (sizeof(R) == 4 && L.n[mode] <= kTcMaxN && L.nlast <= kTcMaxN)   // FP32: tensor cores
+        return tc_pass(s, (const float2*)in, (float2*)out, (const float*)a.mat, mode, coef, accumulate,
+                       in_scale, a.skip, a.skip_k, st);
     if (mode == L.D - 1) {
         const int nl = L.nlast;
         const size_t sm = (size_t)((nl * nl + 1) & ~1) * esz + (size_t)wpb * kMaxNTile * 2 * esz;
@@ -1531,20 +1534,27 @@ __device__ __forceinline__ int q_gather(const ApplyArgs<R>& a, QuadMeta& m, type
     return nitems;
 }
 
+// acc += t x for a real t and a complex x: one packed two-lane FMA in FP32
+// (the same fused operation on each of re and im), two FMAs in FP64.
+__device__ __forceinline__ void cfma(float2& acc, float t, float2 x) {
+    acc = __ffma2_rn(make_float2(t, t), x, acc);
+}
+__device__ __forceinline__ void cfma(double2& acc, double t, double2 x) {
+    acc.x = fma(t, x.x, acc.x);
+    acc.y = fma(t, x.y, acc.y);
+}
+
 // acc[t] += sum_v trow[rj[v]] x[v][W q + t] over the compact rows.
 template <typename R, int W>
 __device__ __forceinline__ void q_column(const R* trow, const int* rj, const typename Cx<R>::T* xcol,
-                                         int na, int nlw, R (&ax)[W], R (&ay)[W]) {
+                                         int na, int nlw, typename Cx<R>::T (&acc)[W]) {
     using V = typename Cx<R>::T;
     for (int v = 0; v < na; ++v) {
         const R tv = trow[rj[v]];
         V x[W];
         ld_w<R, W>(xcol + v * nlw, x);
 #pragma unroll
-        for (int t = 0; t < W; ++t) {
-            ax[t] += tv * x[t].x;
-            ay[t] += tv * x[t].y;
-        }
+        for (int t = 0; t < W; ++t) cfma(acc[t], tv, x[t]);
     }
 }
 
@@ -1607,15 +1617,15 @@ __global__ void __launch_bounds__(kApplyThreads) k_outer_q(ApplyArgs<R> a) {
             const int uu = it >> 3, q = it & 7;
             const uint32_t rb = m.rbt[uu];
             const uint32_t bq = (rb >> (W * q)) & ((1u << W) - 1u);
-            R ax[W], ay[W];
+            V acc[W];
 #pragma unroll
-            for (int t = 0; t < W; ++t) ax[t] = ay[t] = 0;
-            q_column<R, W>(Tk + m.rj[uu] * nkp, m.rj, tile + W * q, na, nlw, ax, ay);
+            for (int t = 0; t < W; ++t) acc[t] = cmake<R>(0, 0);
+            q_column<R, W>(Tk + m.rj[uu] * nkp, m.rj, tile + W * q, na, nlw, acc);
             uint32_t p = m.rst[uu] + (uint32_t)__popc(rb & ((1u << (W * q)) - 1u));
 #pragma unroll
             for (int t = 0; t < W; ++t) {
                 if ((bq >> t) & 1u) {
-                    if (pq_in_bounds(p, nact, 25, a.cnt)) q_accumulate(a.out + p, cmake<R>(ax[t], ay[t]));
+                    if (pq_in_bounds(p, nact, 25, a.cnt)) q_accumulate(a.out + p, acc[t]);
                     ++p;
                 }
             }
@@ -1719,10 +1729,10 @@ __global__ void __launch_bounds__(kApplyThreads) k_inner_q(ApplyArgs<R> a) {
             const uint32_t rb = m.rbt[uu];
             const uint32_t bq = (rb >> (W * q)) & ((1u << W) - 1u);
             const int ju = m.rj[uu];
-            R ax[W], ay[W];
+            V acc[W];
 #pragma unroll
-            for (int t = 0; t < W; ++t) ax[t] = ay[t] = 0;
-            q_column<R, W>(Tq + ju * n2p, m.rj, tile + W * q, na, nlw, ax, ay);   // mode D-2
+            for (int t = 0; t < W; ++t) acc[t] = cmake<R>(0, 0);
+            q_column<R, W>(Tq + ju * n2p, m.rj, tile + W * q, na, nlw, acc);   // mode D-2
             const V* xrow = tile + uu * nlw;
             {   // mode D-1 over the row's active span
                 const int slo = __ffs(rb) - 1, shi = 31 - __clz(rb);
@@ -1732,8 +1742,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_inner_q(ApplyArgs<R> a) {
                     ld_real_w<R, W>(Tlq + sp * nlw + W * q, tq);
 #pragma unroll
                     for (int t = 0; t < W; ++t) {
-                        ax[t] += tq[t] * x.x;
-                        ay[t] += tq[t] * x.y;
+                        cfma(acc[t], tq[t], x);
                     }
                 }
             }
@@ -1754,15 +1763,14 @@ __global__ void __launch_bounds__(kApplyThreads) k_inner_q(ApplyArgs<R> a) {
                 ld_w<R, W>(xrow + W * q, x);
 #pragma unroll
                 for (int t = 0; t < W; ++t) {
-                    ax[t] += vv[t] * x[t].x;
-                    ay[t] += vv[t] * x[t].y;
+                    cfma(acc[t], vv[t], x[t]);
                 }
             }
             uint32_t p = m.rst[uu] + (uint32_t)__popc(rb & ((1u << (W * q)) - 1u));
 #pragma unroll
             for (int t = 0; t < W; ++t) {
                 if ((bq >> t) & 1u) {
-                    if (pq_in_bounds(p, nact, 28, a.cnt)) a.out[p] = cmake<R>(ax[t], ay[t]);
+                    if (pq_in_bounds(p, nact, 28, a.cnt)) a.out[p] = acc[t];
                     ++p;
                 }
             }

@@ -386,6 +386,34 @@ static pq_status create_state(const pq_basis* basis_, int precision, size_t capa
     return PQ_OK;
 }
 
+// An FP64 state on the basis, capacity and packet of s, with an empty active
+// set: the adjoint sweep of a gradient whose forward run is FP32 (adjoint.cu).
+pq_status make_fp64_twin(const State& s, State** out) {
+    State* t = nullptr;
+    pq_status rc = create_state(reinterpret_cast<const pq_basis*>(s.basis), PQ_FP64, s.cap, &t);
+    if (rc) return rc;
+    const size_t nf = (size_t)t->lat.D * kMaxN * 2;
+    if ((rc = dalloc(&t->fac64, nf * 8)) || (rc = dalloc(&t->fac32, nf * 4)) ||
+        (rc = cuda_status(cudaMemcpy(t->fac64, s.fac64, nf * 8, cudaMemcpyDeviceToDevice),
+                          "copying the packet")) ||
+        (rc = cuda_status(cudaMemcpy(t->fac32, s.fac32, nf * 4, cudaMemcpyDeviceToDevice),
+                          "copying the packet"))) {
+        free_state(t);
+        return rc;
+    }
+    t->theta = s.theta;
+    t->radius = s.radius;
+    for (int k = 0; k < kMaxD; ++k) {
+        t->q0[k] = s.q0[k];
+        t->p0[k] = s.p0[k];
+        t->width[k] = s.width[k];
+    }
+    *out = t;
+    return PQ_OK;
+}
+
+void free_twin(State* t) { free_state(t); }
+
 static pq_status check_capacity(State& s, cudaStream_t st) {
     PQ_CUDA_TRY(cudaMemcpyAsync(s.h_cnt, s.cnt, CNT_SIZE * 8, cudaMemcpyDeviceToHost, st));
     PQ_CUDA_TRY(cudaStreamSynchronize(st));
@@ -827,7 +855,14 @@ PQ_API pq_status pq_apply_H(const pq_state* state, const void* in, void* out, in
         set_error("in and out must not overlap");
         return PQ_EINVAL;
     }
+#ifdef PQ_BOUNDS_CHECK
+    // self-checking build: report a recorded out-of-range access at once
+    pq_status rc = apply_H_launch(*s, in, out, precision, nullptr, nullptr, 0, (cudaStream_t)stream);
+    if (rc) return rc;
+    return check_capacity(const_cast<State&>(*s), (cudaStream_t)stream);
+#else
     return apply_H_launch(*s, in, out, precision, nullptr, nullptr, 0, (cudaStream_t)stream);
+#endif
 }
 
 PQ_API pq_status pq_apply_H_host(pq_state* state, const void* in, void* out, int precision,

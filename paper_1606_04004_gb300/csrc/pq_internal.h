@@ -251,6 +251,16 @@ pq_status load_set(State& s, const uint32_t* d_keys, int64_t n, cudaStream_t st,
                    bool remap = false);
 int grid_size();
 
+// tc_fibre.cu: dense 1D operators on the tensor cores (FP32 data, split TF32)
+// Full grid: Y (+)= M along mode k of X (M complex interleaved, or its real part).
+pq_status tc_grid_mode(const State& s, const float2* X, float2* Y, const float* M, int k,
+                       int accumulate, bool real_only, cudaStream_t st);
+// Pruned set: out (+)= coef P_A (M along mode k) in, M real.
+pq_status tc_pass(const State& s, const float2* in, float2* out, const float* M, int k, double coef,
+                  int accumulate, const double* in_scale, const int* skip, int skip_k,
+                  cudaStream_t st);
+constexpr int kTcMaxN = 64;   // matrix size and last-mode length the tensor-core passes take
+
 // apply_h.cu
 // in_scale (device, nullable): the input is multiplied by *in_scale on load.
 // skip (device, nullable): the launch does nothing when *skip <= skip_k.
@@ -271,6 +281,11 @@ pq_status energy_of_current(State& s, double* E, cudaStream_t st);
 pq_status pvb_apply(State& s, const void* in, void* out, int prec, cudaStream_t st);
 pq_status pvb_observe_current(State& s, double theta, cudaStream_t st);
 pq_status pvb_propagate(State& s, const pq_prop_desc& d, int nsteps, cudaStream_t st);
+
+// capi.cu: an FP64 state on the basis, capacity and packet of s (empty set),
+// and its release
+pq_status make_fp64_twin(const State& s, State** out);
+void free_twin(State* t);
 
 // adjoint.cu
 pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,

@@ -289,11 +289,14 @@ struct Pvb {
         n = std::min<int64_t>(s.h_cnt[CNT_NA], (int64_t)s.cap);
         return PQ_OK;
     }
-    // Y (+)= M_k along mode k of X, every mode of the full grid
-    pq_status mode(const V* in, V* out, const R* M, int k, int acc) {
+    // Y (+)= M_k along mode k of X, every mode of the full grid; `real`: M is
+    // real (its imaginary parts are zero: the kinetic matrix)
+    pq_status mode(const V* in, V* out, const R* M, int k, int acc, bool real = false) {
         const Lattice& L = s.lat;
         const int nk = L.n[k];
         const uint32_t inner = L.stride[k];
+        if (sizeof(R) == 4 && nk <= kTcMaxN)   // FP32: tensor cores, split TF32
+            return tc_grid_mode(s, (const float2*)in, (float2*)out, (const float*)M, k, acc, real, st);
         if (nk > kMaxNTile) {
             k_grid_mode_long<R><<<grid_size() * 8, kPvbThreads, 0, st>>>(in, out, M, nk, inner,
                                                                          L.nfull, acc);
@@ -344,7 +347,7 @@ struct Pvb {
         k_grid_potential<R><<<grid_size() * 8, kPvbThreads, 0, st>>>(cur, Z, s.lat, pot, potc, s.nterms);
         PQ_CHECK_LAUNCH();
         for (int k = 0; k < s.lat.D; ++k)
-            if ((rc = mode(cur, Z, mat(s.pvbT64, s.pvbT32, k), k, 1))) return rc;
+            if ((rc = mode(cur, Z, mat(s.pvbT64, s.pvbT32, k), k, 1, true))) return rc;
         V* c2 = Z;
         V* t2 = cur;
         if ((rc = all_modes(c2, t2, s.pvbBh64, s.pvbBh32))) return rc;     // (x B^dagger)

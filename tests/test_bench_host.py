@@ -66,7 +66,7 @@ def test_traffic_record_only_for_the_measured_source(tmp_path, monkeypatch):
     src.mkdir(parents=True)
     (tmp_path / "profiles").mkdir()
     (src / "apply_h.cu").write_text("// kernel v1\nint k;\n")
-    rec = {"apply_h_code_sha256": bench.code_digest(src / "apply_h.cu"),
+    rec = {"apply_code_sha256": bench.apply_digest(str(tmp_path)),
            "dram_bytes_per_coef": 100.0}
     (tmp_path / "profiles" / "apply_h_hh6d_traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
@@ -82,8 +82,8 @@ def test_traffic_record_only_for_the_measured_source(tmp_path, monkeypatch):
 def test_committed_traffic_record_matches_the_kernel_source():
     # the committed counters were taken on the H.psi kernels as they are now
     rec = bench._traffic_record()
-    assert rec is not None, ("apply_h.cu changed since the ncu traffic capture: re-take it, "
-                             "or the bench reports traffic as null")
+    assert rec is not None, ("the H.psi sources changed since the ncu traffic capture: "
+                             "re-take it, or the bench reports traffic as null")
     assert 20 < rec["dram_bytes_per_coef"] < 200
 
 

@@ -67,6 +67,14 @@ CASES = [
     ((9, 12, 20), 0.4),
     ((40, 6, 28, 11), 0.3),
     ((5, 30), 0.7),
+    # FP32 slab passes: a full 24^3 cube (more points than the staging buffer
+    # holds), ragged 6D (cube + pair + single pass), 5D (cube + pair), odd
+    # sizes in every tile mode
+    ((24, 24, 24), 1.0),
+    ((4, 5, 3, 6, 4, 5), 0.5),
+    ((3, 5, 7, 9, 11), 0.6),
+    ((2, 3, 24, 24, 24), 0.97),
+    ((7, 3, 32, 2, 13), 0.5),
 ]
 
 
@@ -82,6 +90,14 @@ def test_apply_ellipsoid_4d(prec):
     dims = (24, 24, 24, 24)
     A = W.ellipsoid_active_set(dims, (9, 8, 10, 7))
     _run(dims, A, 9, prec, nterms=6)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_ellipsoid_6d(prec):
+    # a 6D ball of 1.1e5 points on 10^6: ragged fibres in every mode
+    dims = (10,) * 6
+    A = W.ellipsoid_active_set(dims, (4.6, 4.1, 4.9, 4.3, 4.4, 4.8))
+    _run(dims, A, 11, prec, nterms=8)
 
 
 @pytest.mark.parametrize("prec", [0, 1])

@@ -28,7 +28,8 @@ def _state_with(b, A, psi, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("D,n,nx,np_,frac", [(2, 16, 4, 4, 0.5), (3, 16, 4, 4, 0.3),
-                                             (2, 64, 8, 8, 0.4), (1, 16, 4, 4, 0.8)])
+                                             (2, 64, 8, 8, 0.4), (1, 16, 4, 4, 0.8),
+                                             (3, 64, 8, 8, 0.15), (3, 24, 4, 6, 0.5)])
 def test_pw_apply_random_sets(D, n, nx, np_, frac, prec):
     import torch
     from oracle import propagate, pruned
