@@ -67,6 +67,26 @@ def potential_diag(A, dims, grids, vfunc):
     return vfunc(q)
 
 
+# Lattices up to this many points take the whole-lattice form of the pruned
+# products below (the coefficients embedded in the lattice with exact zeros
+# off A, each 1D operator applied along its mode by numpy's tensordot, the
+# result read back on A): the same sum as the member-by-member form, whose
+# absent members would only add exact zeros.  Larger lattices (24^6) use the
+# member-by-member form.
+WHOLE_LATTICE_LIMIT = 1 << 22
+
+
+def _embed(A, x, dims):
+    full = np.zeros(int(np.prod(dims)), dtype=np.complex128)
+    full[A] = x
+    return full.reshape(tuple(int(d) for d in dims))
+
+
+def _along(h, full, kappa):
+    """The matrix h applied along mode kappa of a whole-lattice array."""
+    return np.moveaxis(np.tensordot(np.asarray(h), full, axes=([1], [kappa])), 0, kappa)
+
+
 def apply_H(A, psi, dims, Ts, vdiag):
     """y = P_A H P_A a on the active set, for a DVR Hamiltonian
     H = sum_kappa T^(kappa) (x) 1 + V with diagonal V (Sec. 2.1, Sec. 2.2.2
@@ -81,6 +101,11 @@ def apply_H(A, psi, dims, Ts, vdiag):
     psi = np.asarray(psi, dtype=np.complex128)
     y = np.asarray(vdiag, dtype=np.float64) * psi
     if len(A) == 0:
+        return y
+    if int(np.prod(dims)) <= WHOLE_LATTICE_LIMIT:
+        full = _embed(A, psi, dims)
+        for k in range(len(dims)):
+            y += _along(np.asarray(Ts[k], dtype=np.float64), full, k).reshape(-1)[A]
         return y
     dg = digits(A, dims)
     st = strides_of(dims)
@@ -126,6 +151,8 @@ def mode_apply(A, x, dims, kappa, h):
     y = np.zeros(len(A), dtype=np.complex128)
     if len(A) == 0:
         return y
+    if int(np.prod(dims)) <= WHOLE_LATTICE_LIMIT:
+        return _along(h, _embed(A, x, dims), kappa).reshape(-1)[A]
     dg = digits(A, dims)
     st = strides_of(dims)
     where = PositionMap(A, int(np.prod(dims)))

@@ -57,7 +57,8 @@ static void free_state(State* s) {
     if (s->rowinfo) dev_free(s->rowinfo, 0, false);
     {
         void* pv[] = {s->pvbB64, s->pvbB32, s->pvbBh64, s->pvbBh32, s->pvbS64, s->pvbS32,
-                      s->pvbT64, s->pvbT32, s->pvb_grid, s->pvb_vec, s->fac_bra64};
+                      s->pvbSi64, s->pvbSi32, s->pvbT64, s->pvbT32, s->pvb_grid, s->pvb_vec,
+                      s->fac_bra64};
         for (void* p : pv)
             dev_free(p, 0, false);
     }
@@ -241,7 +242,7 @@ static pq_status upload_pvb(State& s) {
     const Basis& b = *s.basis;
     const int D = s.lat.D, lv = s.lead_virtual;
     const size_t msz = (size_t)D * kMaxN * kMaxN * 2;
-    std::vector<double> Bm(msz, 0.0), Bh(msz, 0.0), Sm(msz, 0.0), Tm(msz, 0.0);
+    std::vector<double> Bm(msz, 0.0), Bh(msz, 0.0), Sm(msz, 0.0), Tm(msz, 0.0), Si(msz, 0.0);
     double smax = 0.0;
     for (int k = 0; k < D; ++k) {
         const int ku = k - lv;
@@ -250,9 +251,20 @@ static pq_status upload_pvb(State& s) {
             for (int j = 0; j < n; ++j) {
                 const size_t o = (((size_t)k * kMaxN + i) * kMaxN + j) * 2;
                 if (ku < 0) {   // virtual size-1 mode: identity, no kinetic energy
-                    Bm[o] = Bh[o] = Sm[o] = 1.0;
+                    Bm[o] = Bh[o] = Sm[o] = Si[o] = 1.0;
                     continue;
                 }
+                // S^-1 = (B^dagger B)^-1 = G^dagger G, since B = G^-dagger
+                double sr = 0.0, si = 0.0;
+                for (int q = 0; q < n; ++q) {
+                    const size_t gi = ((size_t)q * n + i) * 2, gj = ((size_t)q * n + j) * 2;
+                    const double ar = b.Gc[ku][gi], ai = -b.Gc[ku][gi + 1];
+                    const double br = b.Gc[ku][gj], bi = b.Gc[ku][gj + 1];
+                    sr += ar * br - ai * bi;
+                    si += ar * bi + ai * br;
+                }
+                Si[o] = sr;
+                Si[o + 1] = si;
                 const size_t e = ((size_t)i * n + j) * 2, et = ((size_t)j * n + i) * 2;
                 Bm[o] = b.Bc[ku][e];
                 Bm[o + 1] = b.Bc[ku][e + 1];
@@ -274,10 +286,11 @@ static pq_status upload_pvb(State& s) {
     };
     pq_status rc;
     if ((rc = up(Bm, &s.pvbB64, &s.pvbB32)) || (rc = up(Bh, &s.pvbBh64, &s.pvbBh32)) ||
-        (rc = up(Sm, &s.pvbS64, &s.pvbS32)) || (rc = up(Tm, &s.pvbT64, &s.pvbT32)))
+        (rc = up(Sm, &s.pvbS64, &s.pvbS32)) || (rc = up(Tm, &s.pvbT64, &s.pvbT32)) ||
+        (rc = up(Si, &s.pvbSi64, &s.pvbSi32)))
         return rc;
     if ((rc = dalloc(&s.pvb_grid, (size_t)3 * s.lat.nfull * s.esize)) ||
-        (rc = dalloc(&s.pvb_vec, (size_t)5 * s.cap * s.esize)))
+        (rc = dalloc(&s.pvb_vec, (size_t)6 * s.cap * s.esize)))
         return rc;
     s.pvb_smax = smax > 0 ? smax : 1.0;
     s.pvb = true;

@@ -210,6 +210,8 @@ struct State {
     double* pvbB64 = nullptr; float* pvbB32 = nullptr;
     double* pvbBh64 = nullptr; float* pvbBh32 = nullptr;
     double* pvbS64 = nullptr; float* pvbS32 = nullptr;
+    double* pvbSi64 = nullptr; float* pvbSi32 = nullptr;   // S^-1 = G^dagger G (CG preconditioner)
+    int pvb_cg_pred = 16;          // conjugate-gradient iterations launched before the first poll
     double* pvbT64 = nullptr; float* pvbT32 = nullptr;
     void* pvb_grid = nullptr;
     void* pvb_vec = nullptr;
@@ -253,8 +255,10 @@ int grid_size();
 
 // tc_fibre.cu: dense 1D operators on the tensor cores (FP32 data, split TF32)
 // Full grid: Y (+)= M along mode k of X (M complex interleaved, or its real part).
+// `gate` (device, nullable): the launch does nothing while *gate != 0.
 pq_status tc_grid_mode(const State& s, const float2* X, float2* Y, const float* M, int k,
-                       int accumulate, bool real_only, cudaStream_t st);
+                       int accumulate, bool real_only, cudaStream_t st,
+                       const double* gate = nullptr);
 // Pruned set: out (+)= coef P_A (M along mode k) in, M real.
 pq_status tc_pass(const State& s, const float2* in, float2* out, const float* M, int k, double coef,
                   int accumulate, const double* in_scale, const int* skip, int skip_k,

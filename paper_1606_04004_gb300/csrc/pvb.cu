@@ -22,20 +22,24 @@ namespace pq {
 constexpr int kPvbThreads = 256;
 using cd = std::complex<double>;
 
-// X[key[p]] = a[p]
+// X[g] = a[rank(g)] for active lattice points g, 0 elsewhere: the whole grid
+// in one pass (the active set's bitmap and rank offsets give the position).
+// `gate` (nullable): nothing to do while *gate != 0 (a converged solve).
 template <typename R>
-__global__ void k_embed(const uint32_t* __restrict__ keys, const typename Cx<R>::T* __restrict__ a,
-                        const int64_t* na, int64_t cap, typename Cx<R>::T* __restrict__ X) {
-    const int64_t n = min(*na, cap);
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x)
-        X[keys[p]] = a[p];
+__global__ void k_embed_full(const uint64_t* __restrict__ bits, const uint32_t* __restrict__ off,
+                             const typename Cx<R>::T* __restrict__ a, uint32_t nfull,
+                             typename Cx<R>::T* __restrict__ X, const double* gate) {
+    if (gate && *gate != 0.0) return;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nfull; g += gridDim.x * blockDim.x)
+        X[g] = bit_test(bits, g) ? a[rank_of(bits, off, g)] : cmake<R>(0, 0);
 }
 
 // y[p] = Y[key[p]]
 template <typename R>
 __global__ void k_restrict(const uint32_t* __restrict__ keys, const typename Cx<R>::T* __restrict__ Y,
-                           const int64_t* na, int64_t cap, typename Cx<R>::T* __restrict__ y) {
+                           const int64_t* na, int64_t cap, typename Cx<R>::T* __restrict__ y,
+                           const double* gate) {
+    if (gate && *gate != 0.0) return;
     const int64_t n = min(*na, cap);
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x)
@@ -49,8 +53,10 @@ __global__ void k_restrict(const uint32_t* __restrict__ keys, const typename Cx<
 template <typename R>
 __global__ void __launch_bounds__(kPvbThreads) k_grid_mode(
     const typename Cx<R>::T* __restrict__ X, typename Cx<R>::T* __restrict__ Y,
-    const R* __restrict__ M, int nk, uint32_t inner, uint32_t total, int accumulate) {
+    const R* __restrict__ M, int nk, uint32_t inner, uint32_t total, int accumulate,
+    const double* gate) {
     using V = typename Cx<R>::T;
+    if (gate && *gate != 0.0) return;
     extern __shared__ __align__(16) unsigned char smem[];
     V* Ms = reinterpret_cast<V*>(smem);   // Ms[j * nk + i] = M[i][j]
     for (int e = threadIdx.x; e < nk * nk; e += blockDim.x) {
@@ -93,8 +99,10 @@ __global__ void __launch_bounds__(kPvbThreads) k_grid_mode(
 template <typename R>
 __global__ void __launch_bounds__(kPvbThreads) k_grid_mode_long(
     const typename Cx<R>::T* __restrict__ X, typename Cx<R>::T* __restrict__ Y,
-    const R* __restrict__ M, int nk, uint32_t inner, uint32_t total, int accumulate) {
+    const R* __restrict__ M, int nk, uint32_t inner, uint32_t total, int accumulate,
+    const double* gate) {
     using V = typename Cx<R>::T;
+    if (gate && *gate != 0.0) return;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const uint32_t in = t % inner, q = t / inner;
         const uint32_t i = q % (uint32_t)nk, o = q / (uint32_t)nk;
@@ -141,7 +149,9 @@ __global__ void k_grid_potential(const typename Cx<R>::T* __restrict__ X,
 template <typename R>
 __global__ void __launch_bounds__(kPvbThreads) k_cdot(const typename Cx<R>::T* __restrict__ x,
                                                        const typename Cx<R>::T* __restrict__ y,
-                                                       int64_t n, double* partials) {
+                                                       int64_t n, double* partials,
+                                                       const double* gate = nullptr) {
+    if (gate && *gate != 0.0) return;
     double re = 0.0, im = 0.0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -184,14 +194,20 @@ __global__ void k_lincomb(typename Cx<R>::T* out, double a1r, double a1i,
 }
 
 // Conjugate-gradient scalars on the device (slots of a small double array),
-// so that an iteration needs no host round trip.
-enum { kCgRR = 0, kCgY2, kCgAlpha, kCgBeta, kCgDone, kCgFail, kCgIt, kCgSlots };
+// so that an iteration needs no host round trip.  Preconditioned CG for
+// S_AA x = y with M = P_A (x_k S_k^-1) P_A^T:
+//   r = y, z = M r, p = z;  per iteration  alpha = <r,z> / <p,Sp>,
+//   x += alpha p, r -= alpha Sp, converged when <r,r> <= tol^2 <y,y>,
+//   z = M r, beta = <r,z>_new / <r,z>, p = z + beta p.
+enum { kCgRR = 0, kCgY2, kCgAlpha, kCgBeta, kCgDone, kCgFail, kCgIt, kCgRZ, kCgSlots };
 
-// Sum of the real parts of partials[G][2] (fixed order), then the CG update of
-// `mode`: 0 = start (rr = <y, y>), 1 = after <p, S p> (alpha), 2 = after the
-// new <r, r> (beta, convergence).
+// Sum of the real parts of partials[G][2] (fixed order), then the update of
+// `mode`: 0 = start (<y,y>: rr and the reference), 3 = start (<r,z>),
+// 1 = after <p,Sp> (alpha), 2 = after <r,r> (iteration count, convergence),
+// 4 = after the new <r,z> (beta).
 __global__ void k_cg_scalar(const double* partials, int G, double* cg, int mode, double tol2) {
     const int lane = threadIdx.x;
+    if (mode != 0 && mode != 3 && cg[kCgDone] != 0.0) return;
     double acc = 0.0;
     for (int b = lane; b < G; b += 32) acc += partials[2 * b];
     acc = warp_sum(acc);
@@ -204,20 +220,25 @@ __global__ void k_cg_scalar(const double* partials, int G, double* cg, int mode,
         cg[kCgIt] = 0.0;
         return;
     }
-    if (cg[kCgDone] != 0.0) return;
+    if (mode == 3) {
+        cg[kCgRZ] = acc;
+        return;
+    }
     if (mode == 1) {
-        const double al = cg[kCgRR] / acc;
+        const double al = cg[kCgRZ] / acc;
         if (!isfinite(al)) {
             cg[kCgFail] = 1.0;
             cg[kCgDone] = 1.0;
             return;
         }
         cg[kCgAlpha] = al;
-    } else {
-        cg[kCgBeta] = acc / cg[kCgRR];
+    } else if (mode == 2) {
         cg[kCgRR] = acc;
         cg[kCgIt] += 1.0;
         if (acc <= tol2 * cg[kCgY2]) cg[kCgDone] = 1.0;
+    } else {
+        cg[kCgBeta] = acc / cg[kCgRZ];
+        cg[kCgRZ] = acc;
     }
 }
 
@@ -268,6 +289,7 @@ struct Pvb {
     V* Z;
     double* part;
     int G;
+    const double* gate = nullptr;   // set during a solve: its kernels stop once it converged
 
     Pvb(State& s_, cudaStream_t st_) : s(s_), st(st_), n(0) {
         X = (V*)s.pvb_grid;
@@ -296,10 +318,11 @@ struct Pvb {
         const int nk = L.n[k];
         const uint32_t inner = L.stride[k];
         if (sizeof(R) == 4 && nk <= kTcMaxN)   // FP32: tensor cores, split TF32
-            return tc_grid_mode(s, (const float2*)in, (float2*)out, (const float*)M, k, acc, real, st);
+            return tc_grid_mode(s, (const float2*)in, (float2*)out, (const float*)M, k, acc, real, st,
+                                gate);
         if (nk > kMaxNTile) {
             k_grid_mode_long<R><<<grid_size() * 8, kPvbThreads, 0, st>>>(in, out, M, nk, inner,
-                                                                         L.nfull, acc);
+                                                                         L.nfull, acc, gate);
             PQ_CHECK_LAUNCH();
             return PQ_OK;
         }
@@ -310,7 +333,8 @@ struct Pvb {
                                              227 * 1024));
             attr = true;
         }
-        k_grid_mode<R><<<grid_size() * 8, kPvbThreads, sm, st>>>(in, out, M, nk, inner, L.nfull, acc);
+        k_grid_mode<R><<<grid_size() * 8, kPvbThreads, sm, st>>>(in, out, M, nk, inner, L.nfull, acc,
+                                                                 gate);
         PQ_CHECK_LAUNCH();
         return PQ_OK;
     }
@@ -324,15 +348,25 @@ struct Pvb {
         return PQ_OK;
     }
     pq_status embed(const void* a) {
-        PQ_CUDA_TRY(cudaMemsetAsync(X, 0, (size_t)s.lat.nfull * sizeof(V), st));
-        k_embed<R><<<G, kPvbThreads, 0, st>>>(s.keys, (const V*)a, s.cnt + CNT_NA, (int64_t)s.cap, X);
+        k_embed_full<R><<<grid_size() * 4, kPvbThreads, 0, st>>>(s.bits, s.off, (const V*)a,
+                                                                s.lat.nfull, X, gate);
         PQ_CHECK_LAUNCH();
         return PQ_OK;
     }
     pq_status restrict_to(const V* full, void* y) {
-        k_restrict<R><<<G, kPvbThreads, 0, st>>>(s.keys, full, s.cnt + CNT_NA, (int64_t)s.cap, (V*)y);
+        k_restrict<R><<<G, kPvbThreads, 0, st>>>(s.keys, full, s.cnt + CNT_NA, (int64_t)s.cap, (V*)y,
+                                                 gate);
         PQ_CHECK_LAUNCH();
         return PQ_OK;
+    }
+    // y = M v = P_A (x_k S_k^-1) P_A^T v, the preconditioner of the S_AA solve
+    pq_status Minv(const void* v, void* y) {
+        pq_status rc;
+        if ((rc = embed(v))) return rc;
+        V* cur = X;
+        V* tmp = Y;
+        if ((rc = all_modes(cur, tmp, s.pvbSi64, s.pvbSi32))) return rc;
+        return restrict_to(cur, y);
     }
     // y = H_AA a
     pq_status H(const void* a, void* y) {
@@ -383,22 +417,25 @@ struct Pvb {
         return PQ_OK;
     }
     void* vec(int i) { return (char*)s.pvb_vec + (size_t)i * s.cap * sizeof(V); }
-    // x = S_AA^{-1} y by conjugate gradients (x, y distinct).  The scalars
-    // live on the device; the host looks at the convergence flag once every
-    // kCgBatch iterations (iterations after convergence change nothing).
+    // x = S_AA^{-1} y by preconditioned conjugate gradients (x, y distinct),
+    // M = P_A (x_k S_k^-1) P_A^T.  The scalars live on the device and every
+    // kernel of an iteration does nothing once the solve has converged, so
+    // iterations are launched in batches: as many as the previous solve took
+    // (plus two), then the host reads the convergence flag once; only a solve
+    // that needs more continues in smaller batches, each followed by a read.
     pq_status solve(const void* y, void* x, double tol) {
         void* r = vec(0);
         void* p = vec(1);
         void* Sp = vec(2);
+        void* z = vec(5);
         double* cg = s.red_tmp + 8192;
-        constexpr int kCgBatch = 4;
         const int maxit = 2000;
         const double tol2 = tol * tol;
         pq_status rc;
         PQ_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(V), st));
-        if ((rc = lin(r, 1.0, y)) || (rc = lin(p, 1.0, y))) return rc;
         auto dot_into = [&](const void* a, const void* b, int mode) -> pq_status {
-            k_cdot<R><<<G, kPvbThreads, 0, st>>>((const V*)a, (const V*)b, n, part);
+            k_cdot<R><<<G, kPvbThreads, 0, st>>>((const V*)a, (const V*)b, n, part,
+                                                 mode == 0 || mode == 3 ? nullptr : cg + kCgDone);
             PQ_CHECK_LAUNCH();
             k_cg_scalar<<<1, 32, 0, st>>>(part, G, cg, mode, tol2);
             PQ_CHECK_LAUNCH();
@@ -410,24 +447,43 @@ struct Pvb {
             PQ_CHECK_LAUNCH();
             return PQ_OK;
         };
-        if ((rc = dot_into(r, r, 0))) return rc;
-        double flags[2];
-        for (int it = 0;; it += kCgBatch) {
+        // start: r = y, z = M r, p = z
+        if ((rc = lin(r, 1.0, y)) || (rc = dot_into(y, y, 0)) || (rc = Minv(r, z)) ||
+            (rc = lin(p, 1.0, z)) || (rc = dot_into(r, z, 3)))
+            return rc;
+        gate = cg + kCgDone;
+        auto iterate = [&]() -> pq_status {
+            pq_status e;
+            if ((e = S(p, Sp)) || (e = dot_into(p, Sp, 1)) || (e = axpy(x, x, p, kCgAlpha, 1.0)) ||
+                (e = axpy(r, r, Sp, kCgAlpha, -1.0)) || (e = dot_into(r, r, 2)) || (e = Minv(r, z)) ||
+                (e = dot_into(r, z, 4)) || (e = axpy(p, z, p, kCgBeta, 1.0)))
+                return e;
+            return PQ_OK;
+        };
+        int launched = 0, batch = std::max(2, s.pvb_cg_pred);
+        double flags[3];
+        while (true) {
+            for (int b = 0; b < batch && launched < maxit; ++b, ++launched)
+                if ((rc = iterate())) {
+                    gate = nullptr;
+                    return rc;
+                }
             PQ_CUDA_TRY(cudaMemcpyAsync(flags, cg + kCgDone, sizeof(flags), cudaMemcpyDeviceToHost, st));
             PQ_CUDA_TRY(cudaStreamSynchronize(st));
             if (flags[1] != 0.0) {
+                gate = nullptr;
                 set_error("pvB: conjugate gradients broke down");
                 return PQ_ENUMERIC;
             }
-            if (flags[0] != 0.0) return PQ_OK;
-            if (it >= maxit) break;
-            for (int b = 0; b < kCgBatch; ++b) {
-                if ((rc = S(p, Sp)) || (rc = dot_into(p, Sp, 1)) ||
-                    (rc = axpy(x, x, p, kCgAlpha, 1.0)) || (rc = axpy(r, r, Sp, kCgAlpha, -1.0)) ||
-                    (rc = dot_into(r, r, 2)) || (rc = axpy(p, r, p, kCgBeta, 1.0)))
-                    return rc;
+            if (flags[0] != 0.0) {
+                gate = nullptr;
+                s.pvb_cg_pred = (int)flags[2] + 2;
+                return PQ_OK;
             }
+            if (launched >= maxit) break;
+            batch = std::max(4, batch / 4);
         }
+        gate = nullptr;
         set_error("pvB: conjugate gradients did not converge in %d iterations", maxit);
         return PQ_ENUMERIC;
     }

@@ -58,6 +58,7 @@ struct TcArgs {
     const int64_t* nunits;
     int mode;
     int64_t* cnt;            // state counters (error bit 4: a tensor-core wait gave up)
+    const double* gate;      // nullable: nothing to do while *gate != 0
 };
 
 __device__ __forceinline__ uint32_t tc_smem(const void* p) {
@@ -158,6 +159,7 @@ struct TcSmem {
 template <int NMAT, int GM>
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mode(const TcArgs a) {
     if (a.skip && *a.skip <= a.skip_k) return;
+    if (a.gate && *a.gate != 0.0) return;
     if (a.cnt && (a.cnt[CNT_ERR] & 1)) return;
     using S = TcSmem<NMAT>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -399,8 +401,9 @@ static pq_status tc_launch(const TcArgs& a, int64_t grid_hint, cudaStream_t st) 
 // Full grid (pvB): Y (+)= M along mode k of X, FP32.  M complex interleaved
 // (row stride kMaxN); `real_only` applies its real part (the kinetic matrix).
 pq_status tc_grid_mode(const State& s, const float2* X, float2* Y, const float* M, int k,
-                       int accumulate, bool real_only, cudaStream_t st) {
+                       int accumulate, bool real_only, cudaStream_t st, const double* gate) {
     TcArgs a{};
+    a.gate = gate;
     a.in = X;
     a.out = Y;
     a.M = M;

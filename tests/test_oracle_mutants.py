@@ -155,22 +155,35 @@ MUTANTS = [
      [lambda: P.test_prune_bruteforce((4, 3, 5), 1)]),
     ("strides_wrong_extent", "oracle.pruned", "strides_of",
      "s[k] = s[k + 1] * int(dims[k + 1])", "s[k] = s[k + 1] * int(dims[k])",
-     [lambda: P.test_pruned_apply_equals_PHP((4, 5, 3), 0.4, 2)]),
+     [lambda: P.test_pruned_apply_member_form_equals_PHP((4, 5, 3), 0.4, 2)]),
     ("apply_T_transposed", "oracle.pruned", "apply_H",
      "T[ik[found], j]", "T[j, ik[found]]",
-     [lambda: P.test_pruned_apply_equals_PHP((6, 5), 0.5, 1)]),
+     [lambda: P.test_pruned_apply_member_form_equals_PHP((6, 5), 0.5, 1)]),
     ("apply_mode_dropped", "oracle.pruned", "apply_H",
      "for kappa, n in enumerate(dims):", "for kappa, n in list(enumerate(dims))[1:]:",
-     [lambda: P.test_pruned_apply_equals_PHP((6, 5), 0.5, 1)]),
+     [lambda: P.test_pruned_apply_member_form_equals_PHP((6, 5), 0.5, 1)]),
     ("apply_potential_dropped", "oracle.pruned", "apply_H",
      "y = np.asarray(vdiag, dtype=np.float64) * psi", "y = 0.0 * psi",
      [lambda: P.test_pruned_apply_equals_PHP((6, 5), 0.5, 1)]),
+    ("apply_whole_mode_dropped", "oracle.pruned", "apply_H",
+     "for k in range(len(dims)):", "for k in range(1, len(dims)):",
+     [lambda: P.test_pruned_apply_equals_PHP((6, 5), 0.5, 1)]),
+    ("along_transposed", "oracle.pruned", "_along",
+     "axes=([1], [kappa])", "axes=([0], [kappa])",
+     [lambda: P.test_pruned_apply_equals_PHP((6, 5), 0.5, 1)]),
+    ("embed_off_set", "oracle.pruned", "_embed",
+     "full[A] = x", "full[np.sort((A + 1) % full.size)] = x",
+     [lambda: P.test_pruned_apply_equals_PHP((6, 5), 0.5, 1)]),
+    ("mode_apply_whole_transposed", "oracle.pruned", "mode_apply",
+     "return _along(h, _embed(A, x, dims), kappa)",
+     "return _along(np.asarray(h).T, _embed(A, x, dims), kappa)",
+     [lambda: P.test_sop_sequential_equals_dense_truncated_products((6, 7), 2)]),
     ("apply_at_T_transposed", "oracle.pruned", "apply_H_at",
      "T[ik[found], j]", "T[j, ik[found]]",
      [P.test_pruned_apply_at_sample_equals_full]),
     ("mode_apply_transposed", "oracle.pruned", "mode_apply",
      "h[ik[found], j]", "h[j, ik[found]]",
-     [lambda: P.test_sop_sequential_equals_dense_truncated_products((6, 7), 2)]),
+     [lambda: P.test_sop_sequential_member_form((6, 7), 2)]),
     ("sop_mode_order", "oracle.pruned", "apply_H_sop",
      "sorted(facs, reverse=True)", "sorted(facs)",
      [lambda: P.test_sop_sequential_equals_dense_truncated_products((5, 4, 6), 1)]),

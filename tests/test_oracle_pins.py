@@ -167,6 +167,42 @@ def test_pruned_apply_equals_PHP(dims, frac, seed):
     np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-12)
 
 
+class member_form:
+    """Run the oracle's pruned products in their member-by-member form (the
+    one large lattices take) instead of the whole-lattice form."""
+
+    def __enter__(self):
+        self.old = pruned.WHOLE_LATTICE_LIMIT
+        pruned.WHOLE_LATTICE_LIMIT = 0
+
+    def __exit__(self, *a):
+        pruned.WHOLE_LATTICE_LIMIT = self.old
+
+
+@pytest.mark.parametrize("dims,frac,seed", [((6, 5), 0.5, 1), ((4, 5, 3), 0.4, 2),
+                                            ((3, 4, 2, 3), 0.3, 3), ((7,), 0.6, 4),
+                                            ((4, 5, 3), 1.0, 5)])
+def test_pruned_apply_member_form_equals_PHP(dims, frac, seed):
+    # the same pin on the member-by-member form of the pruned product
+    with member_form():
+        test_pruned_apply_equals_PHP(dims, frac, seed)
+
+
+def test_pruned_apply_forms_agree():
+    # the whole-lattice and the member-by-member forms add the same terms (an
+    # absent member contributes an exact zero): equal to rounding
+    dims = (5, 6, 4)
+    rng = np.random.default_rng(21)
+    Ts = [rng.standard_normal((d, d)) for d in dims]
+    A = W.random_active_set(dims, 0.35, 21)
+    psi = W.random_psi(len(A), 22)
+    v = rng.standard_normal(len(A))
+    y1 = pruned.apply_H(A, psi, dims, Ts, v)
+    with member_form():
+        y2 = pruned.apply_H(A, psi, dims, Ts, v)
+    np.testing.assert_allclose(y1, y2, rtol=1e-13, atol=1e-13)
+
+
 def test_pruned_apply_at_sample_equals_full():
     dims = (5, 4, 6)
     rng = np.random.default_rng(11)
@@ -661,6 +697,13 @@ def test_pvb_biorthogonal():
     Sb = B.conj().T @ B
     ev = np.sort(np.linalg.eigvals(np.linalg.solve(Sb, Hb)).real)
     np.testing.assert_allclose(ev, np.linalg.eigvalsh(H), rtol=1e-8, atol=1e-12)
+
+
+@pytest.mark.parametrize("dims,seed", [((5, 4, 6), 1), ((6, 7), 2), ((3, 4, 2, 3), 3)])
+def test_sop_sequential_member_form(dims, seed):
+    # the same pin on the member-by-member form of each factor's pass
+    with member_form():
+        test_sop_sequential_equals_dense_truncated_products(dims, seed)
 
 
 @pytest.mark.parametrize("dims,seed", [((5, 4, 6), 1), ((6, 7), 2), ((3, 4, 2, 3), 3)])
