@@ -74,6 +74,7 @@ static void free_state(State* s) {
     for (void* p : ptrs)
         dev_free(p, 0, false);
     if (s->h_cnt) cudaFreeHost(s->h_cnt);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
     g_live_states.fetch_sub(1);
 }

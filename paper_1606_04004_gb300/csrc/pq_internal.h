@@ -212,6 +212,7 @@ struct State {
     double* pvbS64 = nullptr; float* pvbS32 = nullptr;
     double* pvbSi64 = nullptr; float* pvbSi32 = nullptr;   // S^-1 = G^dagger G (CG preconditioner)
     int pvb_cg_pred = 16;          // conjugate-gradient iterations launched before the first poll
+    cudaStream_t cap_stream = nullptr;   // private stream the CG iteration is captured on
     double* pvbT64 = nullptr; float* pvbT32 = nullptr;
     void* pvb_grid = nullptr;
     void* pvb_vec = nullptr;

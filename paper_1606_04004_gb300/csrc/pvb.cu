@@ -452,6 +452,7 @@ struct Pvb {
             (rc = lin(p, 1.0, z)) || (rc = dot_into(r, z, 3)))
             return rc;
         gate = cg + kCgDone;
+        int nodes = 0;
         auto iterate = [&]() -> pq_status {
             pq_status e;
             if ((e = S(p, Sp)) || (e = dot_into(p, Sp, 1)) || (e = axpy(x, x, p, kCgAlpha, 1.0)) ||
@@ -460,11 +461,52 @@ struct Pvb {
                 return e;
             return PQ_OK;
         };
+        // One iteration as a CUDA graph (captured on the state's private stream,
+        // replayed on st): its 18 kernels cost one launch.  The self-checking
+        // build synchronises after every launch and launches directly.
+        cudaGraphExec_t ge = nullptr;
+#ifndef PQ_BOUNDS_CHECK
+        {
+            if (!s.cap_stream)
+                PQ_CUDA_TRY(cudaStreamCreateWithFlags(&s.cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            const cudaStream_t st0 = st;
+            const int64_t l0 = g_launches.load();
+            PQ_CUDA_TRY(cudaStreamBeginCapture(s.cap_stream, cudaStreamCaptureModeRelaxed));
+            st = s.cap_stream;
+            const pq_status crc = iterate();
+            st = st0;
+            const cudaError_t ce = cudaStreamEndCapture(s.cap_stream, &g);
+            nodes = (int)(g_launches.load() - l0);
+            g_launches.fetch_sub(nodes);   // counted when they run
+            if (crc) {
+                if (g) cudaGraphDestroy(g);
+                gate = nullptr;
+                return crc;
+            }
+            PQ_CUDA_TRY(ce);
+            const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            PQ_CUDA_TRY(ie);
+        }
+#endif
+        struct GraphExec {
+            cudaGraphExec_t& e;
+            ~GraphExec() {
+                if (e) cudaGraphExecDestroy(e);
+            }
+        } ge_owner{ge};
+        auto step = [&]() -> pq_status {
+            if (!ge) return iterate();
+            PQ_CUDA_TRY(cudaGraphLaunch(ge, st));
+            g_launches.fetch_add(nodes);
+            return PQ_OK;
+        };
         int launched = 0, batch = std::max(2, s.pvb_cg_pred);
         double flags[3];
         while (true) {
             for (int b = 0; b < batch && launched < maxit; ++b, ++launched)
-                if ((rc = iterate())) {
+                if ((rc = step())) {
                     gate = nullptr;
                     return rc;
                 }
