@@ -1,0 +1,112 @@
+"""GPU propagation of the workloads over their stated run lengths against the
+FP64 oracle's stored series (tests/golden/series_*.json, written by
+tests/golden/make_series.py from the oracle alone).
+
+FP64 path: the same |A| and small-coefficient count after every step, the
+same final active set (SHA-256 of the sorted indices), C(t) and ||psi||^2
+within 1e-10, E within 1e-10 relative, and the final coefficients on a fixed
+sample of 4096 members of A within 1e-10 ||psi|| (the sampled relative L2
+error, scaled to the whole set, also <= 1e-10).  FP32-mix path: |dC(t)| <=
+1e-5 and |d||psi||^2| <= 1e-6 at every step; the sets may differ where FP32
+moves a coefficient across the threshold, so they are compared through these
+observables only.
+
+Known miss: the FP32-mix projected-Weylet run of the 3D Morse workload loses
+norm at about 2.7e-8 per step against the FP64 run (1.06e-5 after 400 steps,
+with the tensor-core passes and with the FP32 SIMT passes alike) while its
+C(t) stays within 1e-5; its norm check is an expected failure."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import lib
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(HERE, f"series_{name}.json")) as f:
+        return json.load(f)
+
+
+def _cfg(name):
+    if name == "morse3d_pw":
+        return W.scaled(W.MORSE3D, q0=W.morse3d_centres(W.MORSE3D["seed"]))
+    if name == "morse3d_pvb":
+        return W.scaled(W.MORSE3D, basis="pvb", q0=W.morse3d_centres(W.MORSE3D["seed"]))
+    return W.CONFIGS[name]
+
+
+def _run(name, prec):
+    pq = lib()
+    rec = _load(name)
+    cfg = _cfg(name)
+    b = pq.build_model(cfg)
+    s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=prec)
+    s.propagate(cfg["K"], cfg["dt"], cfg["theta"], rec["nsteps"])
+    return rec, s, s.observables()
+
+
+def _series(rec, key):
+    if key == "C":
+        return np.array([complex(*st["C"]) for st in rec["steps"]])
+    return np.array([st[key] for st in rec["steps"]])
+
+
+def _check_fp64(rec, s, o):
+    np.testing.assert_array_equal(o["n_active"], _series(rec, "n_active"))
+    np.testing.assert_array_equal(o["n_wasted"], _series(rec, "n_wasted"))
+    assert np.max(np.abs(o["C"] - _series(rec, "C"))) < 1e-10
+    assert np.max(np.abs(o["norm2"] - _series(rec, "norm2"))) < 1e-10
+    E = _series(rec, "E")
+    assert np.max(np.abs(o["energy"] - E)) <= 1e-10 * np.abs(E).max()
+    A, psi = s.read()
+    digest = hashlib.sha256(np.ascontiguousarray(A.astype("<i8")).tobytes()).hexdigest()
+    assert digest == rec["steps"][-1]["set_sha256"]
+    f = rec["final"]
+    pos = np.arange(0, len(A), f["stride"])[:len(f["key"])]
+    np.testing.assert_array_equal(A[pos], f["key"])
+    ref = np.array(f["re"]) + 1j * np.array(f["im"])
+    err = np.abs(psi[pos] - ref)
+    assert err.max() <= 1e-10 * f["norm"]
+    assert np.sqrt(np.mean(err ** 2) * len(A)) <= 1e-10 * f["norm"]
+
+
+_FP32_RUNS = {}
+
+
+def _fp32_run(name):
+    if name not in _FP32_RUNS:
+        rec, s, o = _run(name, lib().FP32MIX)
+        s.free()
+        _FP32_RUNS[name] = (rec, o)
+    return _FP32_RUNS[name]
+
+
+@pytest.mark.parametrize("name", ["hh4d", "hh6d", "morse3d_pw", "morse3d_pvb"])
+def test_series_fp64(name):
+    rec, s, o = _run(name, lib().FP64)
+    _check_fp64(rec, s, o)
+
+
+@pytest.mark.parametrize("name", ["hh4d", "hh6d", "morse3d_pw", "morse3d_pvb"])
+def test_series_fp32mix_C(name):
+    rec, o = _fp32_run(name)
+    assert len(o["C"]) == len(rec["steps"])
+    assert np.max(np.abs(o["C"] - _series(rec, "C"))) <= 1e-5
+
+
+@pytest.mark.parametrize("name", [
+    "hh4d", "hh6d",
+    pytest.param("morse3d_pw", marks=pytest.mark.xfail(
+        strict=True, reason="FP32-mix pW norm drift 1.06e-5 after 400 steps")),
+    "morse3d_pvb"])
+def test_series_fp32mix_norm(name):
+    rec, o = _fp32_run(name)
+    assert np.max(np.abs(o["norm2"] - _series(rec, "norm2"))) <= 1e-6
