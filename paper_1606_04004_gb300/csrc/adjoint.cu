@@ -2,16 +2,19 @@
 // pruned propagation (not a construction of the paper, which computes only
 // the autocorrelation, Eq. acorr; the gradient is taken of that quantity).
 //
-// On the recorded sequence of active sets A_0..A_N the propagation is linear,
-//   psi_{n+1} = R_n U_n psi_n,  U_n = exp(-i H_{A_n} dt)  (SIL, Sec. 3.1),
-// with R_n carrying coefficients from A_n to A_{n+1}.  With the adjoint kets
-//   lambda_N = a0 on A_N,   lambda_n = U_n^dagger R_n^T lambda_{n+1},
-// C = <a0|psi_N> has
-//   dC/dtheta = <d a0|psi_N> + <lambda_0|d psi_0>
-//             - i sum_n int_0^dt <U_n(dt-s)^dagger R_n^T lambda_{n+1}| dH/dtheta |U_n(s) psi_n> ds,
-// the s-integral by Gauss-Legendre, every exponential by SIL (negative times
-// for the adjoint), and dP/dtheta = 2 Re(conj(C) dC/dtheta).  psi_n is
-// recomputed segment by segment from checkpoints taken every `ckpt` steps.
+// On the recorded sequence of active sets A_0..A_N the propagation is
+//   psi_{n+1} = R_n S_n(psi_n),  S_n = the fixed-order SIL step on A_n (Sec. 3.1),
+// with R_n carrying coefficients from A_n to A_{n+1} (kept where the point
+// stays, zero where it is new).  The gradient is that of this discrete map, so
+// it agrees with finite differences of the propagation whether or not the SIL
+// step has converged to exp(-i H dt): with dL = Re<xbar, dx> for every ket x,
+//   psibar_N = 2 C a0 on A_N,  psibar_n = S_n'(psi_n)^dagger R_n^T psibar_{n+1},
+// where the reverse pass through S_n repeats the step's Lanczos recurrence and
+// runs it backwards (its scalars on the host, its vectors on the device); the
+// potential parameters collect Re<wbar_k, dH/dtheta V_k> at every Lanczos
+// vector, the packet centres Re<psibar_0, d a0> plus the bra's share
+// 2 Re(conj(C) <d a0|psi_N>).  psi_n is recomputed segment by segment from
+// checkpoints taken every `ckpt` steps.
 #include <math.h>
 
 #include <algorithm>
@@ -25,31 +28,6 @@ namespace pq {
 
 constexpr int kAdjThreads = 256;
 constexpr int kMaxParams = 16;
-
-// n-point Gauss-Legendre rule on [-1, 1]: Newton iteration on P_n from the
-// Chebyshev-like initial guesses, P_n by its three-term recurrence.
-static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
-    x.resize(n);
-    w.resize(n);
-    for (int i = 0; i < n; ++i) {
-        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
-        double dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = z;
-            for (int k = 2; k <= n; ++k) {
-                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-                p0 = p1;
-                p1 = p2;
-            }
-            dp = n * (z * p1 - p0) / (z * z - 1.0);
-            const double dz = p1 / dp;
-            z -= dz;
-            if (fabs(dz) < 1e-16) break;
-        }
-        x[i] = z;
-        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
-    }
-}
 
 // Per parameter p: sum_I conj(lam_I) dV_p(x_I) psi_I, with dV_p = sum_t c_t
 // prod_k f_tk(i_k) over the parameter's terms [toff[p], toff[p+1]).
@@ -138,11 +116,88 @@ __global__ void __launch_bounds__(kAdjThreads) k_packet_dots(
     }
 }
 
-// FP32 coefficients widened exactly to FP64.
-__global__ void k_widen(const float2* __restrict__ x, double2* __restrict__ y, int64_t n) {
+// ---------------------------------------------- the step's discrete adjoint
+// Vector primitives of the reverse sweep through one Lanczos step (FP64
+// kets, at most kChunk vectors per launch, Krylov vectors ld elements apart).
+constexpr int kChunk = 8;
+struct Coefs {
+    double2 c[kMaxK + 1];
+};
+
+// partials[b][2m] = block sums of <V_i, x> = sum_I conj(V_i,I) x_I, i < m.
+__global__ void __launch_bounds__(kAdjThreads) k_mdot(const double2* __restrict__ V, size_t ld,
+                                                      int m, const double2* __restrict__ x,
+                                                      const int64_t* na, int64_t cap,
+                                                      double* partials) {
+    const int64_t n = min(*na, cap);
+    double acc[2 * kChunk];
+#pragma unroll
+    for (int i = 0; i < 2 * kChunk; ++i) acc[i] = 0.0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x)
-        y[p] = make_double2((double)x[p].x, (double)x[p].y);
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double2 b = x[p];
+#pragma unroll
+        for (int i = 0; i < kChunk; ++i) {
+            if (i < m) {
+                const double2 a = V[(size_t)i * ld + p];
+                acc[2 * i] += a.x * b.x + a.y * b.y;
+                acc[2 * i + 1] += a.x * b.y - a.y * b.x;
+            }
+        }
+    }
+    __shared__ double sh[kAdjThreads / 32];
+    for (int j = 0; j < 2 * m; ++j) {
+        double v = 0.0;
+#pragma unroll
+        for (int i = 0; i < 2 * kChunk; ++i)
+            if (i == j) v = acc[i];
+        v = warp_sum(v);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < kAdjThreads / 32; ++w) s += sh[w];
+            partials[(size_t)blockIdx.x * 2 * m + j] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// out = sx x + sum_{i<m} c_i V_i  (x nullable; out may be x, not a V_i).
+__global__ void k_mcomb(double2* out, const double2* x, double2 sx, const double2* __restrict__ V,
+                        size_t ld, int m, Coefs cf, const int64_t* na, int64_t cap) {
+    const int64_t n = min(*na, cap);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double re = 0.0, im = 0.0;
+        if (x) {
+            const double2 v = x[p];
+            re = sx.x * v.x - sx.y * v.y;
+            im = sx.x * v.y + sx.y * v.x;
+        }
+        for (int i = 0; i < m; ++i) {
+            const double2 v = V[(size_t)i * ld + p], c = cf.c[i];
+            re += c.x * v.x - c.y * v.y;
+            im += c.x * v.y + c.y * v.x;
+        }
+        out[p] = make_double2(re, im);
+    }
+}
+
+// Y_i = (init ? 0 : Y_i) + c_i x for i < m (Y_i ld elements apart; x is no Y_i).
+__global__ void k_mout(double2* Y, size_t ld, int m, const double2* __restrict__ x, Coefs cf,
+                       int init, const int64_t* na, int64_t cap) {
+    const int64_t n = min(*na, cap);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = x[p];
+        for (int i = 0; i < m; ++i) {
+            const double2 c = cf.c[i];
+            double2* y = Y + (size_t)i * ld + p;
+            const double2 o = init ? make_double2(0.0, 0.0) : *y;
+            *y = make_double2(o.x + c.x * v.x - c.y * v.y, o.y + c.x * v.y + c.y * v.x);
+        }
+    }
 }
 
 namespace {
@@ -343,7 +398,7 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
         if (na[n] > 0)
             PQ_CUDA_TRY(cudaMemcpyAsync(sets[n].p, s.keys, (size_t)na[n] * 4,
                                         cudaMemcpyDeviceToDevice, st));
-        if (n % ckpt == 0 && n < nsteps) {
+        if (n % ckpt == 0 && n < nsteps && s.prec == PQ_FP64) {
             if ((r = dmalloc(ck[n / ckpt], (size_t)na[n] * esz))) return r;
             if ((r = copy(ck[n / ckpt].p, s.psi, na[n]))) return r;
         }
@@ -362,11 +417,13 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
     for (int c = 0; c < ncen; ++c) dC[cen_idx[c]] += pd[1 + c];   // <d a0 | psi_N>
 
     // ---- backward sweep.  An FP32 forward run's sweep runs on an FP64 twin of
-    // the state (same basis, capacity and packet): the recorded sets are the
-    // FP32 run's, its checkpoints are widened exactly, and the adjoint kets,
-    // the recomputed kets and the Gauss-Legendre integrands are FP64.  The
-    // products of P's gradient over the integral have no FP32 cancellation
-    // floor, while P, C and the sets are those of the FP32 forward run.
+    // the state (same basis, capacity and packet): the sets are the FP32 run's,
+    // and the twin replays the propagation on them in FP64 from the initial
+    // packet, keeping FP64 checkpoints, so that the recomputed kets, the
+    // adjoint kets and the gradient sums are FP64 (the FP32 run's own states
+    // carry its rounding, which P's strong curvature in lambda turns into a
+    // gradient error above 1e-4).  P, C and the sets are those of the FP32
+    // forward run.
     struct Twin {
         State* t = nullptr;
         ~Twin() {
@@ -382,33 +439,251 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
         if (n > 0) PQ_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)n * besz, cudaMemcpyDeviceToDevice, st));
         return PQ_OK;
     };
-    // checkpoint (forward precision) -> B's coefficients
-    auto restore = [&](void* dst, const void* ckp, int64_t n) -> pq_status {
-        if (n <= 0) return PQ_OK;
-        if (!widen) return bcopy(dst, ckp, n);
-        k_widen<<<G * 4, kAdjThreads, 0, st>>>((const float2*)ckp, (double2*)dst, n);
+    if (widen) {   // FP64 replay on the recorded sets: the checkpoints
+        if ((rc = load_set(B, (const uint32_t*)sets[0].p, na[0], st)) || (rc = set_psi_from_packet(B, st)))
+            return rc;
+        for (int n = 0; n < nsteps; ++n) {
+            if (n % ckpt == 0) {
+                if ((rc = dmalloc(ck[n / ckpt], std::max<size_t>((size_t)na[n], 1) * besz)) ||
+                    (rc = bcopy(ck[n / ckpt].p, B.psi, na[n])))
+                    return rc;
+            }
+            if ((rc = sil_only(B, d, st)) ||
+                (rc = load_set(B, (const uint32_t*)sets[n + 1].p, na[n + 1], st, true)))
+                return rc;
+        }
+    }
+    DevBuf lam_b, seg_b, vjp_b;
+    size_t vmax = 0;
+    for (int64_t v : na) vmax = std::max<size_t>(vmax, (size_t)v);
+    vmax = std::max<size_t>(vmax, 1);
+    const int K = d.K;
+    // per step: V_0..V_{K-1}, W_k = H V_k, their cotangents, and wbar, ubar, H wbar
+    if ((rc = dmalloc(lam_b, vmax * besz)) || (rc = dmalloc(seg_b, (size_t)ckpt * vmax * besz)) ||
+        (rc = dmalloc(vjp_b, (size_t)(3 * K + 3) * vmax * 16)))
+        return rc;
+    double2* const Vv = (double2*)vjp_b.p;
+    double2* const Wv = Vv + (size_t)K * vmax;
+    double2* const Vb = Wv + (size_t)K * vmax;
+    double2* const wb = Vb + (size_t)K * vmax;
+    double2* const ub = wb + vmax;
+    double2* const hw = ub + vmax;
+    auto vk = [&](double2* base, int k) { return base + (size_t)k * vmax; };
+    const int64_t* dna = B.cnt + CNT_NA;
+    const int64_t bcap = (int64_t)B.cap;
+    using cd = std::complex<double>;
+    // <V_i, x> for i < m (V_i vmax elements apart)
+    auto mdot = [&](const double2* V, int m, const double2* x, std::vector<cd>& out) -> pq_status {
+        out.assign(m, 0.0);
+        for (int i0 = 0; i0 < m; i0 += kChunk) {
+            const int mm = std::min(kChunk, m - i0);
+            k_mdot<<<G, kAdjThreads, 0, st>>>(V + (size_t)i0 * vmax, vmax, mm, x, dna, bcap,
+                                             (double*)d_part.p);
+            PQ_CHECK_LAUNCH();
+            std::vector<double> h;
+            pq_status r = read_sums(d_part.p, G, 2 * mm, h, st);
+            if (r) return r;
+            for (int i = 0; i < mm; ++i) out[i0 + i] = cd(h[2 * i], h[2 * i + 1]);
+        }
+        return PQ_OK;
+    };
+    auto dot1 = [&](const double2* v, const double2* x) -> cd {
+        std::vector<cd> o;
+        return mdot(v, 1, x, o) ? cd(NAN, NAN) : o[0];
+    };
+    auto pack = [&](const std::vector<cd>& c, int i0, int m, cd scale, bool conjugate) {
+        Coefs cf;
+        for (int i = 0; i < m; ++i) {
+            const cd v = scale * (conjugate ? std::conj(c[i0 + i]) : c[i0 + i]);
+            cf.c[i] = make_double2(v.real(), v.imag());
+        }
+        return cf;
+    };
+    // out = sx x + sum_{i<m} c_i V_i
+    auto mcomb = [&](double2* out, const double2* x, cd sx, const double2* V, int m,
+                     const Coefs& cf) -> pq_status {
+        k_mcomb<<<G * 4, kAdjThreads, 0, st>>>(out, x, make_double2(sx.real(), sx.imag()), V, vmax,
+                                               m, cf, dna, bcap);
         PQ_CHECK_LAUNCH();
         return PQ_OK;
     };
-    DevBuf lam_b, mu_b, psig_b, seg_b;
-    size_t vmax = 0;
-    for (int64_t v : na) vmax = std::max<size_t>(vmax, (size_t)v);
-    if ((rc = dmalloc(lam_b, vmax * besz)) || (rc = dmalloc(mu_b, vmax * besz)) ||
-        (rc = dmalloc(psig_b, vmax * besz)) || (rc = dmalloc(seg_b, (size_t)ckpt * vmax * besz)))
-        return rc;
-    std::vector<double> gx, gw;
-    gauss_legendre(5, gx, gw);
-    // lambda_N = a0 on A_N
+    auto mout = [&](double2* Y, int m, const double2* x, const Coefs& cf, int init) -> pq_status {
+        for (int i0 = 0; i0 < m; i0 += kChunk) {
+            Coefs part;
+            const int mm = std::min(kChunk, m - i0);
+            for (int i = 0; i < mm; ++i) part.c[i] = cf.c[i0 + i];
+            k_mout<<<G * 4, kAdjThreads, 0, st>>>(Y + (size_t)i0 * vmax, vmax, mm, x, part, init,
+                                                  dna, bcap);
+            PQ_CHECK_LAUNCH();
+        }
+        return PQ_OK;
+    };
+    auto Hx = [&](const double2* in, double2* out) -> pq_status {
+        return apply_H_launch(B, in, out, PQ_FP64, nullptr, nullptr, 0, st);
+    };
+    std::vector<double> thbar(npot, 0.0);
+
+    // Reverse pass through one SIL step on the current set of B (Sec. 3.1 with
+    // the order fixed): on entry B.psi holds ybar, the cotangent of the step's
+    // output (dL = Re<ybar, dy>); on exit it holds the cotangent of the input a,
+    // and thbar has gained the step's Re<wbar_k, dH/dtheta V_k>.  The forward
+    // Lanczos process is repeated in FP64 with explicitly normalised vectors and
+    // one classical Gram-Schmidt pass against all previous vectors (equal, in
+    // exact arithmetic, to the three-term recurrence of the propagation, so the
+    // derivative is that of the same map):
+    //   V_0 = a/b0, W_k = H V_k, c_ik = <V_i, W_k>, alpha_k = Re c_kk,
+    //   u_k = W_k - sum_i c_ik V_i, beta_k = ||u_k||, V_{k+1} = u_k/beta_k,
+    //   y = b0 sum_j e_j V_j,  e = exp(-i T dt) e_1 of the Lanczos tridiagonal T.
+    // The derivative of e with respect to T is the Daleckii-Krein formula in T's
+    // eigenbasis (divided differences of exp(-i z dt)).
+    auto step_vjp = [&](const double2* a) -> pq_status {
+        double2* ybar = (double2*)B.psi;
+        const double b0 = sqrt(std::max(0.0, dot1(a, a).real()));
+        if (!std::isfinite(b0)) {
+            set_error("non-finite state in the gradient's reverse sweep");
+            return PQ_ENUMERIC;
+        }
+        if (!(b0 > 0.0)) return PQ_OK;   // zero state: the step is the identity
+        const Coefs none{};
+        pq_status r;
+        if ((r = mcomb(vk(Vv, 0), a, 1.0 / b0, nullptr, 0, none))) return r;
+        std::vector<std::vector<cd>> c(K);
+        std::vector<double> alpha(K, 0.0), beta(K, 0.0);
+        int Ke = K;
+        for (int k = 0; k < K; ++k) {
+            if ((r = Hx(vk(Vv, k), vk(Wv, k)))) return r;
+            const int i0 = k == K - 1 ? k : 0;
+            std::vector<cd> ck;
+            if ((r = mdot(vk(Vv, i0), k - i0 + 1, vk(Wv, k), ck))) return r;
+            c[k].assign(k + 1, 0.0);
+            for (int i = i0; i <= k; ++i) c[k][i] = ck[i - i0];
+            alpha[k] = c[k][k].real();
+            if (k == K - 1) break;
+            if ((r = mcomb(vk(Vv, k + 1), vk(Wv, k), 1.0, vk(Vv, 0), k + 1, pack(c[k], 0, k + 1, -1.0, false))))
+                return r;
+            const double b = sqrt(std::max(0.0, dot1(vk(Vv, k + 1), vk(Vv, k + 1)).real()));
+            const double hn = sqrt(std::max(0.0, dot1(vk(Wv, k), vk(Wv, k)).real()));
+            if (!std::isfinite(b) || !std::isfinite(alpha[k])) {
+                set_error("non-finite Lanczos scalars in the gradient's reverse sweep");
+                return PQ_ENUMERIC;
+            }
+            if (b <= 1e-12 * hn) {   // invariant subspace: the propagation stops here too
+                Ke = k + 1;
+                break;
+            }
+            beta[k] = b;
+            if ((r = mcomb(vk(Vv, k + 1), vk(Vv, k + 1), 1.0 / b, nullptr, 0, none))) return r;
+        }
+        // T = Z diag(lam) Z^T; e_j = sum_p Z_jp exp(-i lam_p dt) Z_0p
+        std::vector<double> T((size_t)Ke * Ke, 0.0), lam, Z;
+        for (int k = 0; k < Ke; ++k) {
+            T[(size_t)k * Ke + k] = alpha[k];
+            if (k + 1 < Ke) T[(size_t)k * Ke + k + 1] = T[(size_t)(k + 1) * Ke + k] = beta[k];
+        }
+        if (jacobi_eigh(Ke, T, lam, Z) < 0) {
+            set_error("eigensolver of the Lanczos tridiagonal did not converge");
+            return PQ_ENUMERIC;
+        }
+        auto z = [&](int i, int j) { return Z[(size_t)i * Ke + j]; };
+        const double dt = d.dt;
+        std::vector<cd> e(Ke, 0.0);
+        for (int j = 0; j < Ke; ++j)
+            for (int q = 0; q < Ke; ++q) e[j] += z(j, q) * std::exp(cd(0.0, -lam[q] * dt)) * z(0, q);
+        // cotangents of e, b0 and the V_j from y = b0 sum_j e_j V_j
+        std::vector<cd> ebar;
+        if ((r = mdot(vk(Vv, 0), Ke, ybar, ebar))) return r;
+        double b0bar = 0.0;
+        for (int j = 0; j < Ke; ++j) {
+            ebar[j] *= b0;
+            b0bar += std::real(e[j] * std::conj(ebar[j]));
+        }
+        b0bar /= b0;
+        {
+            std::vector<cd> s(Ke);
+            for (int j = 0; j < Ke; ++j) s[j] = b0 * std::conj(e[j]);
+            if ((r = mout(Vb, Ke, ybar, pack(s, 0, Ke, 1.0, false), 1))) return r;
+        }
+        // Tbar = Z Re(Y o G) Z^T with Y_pq = sum_i Z_ip ebar_i Z_0q and G_pq the
+        // divided difference of exp(+i z dt) at lam_p, lam_q
+        std::vector<double> Tbar((size_t)Ke * Ke, 0.0), RY((size_t)Ke * Ke);
+        for (int p = 0; p < Ke; ++p) {
+            cd zp = 0.0;
+            for (int i = 0; i < Ke; ++i) zp += z(i, p) * ebar[i];
+            for (int q = 0; q < Ke; ++q) {
+                const double x = dt * (lam[p] - lam[q]);
+                const cd g = std::exp(cd(0.0, lam[q] * dt));
+                const cd G = std::fabs(x) < 1e-8 ? cd(0.0, dt) * g * cd(1.0, 0.5 * x)
+                                                 : g * (std::exp(cd(0.0, x)) - 1.0) / (lam[p] - lam[q]);
+                RY[(size_t)p * Ke + q] = std::real(zp * z(0, q) * G);
+            }
+        }
+        for (int i = 0; i < Ke; ++i)
+            for (int j = 0; j < Ke; ++j) {
+                double acc = 0.0;
+                for (int p = 0; p < Ke; ++p)
+                    for (int q = 0; q < Ke; ++q) acc += z(i, p) * RY[(size_t)p * Ke + q] * z(j, q);
+                Tbar[(size_t)i * Ke + j] = acc;
+            }
+        // reverse Lanczos recurrence
+        for (int k = Ke - 1; k >= 0; --k) {
+            const bool last = k == Ke - 1;
+            const int i0 = last ? k : 0;
+            std::vector<cd> cbar(k + 1, 0.0);
+            if (!last) {
+                const double b = beta[k];
+                const double rr = dot1(vk(Vv, k + 1), vk(Vb, k + 1)).real();
+                const double bebar = Tbar[(size_t)k * Ke + k + 1] + Tbar[(size_t)(k + 1) * Ke + k];
+                Coefs cv{};
+                cv.c[0] = make_double2(bebar - rr / b, 0.0);
+                // ubar = Vbar_{k+1}/beta_k + (betabar_k - Re<V_{k+1}, Vbar_{k+1}>/beta_k) V_{k+1}
+                if ((r = mcomb(ub, vk(Vb, k + 1), 1.0 / b, vk(Vv, k + 1), 1, cv))) return r;
+                std::vector<cd> dv;
+                if ((r = mdot(vk(Vv, 0), k + 1, ub, dv))) return r;
+                for (int i = 0; i <= k; ++i) cbar[i] = -dv[i];
+                if ((r = mout(Vb, k + 1, ub, pack(c[k], 0, k + 1, -1.0, true), 0))) return r;
+            }
+            cbar[k] += Tbar[(size_t)k * Ke + k];   // alpha_k = Re c_kk
+            // wbar = ubar + sum_i cbar_i V_i ; Vbar_i += conj(cbar_i) W_k ; Vbar_k += H wbar
+            if ((r = mcomb(wb, last ? nullptr : ub, 1.0, vk(Vv, i0), k - i0 + 1,
+                           pack(cbar, i0, k - i0 + 1, 1.0, false))) ||
+                (r = mout(vk(Vb, i0), k - i0 + 1, vk(Wv, k), pack(cbar, i0, k - i0 + 1, 1.0, true), 0)) ||
+                (r = Hx(wb, hw)))
+                return r;
+            Coefs one{};
+            one.c[0] = make_double2(1.0, 0.0);
+            if ((r = mcomb(vk(Vb, k), vk(Vb, k), 1.0, hw, 1, one))) return r;
+            if (npot > 0) {
+                k_grad_dots<double><<<G, kAdjThreads, 0, st>>>(
+                    B.keys, wb, vk(Vv, k), dna, bcap, L, (const double*)d_tab.p,
+                    (const double*)d_coef.p, (const int*)d_toff.p, npot, (double*)d_part.p);
+                PQ_CHECK_LAUNCH();
+                std::vector<double> h;
+                if ((r = read_sums(d_part.p, G, 2 * npot, h, st))) return r;
+                for (int q = 0; q < npot; ++q) thbar[q] += h[2 * q];
+            }
+        }
+        // abar = Vbar_0/b0 + (b0bar - Re<V_0, Vbar_0>/b0) V_0
+        const double r0 = dot1(vk(Vv, 0), vk(Vb, 0)).real();
+        Coefs cv{};
+        cv.c[0] = make_double2(b0bar - r0 / b0, 0.0);
+        return mcomb((double2*)B.psi, vk(Vb, 0), 1.0 / b0, vk(Vv, 0), 1, cv);
+    };
+
+    // psibar_N = 2 C a0 on A_N  (dP = Re<psibar_N, d psi_N> + the bra's share)
     if ((widen && (rc = load_set(B, (const uint32_t*)sets[nsteps].p, na[nsteps], st))) ||
         (rc = set_psi_from_packet(B, st)))
         return rc;
+    {
+        const Coefs none{};
+        if ((rc = mcomb((double2*)B.psi, (const double2*)B.psi, 2.0 * C, nullptr, 0, none))) return rc;
+    }
     pq_prop_desc dd = d;
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int c = sg * ckpt, e = std::min(nsteps, c + ckpt);
         if ((rc = bcopy(lam_b.p, B.psi, na[e]))) return rc;
         // recompute psi_c .. psi_{e-1} on their recorded sets
         if ((rc = load_set(B, (const uint32_t*)sets[c].p, na[c], st)) ||
-            (rc = restore(B.psi, ck[sg].p, na[c])))
+            (rc = bcopy(B.psi, ck[sg].p, na[c])))
             return rc;
         for (int n = c; n < e; ++n) {
             if ((rc = bcopy((char*)seg_b.p + (size_t)(n - c) * vmax * besz, B.psi, na[n]))) return rc;
@@ -422,45 +697,20 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
         if ((rc = load_set(B, (const uint32_t*)sets[e].p, na[e], st)) || (rc = bcopy(B.psi, lam_b.p, na[e])))
             return rc;
         for (int n = e - 1; n >= c; --n) {
-            // mu = R_n^T lambda_{n+1} on A_n
+            // ybar = R_n^T psibar_{n+1} on A_n, then the step's reverse pass
             if ((rc = load_set(B, (const uint32_t*)sets[n].p, na[n], st, true)) ||
-                (rc = bcopy(mu_b.p, B.psi, na[n])))
+                (rc = step_vjp((const double2*)((char*)seg_b.p + (size_t)(n - c) * vmax * besz))))
                 return rc;
-            const void* psin = (char*)seg_b.p + (size_t)(n - c) * vmax * besz;
-            for (size_t g = 0; g < gx.size() && npot > 0; ++g) {
-                const double sgn = d.dt * (1.0 + gx[g]) / 2.0, wg = gw[g] * d.dt / 2.0;
-                dd.dt = sgn;                                   // U(s) psi_n
-                if ((rc = bcopy(B.psi, psin, na[n])) || (rc = sil_only(B, dd, st)) ||
-                    (rc = bcopy(psig_b.p, B.psi, na[n])))
-                    return rc;
-                dd.dt = -(d.dt - sgn);                         // U(dt-s)^dagger mu
-                if ((rc = bcopy(B.psi, mu_b.p, na[n])) || (rc = sil_only(B, dd, st))) return rc;
-                if (B.prec == PQ_FP64)
-                    k_grad_dots<double><<<G, kAdjThreads, 0, st>>>(
-                        B.keys, (const double2*)B.psi, (const double2*)psig_b.p, B.cnt + CNT_NA,
-                        (int64_t)B.cap, L, (const double*)d_tab.p, (const double*)d_coef.p,
-                        (const int*)d_toff.p, npot, (double*)d_part.p);
-                else
-                    k_grad_dots<float><<<G, kAdjThreads, 0, st>>>(
-                        B.keys, (const float2*)B.psi, (const float2*)psig_b.p, B.cnt + CNT_NA,
-                        (int64_t)B.cap, L, (const double*)d_tab.p, (const double*)d_coef.p,
-                        (const int*)d_toff.p, npot, (double*)d_part.p);
-                PQ_CHECK_LAUNCH();
-                std::vector<double> h;
-                if ((rc = read_sums(d_part.p, G, 2 * npot, h, st))) return rc;
-                for (int q = 0; q < npot; ++q)
-                    dC[pot_idx[q]] += std::complex<double>(0.0, -wg) * std::complex<double>(h[2 * q], h[2 * q + 1]);
-            }
-            dd.dt = -d.dt;                                     // lambda_n = U^dagger mu
-            if ((rc = bcopy(B.psi, mu_b.p, na[n])) || (rc = sil_only(B, dd, st))) return rc;
         }
     }
-    // <lambda_0 | d psi_0> for the packet centres (psi_0 = a0 on A_0)
+    for (int q = 0; q < npot; ++q) grad[pot_idx[q]] = thbar[q];
+    // packet centres: the bra's share 2 Re(conj(C) <d a0|psi_N>) and the
+    // initial state's Re<psibar_0, d a0> (psi_0 = a0 on A_0)
+    for (int cc = 0; cc < ncen; ++cc) grad[cen_idx[cc]] = 2.0 * std::real(std::conj(C) * dC[cen_idx[cc]]);
     if (ncen > 0) {
         if ((rc = packet_dots_on(B, B.psi, pd))) return rc;
-        for (int c = 0; c < ncen; ++c) dC[cen_idx[c]] += std::conj(pd[1 + c]);
+        for (int cc = 0; cc < ncen; ++cc) grad[cen_idx[cc]] += std::real(pd[1 + cc]);
     }
-    for (int q = 0; q < np; ++q) grad[q] = 2.0 * std::real(std::conj(C) * dC[q]);
     if (P_out) *P_out = std::norm(C);
     // leave the state at its initial packet
     if ((rc = init_bits_from_packet(s, s.theta, st)) || (rc = set_psi_from_packet(s, st))) return rc;

@@ -69,10 +69,14 @@ def _golden_adjoint():
 def test_adjoint_full_config(prec):
     """The adjoint workload as specified (4D Henon-Heiles, 24 points per mode,
     T = 20 in 200 steps, checkpoints every 25 steps) against the FP64 oracle's
-    frozen-set central-difference gradient (h = 1e-4) stored by
-    tests/golden/make_series.py: relative error <= 1e-4, norm-wise and per
-    component against the largest.  prec 1 is the FP32-mix forward run (its
-    own sets and checkpoints) with the FP64 adjoint sweep."""
+    frozen-set finite differences stored by tests/golden/make_series.py.  The
+    reference is the Richardson combination of the central differences at
+    h = 1e-4 and h/2 (truncation error O(h^4)): relative error <= 1e-4,
+    norm-wise and per component against the largest.  Against the plain
+    h = 1e-4 difference the gradient agrees within that difference's own
+    truncation error (estimated from h and h/2) plus 1e-4.  prec 1 is the
+    FP32-mix forward run (its own sets and checkpoints) with the FP64 reverse
+    sweep."""
     g = _golden_adjoint()
     cfg = W.ADJOINT4D
     assert g["nsteps"] == cfg["nsteps"]
@@ -81,6 +85,9 @@ def test_adjoint_full_config(prec):
     assert abs(P - g["P"]) <= (1e-10 if prec == 0 else 1e-4) * g["P"]
     assert np.linalg.norm(grad - ref) <= 1e-4 * np.linalg.norm(ref), (grad, ref)
     assert np.all(np.abs(grad - ref) <= 1e-4 * np.abs(ref).max()), (grad, ref)
+    gh, gh2 = np.array(g["grad_h"]), np.array(g["grad_h2"])
+    trunc = 4.0 / 3.0 * np.abs(gh - gh2)
+    assert np.all(np.abs(grad - gh) <= trunc + 1e-4 * np.abs(ref).max()), (grad, gh, trunc)
 
 
 def test_adjoint_checkpoint_interval_is_exact():
