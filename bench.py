@@ -387,6 +387,38 @@ def run_ours(args, cfg):
     e2e = {"value": A_n / e2e_s / 1e9 * ws, "unit": "Gcoef/s",
            "h2d_bytes_per_step": A_n * esz, "d2h_bytes_per_step": A_n * esz}
 
+    # late window: the same state propagated on (untimed) to step --late-start,
+    # then args.steps steps timed the same way (the hh6d set fills the whole
+    # lattice after about 100 steps and stays there for the rest of the run)
+    late = None
+    if args.late_start > 0 and ws == 1:
+        done = len(s.observables()["n_active"]) - 1
+        if args.late_start > done:
+            s.set_timing(False)
+            s.propagate(K, dt, th, args.late_start - done, stream=sptr)
+        n0 = len(s.observables()["n_active"])
+        s.set_timing(True)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk_late:
+            g0.record(stream)
+            s.propagate(K, dt, th, args.steps, stream=sptr)
+            g1.record(stream)
+            torch.cuda.synchronize()
+        ms_late = g0.elapsed_time(g1)
+        na_l = s.observables()["n_active"]
+        coef_l = float(np.sum(na_l[n0 - 1:n0 - 1 + args.steps])) * K
+        tl = s.timing()
+        apply_l = tl["apply_ms"] * 1e-3   # set_timing(True) restarted the counters
+        capp_l = tl["coef_applied"]
+        ach_l = capp_l * bpc / apply_l / 1e9 if apply_l > 0 else 0.0
+        late = {"steps": [n0 - 1, n0 - 1 + args.steps], "value": coef_l / (ms_late * 1e-3) / 1e9,
+                "unit": "Gcoef/s", "ms_per_step": ms_late / args.steps,
+                "n_active_first": int(na_l[n0 - 1]), "n_active_last": int(na_l[-1]),
+                "lattice_points": int(cfg["n"] ** cfg["D"]),
+                "apply_gcoef_s": capp_l / apply_l / 1e9 if apply_l > 0 else None,
+                "achieved_gbs": ach_l, "frac": ach_l / peak, "clocks": clk_late.summary()}
+
     line = {
         "metric": "pruned H.psi active-coefficient applications per second",
         "value": value, "unit": "Gcoef/s", "n_gpus": ws, "steps": args.steps,
@@ -407,6 +439,7 @@ def run_ours(args, cfg):
                      "alu": alu, "alu_frac": alu["frac"] if alu else None},
         "clocks": clk.summary(),
         "e2e": e2e,
+        "late_window": late,
     }
 
     if rank == 0 and ws == 1 and not args.no_fp64_compare and prec == pq.FP32MIX:
@@ -456,6 +489,8 @@ def run_apply(args, cfg):
     import torch
     import paper_1606_04004_gb300 as pq
     prec = pq.FP32MIX if args.precision == "fp32mix" else pq.FP64
+    if args.lattice:   # a smaller lattice of the same model (profiling captures)
+        cfg = W.scaled(cfg, n=args.lattice)
     b = pq.build_model(cfg)
     r = args.radius
     A = W.ellipsoid_active_set((cfg["n"],) * cfg["D"], (r,) * cfg["D"])
@@ -641,9 +676,10 @@ def run_dwell(args):
     the unpruned FGH run (theta = 0)."""
     import paper_1606_04004_gb300 as pq
 
-    def series(cfg, theta, rule):
+    def series(cfg, theta, rule, prec=None):
         b = pq.build_model(cfg)
-        s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], theta, precision=pq.FP64, radius=rule)
+        prec = pq.FP64 if prec is None else prec
+        s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], theta, precision=prec, radius=rule)
         s.propagate(cfg["K"], cfg["dt"], theta, cfg["nsteps"], radius=rule)
         o = s.observables()
         s.free()
@@ -658,17 +694,17 @@ def run_dwell(args):
     plan = [(W.DWELL2D, "fgh", pq.RADIUS_1, "1"), (W.DWELL2D, "fgh", pq.RADIUS_SQRT2, "sqrt2"),
             (W.DWELL2D_PW, "pw", pq.RADIUS_1, "1"), (W.DWELL2D_PW, "pw", pq.RADIUS_SQRT2, "sqrt2"),
             (W.DWELL2D_PW, "pw", pq.RADIUS_2, "2"), (W.DWELL2D_PVB, "pvb", pq.RADIUS_1, "1")]
-    # pvB is left out unless asked for: every Krylov vector needs a conjugate-
-    # gradient solve driven from the host, and one 2460-step run took longer
-    # than 15 minutes on a GB300
+    # pvB is left out unless asked for: every Krylov vector needs a solve of
+    # S_AA (preconditioned conjugate gradients), about 0.23 s per FP64 step and
+    # 0.07 s per FP32-mix step; --dwell-pvb-fp32 runs its column in FP32-mix
     wanted = args.dwell_bases.split(",") if args.dwell_bases else ["fgh", "pw"]
     plan = [p for p in plan if p[1] in wanted]
     for cfg, basis, rule, name in plan:
-        # pvB solves S_AA x = y by conjugate gradients for every Krylov vector
-        # (host-driven), so it gets a shorter threshold list
+        prec = pq.FP32MIX if (basis == "pvb" and args.dwell_pvb_fp32) else pq.FP64
         for theta in (thetas if basis != "pvb" else (3e-2, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6)):
-            o = series(cfg, theta, rule)
+            o = series(cfg, theta, rule, prec)
             row = {"mode": "dwell", "basis": basis, "radius": name, "theta": theta,
+                   "precision": "fp32mix" if prec == pq.FP32MIX else "fp64",
                    "mean_basis_pct": float(100.0 * o["n_active"].mean() / nfull),
                    "infidelity": float(np.linalg.norm(o["C"] - exact["C"]))}
             print(json.dumps(row), flush=True)
@@ -691,9 +727,12 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--mode", default="step", choices=["step", "apply", "dwell", "snapshot", "peaks"])
     ap.add_argument("--radius", type=float, default=11.2)
+    ap.add_argument("--lattice", type=int, default=0)
+    ap.add_argument("--late-start", type=int, default=100)   # step the late window starts at (0: none)   # --mode apply: points per mode (0: the workload's)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--snapshots", default="0,20,50,100")   # steps of --mode snapshot
     ap.add_argument("--dwell-bases", default="")   # comma list of fgh,pw,pvb (default fgh,pw)
+    ap.add_argument("--dwell-pvb-fp32", action="store_true")   # the pvB column in FP32-mix
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("need at least 3 warm-up steps")

@@ -28,6 +28,8 @@
 //  * generic single-mode passes (k_pass_row, k_pass_fibre): projected Weylets.
 // A tabulated (non-SoP) diagonal potential is added per active point after
 // the passes (k_add_grid_potential).
+#include <type_traits>
+
 #include "device_util.cuh"
 
 namespace pq {
@@ -57,6 +59,7 @@ struct ApplyArgs {
     uint64_t units_cap;         // entries of the units array (bounds-check build)
     int ngroup[4];              // potential terms by tile modes touched (neither, D-2, D-1, both)
     const uint2* rowinfo;       // per-row (start, pattern) table, or null
+    int full_gate;              // 1: run only on a dense set (>= half the lattice); -1: only below; 0: always
     const uint32_t* keys;       // sorted active linear indices (point-parallel pass)
     // generic single-mode pass (phase-space bases)
     const R* mat;               // n x n matrix of the pass (row stride kMaxN)
@@ -66,6 +69,18 @@ struct ApplyArgs {
 
 __device__ __forceinline__ uint64_t low_mask(int s) {
     return s >= 64 ? ~0ull : ((1ull << s) - 1ull);
+}
+
+// Dense-set gate: the item-blocked kernels and the dense-tile kernels of an
+// FP32 H.psi are both launched, and the active-set size on the device selects
+// which of them works (at least half the lattice active: the dense-tile
+// kernels; the set can cross that size inside a device-driven propagation
+// without the host seeing it).
+template <typename A>
+__device__ __forceinline__ bool gated_off(const A& a) {
+    if (a.full_gate == 0) return false;
+    const bool dense = 2 * a.cnt[CNT_NA] >= (int64_t)a.L.nfull;
+    return dense != (a.full_gate > 0);
 }
 
 template <typename R>
@@ -1574,6 +1589,7 @@ template <typename R, int W>
 __global__ void __launch_bounds__(kApplyThreads) k_outer_q(ApplyArgs<R> a) {
     using V = typename Cx<R>::T;
     if (a.skip && *a.skip <= a.skip_k) return;
+    if (gated_off(a)) return;
     if (a.cnt[CNT_ERR] & 1) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ QuadMeta meta[kQWarps];
@@ -1634,6 +1650,419 @@ __global__ void __launch_bounds__(kApplyThreads) k_outer_q(ApplyArgs<R> a) {
     }
 }
 
+// ------------------------------------------------------------------------
+// Dense-tile passes (FP32), for sets that cover at least half the lattice
+// (the 6D Henon-Heiles set fills the whole 24^6 lattice after about 100
+// steps).  A block stages whole tiles of the lattice in shared memory, each
+// point found through the row table (row start in A and pattern: position =
+// start + popcount of the pattern below the point) and zero where inactive, and
+// treats the tile as dense: the passes are batched contractions with no
+// compaction or item lists, and only active outputs are written.  Each thread
+// owns a 4 x 4 block of outputs (four fibre points by four last-mode points)
+// in registers, so one 16-byte shared-memory load of operator entries and two
+// of coefficients feed 16 packed complex FMAs.
+//   inner pass: kDensePlanes planes (modes D-2 and D-1 with the other digits
+//     fixed) per block; both modes and the SoP potential; each output written
+//     once;
+//   pair pass over outer modes (k, k+1): a tile of n[k] x n[k+1] rows (the
+//     rows that differ only in digits k and k+1) by kDenseC last-mode points
+//     per block; both modes, added to the output in place (the block owns
+//     these outputs in this pass).
+// Both run a two-stage pipeline over their units: the asynchronous copies of
+// the next unit are in flight while the block computes the current one from
+// the other buffer.  The products are linear in the input, so the Krylov
+// scale is applied to the results.
+constexpr int kDenseThreads = 288;
+constexpr int kDensePlanes = 8;
+constexpr int kDenseC = 8;
+
+// acc[r][q] += t[r] x[q]
+__device__ __forceinline__ void outer4(float2 (&acc)[4][4], const float4& t, const float2 (&x)[4]) {
+    const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cfma(acc[r][q], tv[r], x[q]);
+}
+
+__device__ __forceinline__ void ld4(const float2* p, float2 (&x)[4]) {
+    const float4 u = reinterpret_cast<const float4*>(p)[0];
+    const float4 v = reinterpret_cast<const float4*>(p)[1];
+    x[0] = make_float2(u.x, u.y);
+    x[1] = make_float2(u.z, u.w);
+    x[2] = make_float2(v.x, v.y);
+    x[3] = make_float2(v.z, v.w);
+}
+
+__device__ __forceinline__ void st4(float2* p, const float2 (&x)[4]) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
+    reinterpret_cast<float4*>(p)[1] = make_float4(x[2].x, x[2].y, x[3].x, x[3].y);
+}
+
+// 8-byte asynchronous global -> shared copy; zero-fills the destination when
+// !valid (no bytes are read then).
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    const int nb = valid ? 8 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gsrc), "r"(nb)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() {
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+
+// Stage points [c0, c0 + n) of a lattice row with row-table entry ri at sdst
+// (16-byte aligned, n even), zero where inactive: 16-byte copies when the span
+// is fully active and starts on an even position, else one 8-byte copy (or
+// zero fill) per point.
+__device__ __forceinline__ void stage_row(float2* sdst, const float2* in, uint2 ri, int c0, int n) {
+    const uint32_t full = n >= 32 ? ~0u : (1u << n) - 1u;
+    const uint32_t m = (ri.y >> c0) & full;
+    uint32_t pos = ri.x + (uint32_t)__popc(ri.y & ((1u << c0) - 1u));
+    if (m == full && !(pos & 1u)) {
+        for (int h = 0; h < n / 2; ++h) cp_async16(sdst + 2 * h, in + pos + 2 * h);
+        return;
+    }
+    for (int c = 0; c < n; ++c) {
+        const bool on = (m >> c) & 1u;
+        cp_async8(sdst + c, on ? in + pos : in, on);
+        pos += on ? 1u : 0u;
+    }
+}
+
+// The dense-tile kernels keep three row-table buffers and two coefficient
+// buffers: in the iteration of unit u the block copies the coefficients of
+// the next unit (rows staged one iteration earlier) and the row-table entries
+// of the unit after it, and computes u; one wait and one barrier per unit.
+
+// Inner pass on a dense set: y = T^{D-2} x + T^{D-1} x + V x per plane.
+__global__ void __launch_bounds__(kDenseThreads) k_dense_inner(ApplyArgs<float> a) {
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (gated_off(a)) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lattice& L = a.L;
+    const int D = L.D, n2 = L.n[D - 2], nl = L.nlast, nt = a.nterms, pl = n2 * nl;
+    const int g1 = a.ngroup[0], g2 = g1 + a.ngroup[1], g3 = g2 + a.ngroup[2];
+    float2* Xb = reinterpret_cast<float2*>(smem);                         // [2][P][n2][nl]
+    float* T2 = reinterpret_cast<float*>(Xb + (size_t)2 * kDensePlanes * pl);   // [j][i] = T^{D-2}[i][j]
+    float* Tl = T2 + n2 * n2;                                             // [s][c] = T^{D-1}[c][s]
+    float* Vr = Tl + nl * nl;                                             // [P][n2] (with the constant)
+    float* Vs = Vr + kDensePlanes * n2;                                   // [P][nl]
+    float* pf = Vs + kDensePlanes * nl;                                   // [P][nt] term prefactors
+    const int nboth = nt - g3;
+    float* F2 = pf + kDensePlanes * (nt > 1 ? nt : 1);                   // [nboth][n2] both-mode factors
+    float* F3 = F2 + nboth * n2;                                          // [nboth][nl]
+    uint2* Rb = reinterpret_cast<uint2*>(((uintptr_t)(F3 + nboth * nl) + 15) & ~(uintptr_t)15);   // [3][P * n2]
+    for (int i = threadIdx.x; i < nboth * n2; i += blockDim.x)
+        F2[i] = a.pot[((size_t)(g3 + i / n2) * D + D - 2) * kMaxN + i % n2];
+    for (int i = threadIdx.x; i < nboth * nl; i += blockDim.x)
+        F3[i] = a.pot[((size_t)(g3 + i / nl) * D + D - 1) * kMaxN + i % nl];
+    for (int i = threadIdx.x; i < n2 * n2; i += blockDim.x) {
+        const int j = i / n2, r = i - j * n2;
+        T2[i] = a.T[(size_t)(D - 2) * kMaxN * kMaxN + r * kMaxN + j];
+    }
+    for (int i = threadIdx.x; i < nl * nl; i += blockDim.x) {
+        const int sp = i / nl, c = i - sp * nl;
+        Tl[i] = a.T[(size_t)(D - 1) * kMaxN * kMaxN + c * kMaxN + sp];
+    }
+    const float scale = a.in_scale ? (float)(*a.in_scale) : 1.f;
+    const int nab = n2 / 4, ncb = nl / 4;
+    const uint32_t nunits = (L.nplanes + kDensePlanes - 1) / kDensePlanes;
+    auto nplanes_of = [&](uint32_t u) {
+        return (int)min((uint32_t)kDensePlanes, L.nplanes - u * kDensePlanes);
+    };
+    auto fetch_rows = [&](uint32_t u, int r3) {   // the unit's rows are consecutive
+        const uint64_t r0 = (uint64_t)u * kDensePlanes * n2;
+        uint2* dst = Rb + (size_t)r3 * kDensePlanes * n2;
+        for (int i = threadIdx.x; i < nplanes_of(u) * n2; i += blockDim.x)
+            cp_async8(dst + i, a.rowinfo + r0 + i, true);
+    };
+    auto issue = [&](uint32_t u, int buf, const uint2* R) {
+        float2* dst = Xb + (size_t)buf * kDensePlanes * pl;
+        for (int rowi = threadIdx.x; rowi < nplanes_of(u) * n2; rowi += blockDim.x)
+            stage_row(dst + (size_t)rowi * nl, a.in, R[rowi], 0, nl);
+    };
+    const uint32_t G = gridDim.x;
+    if (blockIdx.x < nunits) {
+        fetch_rows(blockIdx.x, 0);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        issue(blockIdx.x, 0, Rb);
+        if (blockIdx.x + G < nunits) fetch_rows(blockIdx.x + G, 1);
+        cp_async_commit();
+    }
+    int it = 0;
+    for (uint32_t u = blockIdx.x; u < nunits; u += G, ++it) {
+        const uint32_t P0 = u * kDensePlanes;
+        const int np = nplanes_of(u);
+        cp_async_wait_all();
+        __syncthreads();   // this unit's coefficients and the next unit's rows
+        if (u + G < nunits) issue(u + G, (it + 1) & 1, Rb + (size_t)((it + 1) % 3) * kDensePlanes * n2);
+        if (u + 2 * G < nunits) fetch_rows(u + 2 * G, (it + 2) % 3);
+        cp_async_commit();
+        const float2* X = Xb + (size_t)(it & 1) * kDensePlanes * pl;
+        const uint2* R = Rb + (size_t)(it % 3) * kDensePlanes * n2;
+        // term prefactors over the plane's other digits
+        for (int i = threadIdx.x; i < np * nt; i += blockDim.x) {
+            const int p = i / nt, t = i - p * nt;
+            const uint32_t P = P0 + (uint32_t)p;
+            float v = a.potc[t];
+            for (int kk = 0; kk < D - 2; ++kk) {
+                const int d = (int)((P / L.pstride[kk]) % (uint32_t)L.n[kk]);
+                v *= a.pot[((size_t)t * D + kk) * kMaxN + d];
+            }
+            pf[p * nt + t] = v;
+        }
+        __syncthreads();   // pf
+        for (int i = threadIdx.x; i < np * n2; i += blockDim.x) {
+            const int p = i / n2, r = i - p * n2;
+            float v = 0.f;
+            for (int t = 0; t < g1; ++t) v += pf[p * nt + t];
+            for (int t = g1; t < g2; ++t) v += pf[p * nt + t] * a.pot[((size_t)t * D + D - 2) * kMaxN + r];
+            Vr[p * n2 + r] = v;
+        }
+        for (int i = threadIdx.x; i < np * nl; i += blockDim.x) {
+            const int p = i / nl, c = i - p * nl;
+            float v = 0.f;
+            for (int t = g2; t < g3; ++t) v += pf[p * nt + t] * a.pot[((size_t)t * D + D - 1) * kMaxN + c];
+            Vs[p * nl + c] = v;
+        }
+        __syncthreads();
+        for (int task = threadIdx.x; task < np * nab * ncb; task += blockDim.x) {
+            const int p = task / (nab * ncb), rem = task - p * nab * ncb;
+            const int i0 = (rem / ncb) * 4, c0 = (rem % ncb) * 4;
+            const float2* Xp = X + (size_t)p * pl;
+            float2 acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] = make_float2(0.f, 0.f);
+            // mode D-2: acc[r][q] += T[i0+r][j] x[j][c0+q]
+#pragma unroll 4
+            for (int j = 0; j < n2; ++j) {
+                const float4 t = *reinterpret_cast<const float4*>(T2 + j * n2 + i0);
+                float2 x[4];
+                ld4(Xp + j * nl + c0, x);
+                outer4(acc, t, x);
+            }
+            // mode D-1: acc[r][q] += T[c0+q][s] x[i0+r][s]
+#pragma unroll 4
+            for (int sp = 0; sp < nl; ++sp) {
+                const float4 t = *reinterpret_cast<const float4*>(Tl + sp * nl + c0);
+                const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float2 x = Xp[(i0 + r) * nl + sp];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) cfma(acc[r][q], tv[q], x);
+                }
+            }
+            // potential; active outputs only, 16-byte stores for four active
+            // points that start on an even position
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const uint2 ri = R[p * n2 + i0 + r];
+                const uint32_t mk = (ri.y >> c0) & 0xFu;
+                float2 x[4];
+                ld4(Xp + (i0 + r) * nl + c0, x);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float v = Vr[p * n2 + i0 + r] + Vs[p * nl + c0 + q];
+                    for (int t = 0; t < nboth; ++t)
+                        v += pf[p * nt + g3 + t] * F2[t * n2 + i0 + r] * F3[t * nl + c0 + q];
+                    cfma(acc[r][q], v, x[q]);
+                    acc[r][q].x *= scale;
+                    acc[r][q].y *= scale;
+                }
+                uint32_t pos = ri.x + (uint32_t)__popc(ri.y & ((1u << c0) - 1u));
+                if (mk == 0xFu && !(pos & 1u)) {
+                    st4(a.out + pos, acc[r]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if ((mk >> q) & 1u) a.out[pos++] = acc[r][q];
+                }
+            }
+        }
+        __syncthreads();   // X, pf and the tables are free for the next units
+    }
+}
+
+// Pair pass on a dense set over outer modes (k, k+1): y += T^k x + T^{k+1} x.
+__global__ void __launch_bounds__(kDenseThreads) k_dense_pair(ApplyArgs<float> a) {
+    if (a.skip && *a.skip <= a.skip_k) return;
+    if (gated_off(a)) return;
+    if (a.cnt[CNT_ERR] & 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lattice& L = a.L;
+    const int k = a.mode, na = L.n[k], nb = L.n[k + 1], nl = L.nlast, nbp = nb | 1;
+    const uint32_t sa = L.rstride[k], sb = L.rstride[k + 1];
+    const size_t tile = (size_t)na * nb * kDenseC;
+    float2* Xb = reinterpret_cast<float2*>(smem);                         // [2][na][nb][kDenseC]
+    float* Ta = reinterpret_cast<float*>(Xb + 2 * tile);                  // [j][a] = T^k[a][j]
+    float* Tb = Ta + na * na;                                             // [b][j], row stride nbp
+    uint2* Rb = reinterpret_cast<uint2*>(((uintptr_t)(Tb + nb * nbp) + 15) & ~(uintptr_t)15);   // [3][na * nb]
+    for (int i = threadIdx.x; i < na * na; i += blockDim.x) {
+        const int j = i / na, r = i - j * na;
+        Ta[i] = a.T[(size_t)k * kMaxN * kMaxN + r * kMaxN + j];
+    }
+    for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) {
+        const int r = i / nb, j = i - r * nb;
+        Tb[r * nbp + j] = a.T[(size_t)(k + 1) * kMaxN * kMaxN + r * kMaxN + j];
+    }
+    const float scale = a.in_scale ? (float)(*a.in_scale) : 1.f;
+    const int nch = nl / kDenseC, nab = na / 4, nab_rows = na * nb;
+    const uint32_t ntiles = L.nrows / (uint32_t)(na * nb);
+    const uint64_t nunits = (uint64_t)ntiles * nch;
+    // row (t, 0, 0) and the first last-mode point of the unit's chunk
+    auto unit_base = [&](uint64_t u, int& c0) -> uint64_t {
+        const uint32_t t = (uint32_t)(u / nch);
+        c0 = (int)(u - (uint64_t)t * nch) * kDenseC;
+        const uint32_t hi = t / sb, lo = t - hi * sb;
+        return (uint64_t)hi * sa * na + lo;
+    };
+    auto fetch_rows = [&](uint64_t u, int r3) {
+        int c0;
+        const uint64_t rbase = unit_base(u, c0);
+        uint2* dst = Rb + (size_t)r3 * nab_rows;
+        for (int rowi = threadIdx.x; rowi < nab_rows; rowi += blockDim.x) {
+            const int ra = rowi / nb, rb = rowi - ra * nb;
+            cp_async8(dst + rowi, a.rowinfo + rbase + (uint64_t)ra * sa + (uint64_t)rb * sb, true);
+        }
+    };
+    auto issue = [&](uint64_t u, int buf, const uint2* R) {
+        int c0;
+        unit_base(u, c0);
+        float2* dst = Xb + (size_t)buf * tile;
+        for (int rowi = threadIdx.x; rowi < nab_rows; rowi += blockDim.x)
+            stage_row(dst + (size_t)rowi * kDenseC, a.in, R[rowi], c0, kDenseC);
+    };
+    const uint64_t G = gridDim.x;
+    if (blockIdx.x < nunits) {
+        fetch_rows(blockIdx.x, 0);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();   // also the operator tables
+        issue(blockIdx.x, 0, Rb);
+        if (blockIdx.x + G < nunits) fetch_rows(blockIdx.x + G, 1);
+        cp_async_commit();
+    }
+    int it = 0;
+    for (uint64_t u = blockIdx.x; u < nunits; u += G, ++it) {
+        cp_async_wait_all();
+        __syncthreads();   // this unit's coefficients and the next unit's rows
+        if (u + G < nunits) issue(u + G, (it + 1) & 1, Rb + (size_t)((it + 1) % 3) * nab_rows);
+        if (u + 2 * G < nunits) fetch_rows(u + 2 * G, (it + 2) % 3);
+        cp_async_commit();
+        const uint2* R = Rb + (size_t)(it % 3) * nab_rows;
+        const float2* X = Xb + (size_t)(it & 1) * tile;
+        int c0;
+        unit_base(u, c0);
+        for (int task = threadIdx.x; task < nab * nb * (kDenseC / 4); task += blockDim.x) {
+            const int cb = task % (kDenseC / 4), rem = task / (kDenseC / 4);
+            const int rb = rem % nb, a0 = (rem / nb) * 4, cq = cb * 4;
+            float2 acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] = make_float2(0.f, 0.f);
+            // mode k: acc[r][q] += T^k[a0+r][j] x[j][rb][cq+q]
+#pragma unroll 4
+            for (int j = 0; j < na; ++j) {
+                const float4 tv = *reinterpret_cast<const float4*>(Ta + j * na + a0);
+                float2 x[4];
+                ld4(X + ((size_t)j * nb + rb) * kDenseC + cq, x);
+                outer4(acc, tv, x);
+            }
+            // mode k+1: acc[r][q] += T^{k+1}[rb][j] x[a0+r][j][cq+q]
+            const float* tb = Tb + rb * nbp;
+#pragma unroll 2
+            for (int j = 0; j < nb; ++j) {
+                const float tv = tb[j];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float2 x[4];
+                    ld4(X + ((size_t)(a0 + r) * nb + j) * kDenseC + cq, x);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) cfma(acc[r][q], tv, x[q]);
+                }
+            }
+            // y += scale acc on the active points, two rows at a time with both
+            // rows' loads before their stores (the positions are distinct);
+            // 16-byte accesses for four active points that start on an even
+            // position
+            const int cc = c0 + cq;
+#pragma unroll
+            for (int r0 = 0; r0 < 4; r0 += 2) {
+                uint32_t pos0[2], mk[2];
+                float2 y[2][4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint2 ri = R[(a0 + r0 + h) * nb + rb];
+                    mk[h] = (ri.y >> cc) & 0xFu;
+                    pos0[h] = ri.x + (uint32_t)__popc(ri.y & ((1u << cc) - 1u));
+                    if (mk[h] == 0xFu && !(pos0[h] & 1u)) {
+                        ld4(a.out + pos0[h], y[h]);
+                    } else {
+                        uint32_t pp = pos0[h];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if ((mk[h] >> q) & 1u) y[h][q] = a.out[pp++];
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        y[h][q].x = fmaf(scale, acc[r0 + h][q].x, y[h][q].x);
+                        y[h][q].y = fmaf(scale, acc[r0 + h][q].y, y[h][q].y);
+                    }
+                    if (mk[h] == 0xFu && !(pos0[h] & 1u)) {
+                        st4(a.out + pos0[h], y[h]);
+                    } else {
+                        uint32_t pp = pos0[h];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if ((mk[h] >> q) & 1u) a.out[pp++] = y[h][q];
+                    }
+                }
+            }
+        }
+        __syncthreads();   // the buffer is refilled two units on
+    }
+}
+
+static size_t smem_dense_inner(const Lattice& L, int nterms) {
+    const int n2 = L.n[L.D - 2], nl = L.nlast;
+    return (size_t)2 * kDensePlanes * n2 * nl * 8 + (size_t)(n2 * n2 + nl * nl) * 4 +
+           (size_t)kDensePlanes * (n2 + nl + std::max(nterms, 1)) * 4 + (size_t)nterms * (n2 + nl) * 4 +
+           16 + (size_t)3 * kDensePlanes * n2 * 8;
+}
+
+static size_t smem_dense_pair(const Lattice& L, int k) {
+    const int na = L.n[k], nb = L.n[k + 1];
+    return (size_t)2 * na * nb * kDenseC * 8 + (size_t)(na * na + nb * (nb | 1)) * 4 + 16 +
+           (size_t)3 * na * nb * 8;
+}
+
+// The dense-tile passes take modes of at most 32 points (the row table holds
+// 32-bit patterns), with n[D-2] and the pair modes' first mode multiples of 4
+// and n[D-1] a multiple of kDenseC.
+static bool dense_ok(const Lattice& L, int nterms) {
+    if (L.D < 2 || L.nlast > 32 || L.nlast % kDenseC || L.n[L.D - 2] % 4 || L.n[L.D - 2] > 32)
+        return false;
+    return smem_dense_inner(L, nterms) <= kSmemBudget;
+}
+
 template <typename R, int W>
 static size_t smem_outer_q(int nk, int nl) {
     const int nlw = q_items_per_row(nl, W) * W;
@@ -1647,6 +2076,7 @@ template <typename R, int W>
 __global__ void __launch_bounds__(kApplyThreads) k_inner_q(ApplyArgs<R> a) {
     using V = typename Cx<R>::T;
     if (a.skip && *a.skip <= a.skip_k) return;
+    if (gated_off(a)) return;
     if (a.cnt[CNT_ERR] & 1) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ QuadMeta meta[kQWarps];
@@ -1929,8 +2359,28 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
         cmp_attr[pi] = true;
     }
     const bool compact = L.nlast <= 32;
+    // Dense-tile passes (FP32): launched beside the item-blocked kernels, whose
+    // conditions must then hold for every pass (they honour the gate); pairs
+    // of outer modes from the top, (D-4, D-3), (D-6, D-5), ...
+    bool use_dense = false;
+    bool paired[kMaxD] = {false};
+    if constexpr (std::is_same<R, float>::value) {
+        const int n2 = L.n[L.D - 2], nl = L.nlast;
+        const int nboth = s.nterms - (s.ngroup[0] + s.ngroup[1] + s.ngroup[2]);
+        use_dense = s.rowinfo && dense_ok(L, s.nterms) && !s.vgrid32 && n2 <= 32 &&
+                    smem_inner_q<R, kQWInner>(n2, nl, nboth) <= kSmemBudget;
+        for (int k = 0; k + 2 < L.D && use_dense; ++k)
+            use_dense = L.n[k] <= 32 && smem_outer_q<R, kQWOuter>(L.n[k], nl) <= kSmemBudget;
+        if (use_dense)
+            for (int k = L.D - 4; k >= 0; k -= 2)
+                if (L.n[k] % 4 == 0 && smem_dense_pair(L, k) <= kSmemBudget) paired[k] = paired[k + 1] = true;
+    }
+    const int hint = use_dense ? s.dense_hint : 0;
+    const bool run_sparse = hint != 1, run_dense = use_dense && hint != 0;
+    const int gate = hint < 0 ? 1 : 0;   // both paths launched: the device picks
     // inner pass
-    {
+    a.full_gate = -gate;
+    if (run_sparse) {
         a.units = s.planes;
         a.units_cap = s.rows_cap;
         a.nunits = s.cnt + CNT_PLANES;
@@ -1985,8 +2435,38 @@ static pq_status launch_all(const State& s, const void* in, void* out, const dou
             PQ_CHECK_LAUNCH();
         }
     }
+    if constexpr (std::is_same<R, float>::value) {
+        if (run_dense) {
+            static bool d_attr = false;
+            if (!d_attr) {
+                PQ_CUDA_TRY(cudaFuncSetAttribute(k_dense_inner, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kSmemBudget));
+                PQ_CUDA_TRY(cudaFuncSetAttribute(k_dense_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kSmemBudget));
+                d_attr = true;
+            }
+            ApplyArgs<float> ad = a;
+            ad.full_gate = gate;
+            const size_t smi = smem_dense_inner(L, s.nterms);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_inner, kDenseThreads, smi);
+            k_dense_inner<<<G * (per_sm > 0 ? per_sm : 1), kDenseThreads, smi, st>>>(ad);
+            PQ_CHECK_LAUNCH();
+            for (int k = L.D - 4; k >= 0; k -= 2) {
+                if (!paired[k]) continue;
+                ad.mode = k;
+                const size_t smp = smem_dense_pair(L, k);
+                per_sm = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_pair, kDenseThreads, smp);
+                k_dense_pair<<<G * (per_sm > 0 ? per_sm : 1), kDenseThreads, smp, st>>>(ad);
+                PQ_CHECK_LAUNCH();
+            }
+        }
+    }
     for (int k = L.D - 3; k >= 0; --k) {
+        if (paired[k] && !run_sparse) continue;   // the dense pair pass covers it
         a.mode = k;
+        a.full_gate = paired[k] ? -gate : 0;
         a.units = s.leaders + (size_t)k * s.rows_cap;
         a.units_cap = s.rows_cap;
         a.nunits = s.cnt + CNT_LEAD0 + k;

@@ -55,6 +55,7 @@ static void free_state(State* s) {
     // device finish with it first (cudaFree synchronises by itself)
     if (g_user_free) cudaDeviceSynchronize();
     if (s->rowinfo) dev_free(s->rowinfo, 0, false);
+    if (s->h_na) cudaFreeHost(s->h_na);
     {
         void* pv[] = {s->pvbB64, s->pvbB32, s->pvbBh64, s->pvbBh32, s->pvbS64, s->pvbS32,
                       s->pvbSi64, s->pvbSi32, s->pvbT64, s->pvbT32, s->pvb_grid, s->pvb_vec,

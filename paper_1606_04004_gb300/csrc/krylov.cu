@@ -98,9 +98,11 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(const typename Cx<R>::T* 
     block_partials<1>(vals, partials);
 }
 
-// beta_0 = ||psi||; sigma_0 = 1/beta_0; reset the step's scalars.
+// beta_0 = ||psi||; sigma_0 = 1/beta_0; reset the step's scalars.  track
+// (FP32-mix): the target norm of this step's output follows the adaption
+// since the previous output (see k_renorm_factor).
 __global__ void k_start_step(const double* partials, int G, KrylovScalars* ks, int K,
-                             int64_t* err) {
+                             int64_t* err, int track = 0) {
     __shared__ double tot[1];
     sum_partials(partials, G, 1, tot);
     __syncthreads();
@@ -116,6 +118,12 @@ __global__ void k_start_step(const double* partials, int G, KrylovScalars* ks, i
         } else {
             ks->beta0 = sqrt(n2);
             ks->sigma[0] = 1.0 / ks->beta0;
+        }
+        if (track) {
+            if (ks->rn_target > 0.0 && ks->rn_last > 0.0 && ks->beta0 > 0.0)
+                ks->rn_target *= ks->beta0 / ks->rn_last;
+            else
+                ks->rn_target = ks->beta0;
         }
     }
 }
@@ -415,7 +423,9 @@ __global__ void __launch_bounds__(32) k_tridiag_exp(KrylovScalars* ks, double dt
     const bool ok = tridiag_exp_lanes(ks, n, dt, J, vr, vi);
     if (!ok && r == 0) *err |= 2;
     if (r < n) {
-        const double f = ok ? ks->beta0 * ks->sigma[r] : 0.0;
+        // ks->renorm: the FP32-mix norm correction of the previous step (0 or 1: none)
+        const double g = ks->renorm > 0.0 ? ks->renorm : 1.0;
+        const double f = ok ? ks->beta0 * ks->sigma[r] * g : 0.0;
         ks->coef[2 * r] = vr * f;
         ks->coef[2 * r + 1] = vi * f;
     }
@@ -453,6 +463,29 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(void* psi, const void* 
             ay += cr * v.y + ci * v.x;
         }
         ((V*)psi)[p] = cmake<R>(ax, ay);
+    }
+}
+
+// FP32-mix: norm keeping of the SIL step.  In exact arithmetic the step keeps
+// the norm (exp(-i T dt) is unitary and the Krylov basis orthonormal), so the
+// norm changes only where the adaption removes coefficients.  With FP32
+// coefficients each step's output norm is off by a few 1e-8, which adds up
+// over hundreds of steps; a scale that small is below one FP32 unit in the
+// last place near 1.  So the run carries in FP64 the norm it should have: the
+// target output norm of the step, which follows the adaption (at the next
+// step's start, target *= ||psi after prune|| / ||step output||), and the
+// factor target / ||step output|| is folded into the next step's
+// combination coefficients.  Each output is then off by one step's rounding,
+// not by the sum of all of them.
+__global__ void k_renorm_factor(const double* partials, int G, KrylovScalars* ks) {
+    __shared__ double tot[1];
+    sum_partials(partials, G, 1, tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double n = sqrt(tot[0]);
+        const bool ok = ks->keff > 0 && n > 0.0 && isfinite(n) && ks->rn_target > 0.0;
+        ks->renorm = ok ? ks->rn_target / n : 1.0;
+        ks->rn_last = ok ? n : 0.0;
     }
 }
 
@@ -557,7 +590,7 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
     const int K = d.K;
     k_norm2<R><<<G, kRedThreads, 0, st>>>((const V*)s.psi, s.cnt + CNT_NA, (int64_t)cap, s.red_tmp);
     PQ_CHECK_LAUNCH();
-    k_start_step<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks, K, s.cnt + CNT_ERR);
+    k_start_step<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks, K, s.cnt + CNT_ERR, sizeof(R) == 4 ? 1 : 0);
     PQ_CHECK_LAUNCH();
     pq_status rc;
     for (int k = 0; k < K; ++k) {
@@ -606,6 +639,12 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
     PQ_CHECK_LAUNCH();
     k_combine<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, cap, s.cnt + CNT_NA, s.ks);
     PQ_CHECK_LAUNCH();
+    if (sizeof(R) == 4) {   // FP32-mix: the next step's norm correction
+        k_norm2<R><<<G, kRedThreads, 0, st>>>((const V*)s.psi, s.cnt + CNT_NA, (int64_t)cap, s.red_tmp);
+        PQ_CHECK_LAUNCH();
+        k_renorm_factor<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks);
+        PQ_CHECK_LAUNCH();
+    }
     return PQ_OK;
 }
 
@@ -763,9 +802,28 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
         return PQ_ENOMEM;
     }
     PQ_CUDA_TRY(cudaMemsetAsync(recs, 0, (size_t)(nsteps + 1) * 8 * sizeof(double), st));
+    // FP32 H.psi path hint: the set size now, then the size after step n - 2
+    // read back without blocking (two pinned slots and events)
+    cudaEvent_t hev[2] = {nullptr, nullptr};
+    const bool hinted = s.prec != PQ_FP64;
+    if (hinted) {
+        if (!s.h_na && cudaMallocHost((void**)&s.h_na, 2 * sizeof(int64_t)) != cudaSuccess) {
+            s.h_na = nullptr;
+            set_error("cudaMallocHost failed");
+            dev_free(recs, st, true);
+            return PQ_ENOMEM;
+        }
+        PQ_CUDA_TRY(cudaMemcpyAsync(s.h_na, s.cnt + CNT_NA, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PQ_CUDA_TRY(cudaStreamSynchronize(st));
+        s.dense_hint = 2 * s.h_na[0] >= (int64_t)s.lat.nfull ? 1 : 0;
+        PQ_CUDA_TRY(cudaEventCreateWithFlags(&hev[0], cudaEventDisableTiming));
+        PQ_CUDA_TRY(cudaEventCreateWithFlags(&hev[1], cudaEventDisableTiming));
+    }
     // Slot 0 receives E of the record already on the host (alpha_0 of step 1).
     pq_status rc = PQ_OK;
     for (int n = 0; n < nsteps && rc == PQ_OK; ++n) {
+        if (hinted && n >= 2 && cudaEventQuery(hev[n & 1]) == cudaSuccess)
+            s.dense_hint = 2 * s.h_na[n & 1] >= (int64_t)s.lat.nfull ? 1 : 0;
         double* prevE = recs + (size_t)n * 8 + 4;
         if (rk4)
             rc = s.prec == PQ_FP64 ? rk4_step<double>(s, d, prevE, st) : rk4_step<float>(s, d, prevE, st);
@@ -774,6 +832,10 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
         if (rc) break;
         rc = prune_launch(s, d.theta, d.radius, d.rel_excl, st);
         if (rc) break;
+        if (hinted) {
+            cudaMemcpyAsync(s.h_na + (n & 1), s.cnt + CNT_NA, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+            cudaEventRecord(hev[n & 1], st);
+        }
         s.t += d.dt;
         rc = observe_rec(s, d.theta, recs + (size_t)(n + 1) * 8, st);
     }
@@ -784,6 +846,9 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
                                      cudaMemcpyDeviceToHost, st);
     cudaError_t e3 = cudaStreamSynchronize(st);
     dev_free(recs, st, true);
+    for (cudaEvent_t e : hev)
+        if (e) cudaEventDestroy(e);
+    if (hinted && e3 == cudaSuccess) s.dense_hint = 2 * s.h_cnt[CNT_NA] >= (int64_t)s.lat.nfull ? 1 : 0;
     if (rc) return rc;
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
         set_error("propagate: %s", cudaGetErrorString(e3 != cudaSuccess ? e3 : (e1 ? e1 : e2)));

@@ -7,6 +7,7 @@
 #include <stdio.h>
 
 #include <cmath>
+#include <cstddef>
 
 #include "device_util.cuh"
 
@@ -511,6 +512,10 @@ __global__ void k_set_bits(const uint32_t* __restrict__ keys, int64_t n, uint64_
 // (d_keys may alias nothing of the state).
 pq_status load_set(State& s, const uint32_t* d_keys, int64_t n, cudaStream_t st, bool remap) {
     const Lattice& L = s.lat;
+    s.dense_hint = 2 * n >= (int64_t)L.nfull ? 1 : 0;
+    if (!remap && s.ks)   // new coefficients: no pending FP32-mix norm correction
+        PQ_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(s.ks) + offsetof(KrylovScalars, renorm), 0,
+                                    3 * sizeof(double), st));
     if (!remap) PQ_CUDA_TRY(cudaMemsetAsync(s.cnt + CNT_ERR, 0, sizeof(int64_t), st));
     PQ_CUDA_TRY(cudaMemsetAsync(s.bits_alt, 0, (size_t)L.nwords * 8, st));
     if (n > 0) {

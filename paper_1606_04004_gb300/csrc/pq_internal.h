@@ -156,6 +156,9 @@ struct KrylovScalars {
     double dots[2 * (kMaxK + 1)]; // <V_i, W> (re, im) of the current step
     double hnorm2;                // ||W||^2 before orthogonalisation
     double coef[2 * kMaxK];       // final combination coefficients (re, im)
+    double renorm;                // FP32-mix: norm correction for the next step (0: none)
+    double rn_target;             // FP32-mix: norm the step's output should have (0: unset)
+    double rn_last;               // FP32-mix: norm of the last step's output
     int keff;                     // Krylov dimension reached (breakdown)
     int pad;
     double obs[8];                // C re, C im, norm2, wasted (as double)
@@ -183,6 +186,12 @@ struct State {
                                    // active pattern); (0, 0) for empty rows.  Only when
                                    // n[D-1] <= 32 and the lattice has at most 2^28 rows.
     size_t rows_cap = 0;
+    // FP32 H.psi path hint: 1 = dense-tile passes (at least half the lattice
+    // active), 0 = item-blocked passes, -1 = unknown (both launched, the
+    // device-side set size picks).  Either path is correct for any set; a
+    // stale hint costs speed only.
+    int dense_hint = -1;
+    int64_t* h_na = nullptr;       // pinned: two lagged copies of the active-set size
     int64_t* cnt = nullptr;        // counters (CNT_*)
     uint32_t* scan_tmp = nullptr;  // block sums of the scans
     double* red_tmp = nullptr;     // block partials of the reductions

@@ -144,6 +144,56 @@ def test_apply_hh6d_initial_state_sampled():
     assert np.all(err <= 4e-6 * scale + 1e-30), (err / scale).max()
 
 
+# Sets covering at least half the lattice: in FP32 these take the dense-tile
+# passes (batched contractions over zero-filled tiles; the set size on the
+# device selects them): inner + two pairs (6D), inner + pair (4D), inner +
+# pair + single mode (5D), pair modes that are not multiples of 4 (no pair
+# pass), inner + single mode (3D); full lattices and lattices with holes.
+DENSE = [(4, 8, 4, 8, 8, 8), (8, 12, 16, 24), (8, 4, 8, 12, 16), (3, 8, 5, 8, 8, 8), (24, 24, 8)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("frac", [1.0, 0.9, 0.55])
+@pytest.mark.parametrize("dims", DENSE)
+def test_apply_dense_sets(dims, frac, prec):
+    if frac == 1.0:
+        A = np.arange(int(np.prod(dims)), dtype=np.int64)
+    else:
+        A = W.random_active_set(dims, frac, seed=len(dims) + int(100 * frac))
+    _run(dims, A, 13, prec, nterms=5)
+
+
+def test_apply_hh6d_full_lattice_sampled():
+    """The 6D Henon-Heiles Hamiltonian on the whole 24^6 lattice (the set the
+    propagation reaches after about 100 steps), FP32, in the launch
+    configuration the benchmark's late window times; sampled outputs against
+    the oracle one by one."""
+    import torch
+    from oracle import pruned, propagate
+    pq = lib()
+    cfg = W.HH6D
+    b = pq.build_model(cfg)
+    nfull = 24 ** 6
+    A = np.arange(nfull, dtype=np.int64)
+    psi = W.random_psi(nfull, 21).astype(np.complex64)
+    s = state_with(b, A, psi, pq.FP32MIX)
+    x = torch.from_numpy(psi).to("cuda")
+    y = torch.empty_like(x)
+    s.apply_H(x, y)
+    torch.cuda.synchronize()
+    prob = propagate.problem_from_config(cfg)
+    rng = np.random.default_rng(1)
+    pos = np.unique(np.concatenate([rng.integers(0, nfull, 4000), [0, nfull - 1]]))
+    got = y[torch.from_numpy(pos).to("cuda")].cpu().numpy().astype(np.complex128)
+    vd = prob.vdiag(A[pos])
+    p64 = psi.astype(np.complex128)
+    ref = pruned.apply_H_at(A, p64, prob.dims, prob.Ts, vd, pos)
+    scale = pruned.apply_H_at(A, np.abs(p64), prob.dims, [np.abs(T) for T in prob.Ts],
+                              np.abs(vd), pos).real
+    err = np.abs(got - ref)
+    assert np.all(err <= 4e-6 * scale + 1e-30), (err / scale).max()
+
+
 # Lattices with a mode longer than 64 (FGH DVR, point-parallel pass): up to
 # 246 terms per output, so the FP32 bound is taken at 1e-5 of the rounding scale.
 BIG = [((165, 81), 0.3), ((70, 9), 0.5), ((100, 3, 5), 0.4), ((9, 130), 0.5), ((5, 4, 66), 0.6)]

@@ -9,12 +9,7 @@ sample of 4096 members of A within 1e-10 ||psi|| (the sampled relative L2
 error, scaled to the whole set, also <= 1e-10).  FP32-mix path: |dC(t)| <=
 1e-5 and |d||psi||^2| <= 1e-6 at every step; the sets may differ where FP32
 moves a coefficient across the threshold, so they are compared through these
-observables only.
-
-Known miss: the FP32-mix projected-Weylet run of the 3D Morse workload loses
-norm at about 2.7e-8 per step against the FP64 run (1.06e-5 after 400 steps,
-with the tensor-core passes and with the FP32 SIMT passes alike) while its
-C(t) stays within 1e-5; its norm check is an expected failure."""
+observables only."""
 import hashlib
 import json
 import os
@@ -102,11 +97,7 @@ def test_series_fp32mix_C(name):
     assert np.max(np.abs(o["C"] - _series(rec, "C"))) <= 1e-5
 
 
-@pytest.mark.parametrize("name", [
-    "hh4d", "hh6d",
-    pytest.param("morse3d_pw", marks=pytest.mark.xfail(
-        strict=True, reason="FP32-mix pW norm drift 1.06e-5 after 400 steps")),
-    "morse3d_pvb"])
+@pytest.mark.parametrize("name", ["hh4d", "hh6d", "morse3d_pw", "morse3d_pvb"])
 def test_series_fp32mix_norm(name):
     rec, o = _fp32_run(name)
     assert np.max(np.abs(o["norm2"] - _series(rec, "norm2"))) <= 1e-6
