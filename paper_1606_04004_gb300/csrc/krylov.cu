@@ -63,12 +63,25 @@ __device__ __forceinline__ void block_partials(const double (&vals)[WIDTH], doub
 }
 
 // Column sums of partials[G][width] -> out[width]: warp j sums column j
-// with a fixed lane-strided order and a fixed butterfly (deterministic).
+// with a fixed lane-strided order (four interleaved accumulators per lane, so
+// that four loads are in flight) and a fixed butterfly (deterministic).
 __device__ void sum_partials(const double* partials, int G, int width, double* out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = wid; j < width; j += nw) {
-        double acc = 0.0;
-        for (int b = lane; b < G; b += 32) acc += partials[(size_t)b * width + j];
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int b = lane;
+        for (; b + 96 < G; b += 128) {
+            const double x0 = partials[(size_t)b * width + j];
+            const double x1 = partials[(size_t)(b + 32) * width + j];
+            const double x2 = partials[(size_t)(b + 64) * width + j];
+            const double x3 = partials[(size_t)(b + 96) * width + j];
+            a0 += x0;
+            a1 += x1;
+            a2 += x2;
+            a3 += x3;
+        }
+        for (; b < G; b += 32) a0 += partials[(size_t)b * width + j];
+        double acc = (a0 + a1) + (a2 + a3);
         acc = warp_sum(acc);
         if (lane == 0) out[j] = acc;
     }
