@@ -195,9 +195,13 @@ pq_status pq_state_psi_device(const pq_state* state, void** psi);
  * which equals P_A H P_A in for a DVR Hamiltonian (diagonal V, Sec. 2.1).
  * in, out: device arrays of n_active complex values in A's order, of the type
  * `precision` selects (it may differ from the state's own precision); they
- * must not overlap.  No allocation.  Asynchronous on `stream`.  */
+ * must not overlap.  out_vHv (nullable): device address of two doubles that
+ * receive Re and Im of <in, out> = sum_I conj(in_I) out_I (the Lanczos
+ * alpha of a normalised `in`, Sec. 3.1), summed in FP64 in a fixed order; it
+ * uses the state's reduction scratch, so calls on one state must not overlap
+ * on the device.  No allocation.  Asynchronous on `stream`.  */
 pq_status pq_apply_H(const pq_state* state, const void* in, void* out, int precision,
-                     void* stream);
+                     double* out_vHv, void* stream);
 
 /* Same operator with host buffers: copies `in` (host, n_active complex of
  * `precision`) to the device, applies H, copies the result to `out` (host)

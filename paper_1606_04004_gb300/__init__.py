@@ -96,7 +96,7 @@ _SIGS = {
     "pq_state_size": [_vp, C.POINTER(C.c_int64)],
     "pq_state_read": [_vp, _vp, _vp],
     "pq_state_psi_device": [_vp, C.POINTER(_vp)],
-    "pq_apply_H": [_vp, _vp, _vp, C.c_int, _vp],
+    "pq_apply_H": [_vp, _vp, _vp, C.c_int, _vp, _vp],
     "pq_apply_H_host": [_vp, _vp, _vp, C.c_int, _vp],
     "pq_prune": [_vp, C.c_double, C.c_int, C.c_double, _vp],
     "pq_set_potential_grid": [_vp, _vp, C.c_int64],
@@ -319,14 +319,15 @@ class State:
         _check(_lib.pq_state_psi_device(self._h, C.byref(p)))
         return int(p.value or 0)
 
-    def apply_H(self, x, out, precision=None, stream=None):
-        """out = P_A H P_A x for torch CUDA tensors (complex64 or complex128)."""
+    def apply_H(self, x, out, precision=None, stream=None, vhv=None):
+        """out = P_A H P_A x for torch CUDA tensors (complex64 or complex128);
+        vhv (optional float64 CUDA tensor of 2) receives Re, Im of <x, out>."""
         import torch
         prec = precision if precision is not None else (FP64 if x.dtype == torch.complex128 else FP32MIX)
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         _check(_lib.pq_apply_H(self._h, _vp(x.data_ptr()), _vp(out.data_ptr()), int(prec),
-                               _vp(stream)))
+                               _vp(vhv.data_ptr()) if vhv is not None else None, _vp(stream)))
         return out
 
     def apply_H_host(self, x: np.ndarray, precision=None) -> np.ndarray:

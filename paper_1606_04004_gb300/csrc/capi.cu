@@ -858,8 +858,47 @@ PQ_API pq_status pq_state_psi_device(const pq_state* state, void** psi) {
     return PQ_OK;
 }
 
+// <in, out> over the active set: per-block partials (Re, Im; FP64 sums of the
+// per-element products), then one block adds them in block order.
+constexpr int kVhvThreads = 256;
+template <typename V>
+__global__ void __launch_bounds__(kVhvThreads) k_vhv_partials(const V* __restrict__ x,
+                                                              const V* __restrict__ y,
+                                                              const int64_t* na, int64_t cap,
+                                                              double* partials) {
+    const int64_t n = min(*na, cap);
+    double re = 0.0, im = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const V a = x[p], b = y[p];
+        re += (double)a.x * b.x + (double)a.y * b.y;   // conj(a) b
+        im += (double)a.x * b.y - (double)a.y * b.x;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    __shared__ double sh[2][kVhvThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = re;
+        sh[1][threadIdx.x >> 5] = im;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int w = 0; w < kVhvThreads / 32; ++w) t += sh[threadIdx.x][w];
+        partials[2 * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+__global__ void k_vhv_sum(const double* partials, int G, double* out) {
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int b = 0; b < G; ++b) t += partials[2 * b + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+}
+
 PQ_API pq_status pq_apply_H(const pq_state* state, const void* in, void* out, int precision,
-                            void* stream) {
+                            double* out_vHv, void* stream) {
     clear_error();
     const State* s = reinterpret_cast<const State*>(state);
     if (!s || !in || !out) {
@@ -870,13 +909,26 @@ PQ_API pq_status pq_apply_H(const pq_state* state, const void* in, void* out, in
         set_error("in and out must not overlap");
         return PQ_EINVAL;
     }
+    const cudaStream_t st = (cudaStream_t)stream;
+    pq_status rc = apply_H_launch(*s, in, out, precision, nullptr, nullptr, 0, st);
+    if (rc) return rc;
+    if (out_vHv) {
+        const int G = grid_size();
+        if (precision == PQ_FP64)
+            k_vhv_partials<double2><<<G, kVhvThreads, 0, st>>>((const double2*)in, (const double2*)out,
+                                                               s->cnt + CNT_NA, (int64_t)s->cap, s->red_tmp);
+        else
+            k_vhv_partials<float2><<<G, kVhvThreads, 0, st>>>((const float2*)in, (const float2*)out,
+                                                              s->cnt + CNT_NA, (int64_t)s->cap, s->red_tmp);
+        PQ_CHECK_LAUNCH();
+        k_vhv_sum<<<1, 32, 0, st>>>(s->red_tmp, G, out_vHv);
+        PQ_CHECK_LAUNCH();
+    }
 #ifdef PQ_BOUNDS_CHECK
     // self-checking build: report a recorded out-of-range access at once
-    pq_status rc = apply_H_launch(*s, in, out, precision, nullptr, nullptr, 0, (cudaStream_t)stream);
-    if (rc) return rc;
-    return check_capacity(const_cast<State&>(*s), (cudaStream_t)stream);
+    return check_capacity(const_cast<State&>(*s), st);
 #else
-    return apply_H_launch(*s, in, out, precision, nullptr, nullptr, 0, (cudaStream_t)stream);
+    return PQ_OK;
 #endif
 }
 

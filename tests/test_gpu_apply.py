@@ -31,7 +31,8 @@ def _run(dims, A, seed, prec, nterms=3, problem=ho_problem, tol=None):
     tdt = torch.complex128 if prec == pq.FP64 else torch.complex64
     x = torch.from_numpy(psi).to("cuda")
     y = torch.empty_like(x)
-    s.apply_H(x, y)
+    vhv = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    s.apply_H(x, y, vhv=vhv)
     torch.cuda.synchronize()
     got = y.cpu().numpy().astype(np.complex128)
     vd = vdiag_of(pot, A, dims)
@@ -40,6 +41,13 @@ def _run(dims, A, seed, prec, nterms=3, problem=ho_problem, tol=None):
     err = np.abs(got - ref)
     tl = TOL[prec] if tol is None else tol[prec]
     assert np.all(err <= tl * bound + 1e-300), (err / np.maximum(bound, 1e-300)).max()
+    # <x, Hx> of the same call: the FP64 sum of the products of what was
+    # written, and the oracle's value within the elementwise bound
+    p64 = psi.astype(np.complex128)
+    v = complex(*vhv.cpu().numpy())
+    scale = float(np.sum(np.abs(p64) * np.abs(got))) + 1e-300
+    assert abs(v - np.vdot(p64, got)) <= 1e-12 * scale
+    assert abs(v - np.vdot(p64, ref)) <= tl * float(np.sum(np.abs(p64) * bound)) + 1e-12 * scale
     # host-buffer entry point gives the same numbers
     got_h = s.apply_H_host(psi)
     np.testing.assert_array_equal(got_h, y.cpu().numpy())
