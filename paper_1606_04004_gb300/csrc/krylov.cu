@@ -458,14 +458,17 @@ __global__ void __launch_bounds__(32) k_sil_errcheck(KrylovScalars* ks, int k, d
 }
 
 // psi <- sum_{j < keff} coef_j V_j  (V_0 is psi itself: read before write).
+// partials (nullable): block partials of ||psi||^2 of the result.
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) k_combine(void* psi, const void* Vb, size_t cap,
                                                           const int64_t* na,
-                                                          const KrylovScalars* ks) {
+                                                          const KrylovScalars* ks, double* partials) {
     using V = typename Cx<R>::T;
     const int n_k = ks->keff;
-    if (n_k <= 0) return;
+    if (n_k <= 0) return;   // uniform; the norm keeping then ignores the partials
     const int64_t n = min(*na, (int64_t)cap);
+    Acc<R> an;
+    an.init();
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         R ax = 0, ay = 0;
@@ -476,6 +479,11 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(void* psi, const void* 
             ay += cr * v.y + ci * v.x;
         }
         ((V*)psi)[p] = cmake<R>(ax, ay);
+        an.add(ax * ax + ay * ay);
+    }
+    if (partials) {
+        const double vals[1] = {an.value()};
+        block_partials<1>(vals, partials);
     }
 }
 
@@ -650,11 +658,12 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
     }
     k_tridiag_exp<<<1, 32, 0, st>>>(s.ks, d.dt, s.cnt + CNT_ERR);
     PQ_CHECK_LAUNCH();
-    k_combine<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, cap, s.cnt + CNT_NA, s.ks);
+    // FP32-mix: the combination also sums the output's norm for the next step's
+    // norm correction
+    k_combine<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, cap, s.cnt + CNT_NA, s.ks,
+                                            sizeof(R) == 4 ? s.red_tmp : nullptr);
     PQ_CHECK_LAUNCH();
-    if (sizeof(R) == 4) {   // FP32-mix: the next step's norm correction
-        k_norm2<R><<<G, kRedThreads, 0, st>>>((const V*)s.psi, s.cnt + CNT_NA, (int64_t)cap, s.red_tmp);
-        PQ_CHECK_LAUNCH();
+    if (sizeof(R) == 4) {
         k_renorm_factor<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks);
         PQ_CHECK_LAUNCH();
     }
@@ -808,29 +817,42 @@ pq_status propagate_impl(State& s, const pq_prop_desc& d, int nsteps, cudaStream
     erc = ensure_krylov(s, rk4 ? std::max(d.K, 3) : d.K);
     if (erc) return erc;
     if (nsteps == 0) return PQ_OK;
-    double* recs = nullptr;
-    recs = (double*)dev_alloc((size_t)(nsteps + 1) * 8 * sizeof(double), st, true);
-    if (!recs) {
-        set_error("device allocation of the step records failed");
-        return PQ_ENOMEM;
-    }
-    PQ_CUDA_TRY(cudaMemsetAsync(recs, 0, (size_t)(nsteps + 1) * 8 * sizeof(double), st));
     // FP32 H.psi path hint: the set size now, then the size after step n - 2
-    // read back without blocking (two pinned slots and events)
+    // read back without blocking (two pinned slots and events).  The hint only
+    // picks between two correct paths, so without the events it stays as set.
     cudaEvent_t hev[2] = {nullptr, nullptr};
-    const bool hinted = s.prec != PQ_FP64;
+    bool hinted = s.prec != PQ_FP64;
     if (hinted) {
         if (!s.h_na && cudaMallocHost((void**)&s.h_na, 2 * sizeof(int64_t)) != cudaSuccess) {
             s.h_na = nullptr;
             set_error("cudaMallocHost failed");
-            dev_free(recs, st, true);
             return PQ_ENOMEM;
         }
         PQ_CUDA_TRY(cudaMemcpyAsync(s.h_na, s.cnt + CNT_NA, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         PQ_CUDA_TRY(cudaStreamSynchronize(st));
         s.dense_hint = 2 * s.h_na[0] >= (int64_t)s.lat.nfull ? 1 : 0;
-        PQ_CUDA_TRY(cudaEventCreateWithFlags(&hev[0], cudaEventDisableTiming));
-        PQ_CUDA_TRY(cudaEventCreateWithFlags(&hev[1], cudaEventDisableTiming));
+        if (cudaEventCreateWithFlags(&hev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&hev[1], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            for (cudaEvent_t& e : hev)
+                if (e) cudaEventDestroy(e), e = nullptr;
+            hinted = false;
+        }
+    }
+    double* recs = nullptr;
+    recs = (double*)dev_alloc((size_t)(nsteps + 1) * 8 * sizeof(double), st, true);
+    if (!recs) {
+        for (cudaEvent_t e : hev)
+            if (e) cudaEventDestroy(e);
+        set_error("device allocation of the step records failed");
+        return PQ_ENOMEM;
+    }
+    if (cudaMemsetAsync(recs, 0, (size_t)(nsteps + 1) * 8 * sizeof(double), st) != cudaSuccess) {
+        for (cudaEvent_t e : hev)
+            if (e) cudaEventDestroy(e);
+        dev_free(recs, st, true);
+        set_error("clearing the step records failed");
+        return PQ_ECUDA;
     }
     // Slot 0 receives E of the record already on the host (alpha_0 of step 1).
     pq_status rc = PQ_OK;
