@@ -314,7 +314,7 @@ def run_ours(args, cfg):
     sptr = stream.cuda_stream
     K, dt, th = cfg["K"], cfg["dt"], cfg["theta"]
     # warm-up steps (untimed)
-    s.propagate(K, dt, th, args.warmup, stream=sptr)
+    s.propagate(K, dt, th, args.warmup, stream=sptr, reorth=args.reorth)
     n_before = len(s.observables()["n_active"])
     dims = (cfg["n"],) * cfg["D"]
     fpc_first = fibre_flops_per_coef(s.read()[0], dims) if prec == pq.FP32MIX else None
@@ -326,7 +326,7 @@ def run_ours(args, cfg):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         e0.record(stream)
-        s.propagate(K, dt, th, args.steps, stream=sptr)
+        s.propagate(K, dt, th, args.steps, stream=sptr, reorth=args.reorth)
         e1.record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -395,14 +395,14 @@ def run_ours(args, cfg):
         done = len(s.observables()["n_active"]) - 1
         if args.late_start > done:
             s.set_timing(False)
-            s.propagate(K, dt, th, args.late_start - done, stream=sptr)
+            s.propagate(K, dt, th, args.late_start - done, stream=sptr, reorth=args.reorth)
         n0 = len(s.observables()["n_active"])
         s.set_timing(True)
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk_late:
             g0.record(stream)
-            s.propagate(K, dt, th, args.steps, stream=sptr)
+            s.propagate(K, dt, th, args.steps, stream=sptr, reorth=args.reorth)
             g1.record(stream)
             torch.cuda.synchronize()
         ms_late = g0.elapsed_time(g1)
@@ -427,7 +427,9 @@ def run_ours(args, cfg):
         "data": "synthetic",
         "config": {"workload": f"{cfg['name']}: {cfg['D']}D Henon-Heiles chain, HO-DVR "
                                f"{cfg['n']}^{cfg['D']}, theta {cfg['theta']}, SIL K={K}, dt={dt}",
-                   "precision": args.precision, "n_active_first": int(na[n_before - 1]),
+                   "precision": args.precision,
+                   "lanczos": "three-term recurrence" if args.reorth == 0 else "full re-orthogonalisation",
+                   "n_active_first": int(na[n_before - 1]),
                    "n_active_last": int(na[-1]), "parallelism": f"replicas{ws}",
                    "l2": "working set larger than L2 (Krylov space of 10 vectors)"},
         "gpu_launches": int(launches),
@@ -446,12 +448,12 @@ def run_ours(args, cfg):
         # the same steps on the plain FP64 GPU path, from the same initial state
         s64 = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP64,
                        capacity=cap)
-        s64.propagate(K, dt, th, args.warmup, stream=sptr)
+        s64.propagate(K, dt, th, args.warmup, stream=sptr, reorth=args.reorth)
         s64.set_timing(True)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        s64.propagate(K, dt, th, args.steps, stream=sptr)
+        s64.propagate(K, dt, th, args.steps, stream=sptr, reorth=args.reorth)
         f1.record(stream)
         torch.cuda.synchronize()
         o64 = s64.observables()
@@ -728,6 +730,9 @@ def main():
     ap.add_argument("--mode", default="step", choices=["step", "apply", "dwell", "snapshot", "peaks"])
     ap.add_argument("--radius", type=float, default=11.2)
     ap.add_argument("--lattice", type=int, default=0)
+    # Lanczos orthogonalisation of the timed runs: 0 = three-term recurrence
+    # (each vector against the previous two), 1 = against all earlier vectors
+    ap.add_argument("--reorth", type=int, default=0)
     ap.add_argument("--late-start", type=int, default=100)   # step the late window starts at (0: none)   # --mode apply: points per mode (0: the workload's)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--snapshots", default="0,20,50,100")   # steps of --mode snapshot
