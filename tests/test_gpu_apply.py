@@ -171,6 +171,33 @@ def test_apply_dense_sets(dims, frac, prec):
     _run(dims, A, 13, prec, nterms=5)
 
 
+@pytest.mark.parametrize("dims", [(8, 12, 16, 24), (4, 8, 4, 8, 8, 8)])
+def test_apply_dense_set_from_packet(dims):
+    """A state whose active set comes from its packet (no host-side set
+    size: both H.psi paths are launched and the device-side size selects),
+    with a packet wide enough that the set covers more than half the lattice:
+    FP32 H.psi against the oracle on that set."""
+    import torch
+    from oracle import pruned
+    pq = lib()
+    b, Ts, pot = ho_problem(dims, 17, 4)
+    D = len(dims)
+    s = pq.State(b, [0.0] * D, [0.0] * D, [4.0] * D, 1e-9, precision=pq.FP32MIX)
+    A, psi = s.read()
+    assert 2 * len(A) >= int(np.prod(dims))
+    x = torch.from_numpy(psi).to("cuda")
+    y = torch.empty_like(x)
+    s.apply_H(x, y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.complex128)
+    vd = vdiag_of(pot, A, dims)
+    p64 = psi.astype(np.complex128)
+    ref = pruned.apply_H(A, p64, dims, Ts, vd)
+    bound = rel_bound(Ts, A, p64, dims, vd)
+    err = np.abs(got - ref)
+    assert np.all(err <= TOL[1] * bound + 1e-300), (err / np.maximum(bound, 1e-300)).max()
+
+
 def test_apply_hh6d_full_lattice_sampled():
     """The 6D Henon-Heiles Hamiltonian on the whole 24^6 lattice (the set the
     propagation reaches after about 100 steps), FP32, in the launch
