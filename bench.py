@@ -703,7 +703,10 @@ def run_dwell(args):
     plan = [p for p in plan if p[1] in wanted]
     for cfg, basis, rule, name in plan:
         prec = pq.FP32MIX if (basis == "pvb" and args.dwell_pvb_fp32) else pq.FP64
-        for theta in (thetas if basis != "pvb" else (3e-2, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6)):
+        th_list = thetas if basis != "pvb" else (3e-2, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6)
+        if args.dwell_thetas:
+            th_list = tuple(float(v) for v in args.dwell_thetas.split(","))
+        for theta in th_list:
             o = series(cfg, theta, rule, prec)
             row = {"mode": "dwell", "basis": basis, "radius": name, "theta": theta,
                    "precision": "fp32mix" if prec == pq.FP32MIX else "fp64",
@@ -738,6 +741,7 @@ def main():
     ap.add_argument("--snapshots", default="0,20,50,100")   # steps of --mode snapshot
     ap.add_argument("--dwell-bases", default="")   # comma list of fgh,pw,pvb (default fgh,pw)
     ap.add_argument("--dwell-pvb-fp32", action="store_true")   # the pvB column in FP32-mix
+    ap.add_argument("--dwell-thetas", default="")   # comma list replacing the thresholds of --mode dwell
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("need at least 3 warm-up steps")
