@@ -487,9 +487,17 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
         }
         return PQ_OK;
     };
+    // <v, x>; a failed reduction leaves its status in dot_rc and returns NaN,
+    // which the finiteness checks below turn into an error
+    pq_status dot_rc = PQ_OK;
     auto dot1 = [&](const double2* v, const double2* x) -> cd {
         std::vector<cd> o;
-        return mdot(v, 1, x, o) ? cd(NAN, NAN) : o[0];
+        const pq_status r = mdot(v, 1, x, o);
+        if (r) {
+            if (!dot_rc) dot_rc = r;
+            return cd(NAN, NAN);
+        }
+        return o[0];
     };
     auto pack = [&](const std::vector<cd>& c, int i0, int m, cd scale, bool conjugate) {
         Coefs cf;
@@ -538,11 +546,13 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
     // eigenbasis (divided differences of exp(-i z dt)).
     auto step_vjp = [&](const double2* a) -> pq_status {
         double2* ybar = (double2*)B.psi;
-        const double b0 = sqrt(std::max(0.0, dot1(a, a).real()));
-        if (!std::isfinite(b0)) {
+        const double n0 = dot1(a, a).real();
+        if (dot_rc) return dot_rc;
+        if (!std::isfinite(n0)) {
             set_error("non-finite state in the gradient's reverse sweep");
             return PQ_ENUMERIC;
         }
+        const double b0 = sqrt(std::max(0.0, n0));
         if (!(b0 > 0.0)) return PQ_OK;   // zero state: the step is the identity
         const Coefs none{};
         pq_status r;
@@ -561,9 +571,11 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
             if (k == K - 1) break;
             if ((r = mcomb(vk(Vv, k + 1), vk(Wv, k), 1.0, vk(Vv, 0), k + 1, pack(c[k], 0, k + 1, -1.0, false))))
                 return r;
-            const double b = sqrt(std::max(0.0, dot1(vk(Vv, k + 1), vk(Vv, k + 1)).real()));
-            const double hn = sqrt(std::max(0.0, dot1(vk(Wv, k), vk(Wv, k)).real()));
-            if (!std::isfinite(b) || !std::isfinite(alpha[k])) {
+            const double b2 = dot1(vk(Vv, k + 1), vk(Vv, k + 1)).real();
+            const double h2 = dot1(vk(Wv, k), vk(Wv, k)).real();
+            if (dot_rc) return dot_rc;
+            const double b = sqrt(std::max(0.0, b2)), hn = sqrt(std::max(0.0, h2));
+            if (!std::isfinite(b2) || !std::isfinite(h2) || !std::isfinite(alpha[k])) {
                 set_error("non-finite Lanczos scalars in the gradient's reverse sweep");
                 return PQ_ENUMERIC;
             }
@@ -632,6 +644,7 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
             if (!last) {
                 const double b = beta[k];
                 const double rr = dot1(vk(Vv, k + 1), vk(Vb, k + 1)).real();
+                if (dot_rc) return dot_rc;
                 const double bebar = Tbar[(size_t)k * Ke + k + 1] + Tbar[(size_t)(k + 1) * Ke + k];
                 Coefs cv{};
                 cv.c[0] = make_double2(bebar - rr / b, 0.0);
@@ -664,6 +677,7 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
         }
         // abar = Vbar_0/b0 + (b0bar - Re<V_0, Vbar_0>/b0) V_0
         const double r0 = dot1(vk(Vv, 0), vk(Vb, 0)).real();
+        if (dot_rc) return dot_rc;
         Coefs cv{};
         cv.c[0] = make_double2(b0bar - r0 / b0, 0.0);
         return mcomb((double2*)B.psi, vk(Vb, 0), 1.0 / b0, vk(Vv, 0), 1, cv);
@@ -711,6 +725,11 @@ pq_status survival_grad(State& s, const pq_prop_desc& d, int nsteps, int ckpt,
         if ((rc = packet_dots_on(B, B.psi, pd))) return rc;
         for (int cc = 0; cc < ncen; ++cc) grad[cen_idx[cc]] += std::real(pd[1 + cc]);
     }
+    for (int q = 0; q < np; ++q)
+        if (!std::isfinite(grad[q])) {
+            set_error("non-finite gradient component %d", q);
+            return PQ_ENUMERIC;
+        }
     if (P_out) *P_out = std::norm(C);
     // leave the state at its initial packet
     if ((rc = init_bits_from_packet(s, s.theta, st)) || (rc = set_psi_from_packet(s, st))) return rc;
