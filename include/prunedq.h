@@ -284,16 +284,16 @@ pq_status pq_timing_get(pq_state* state, double* apply_ms, int64_t* n_apply,
  * packet.  The paper computes C(t) only; the gradient is taken of that
  * quantity.  The run starts from the state's initial packet and adaption;
  * the sequence of active sets of that run is recorded and then held fixed
- * (the map is differentiable only with the sets frozen).  Backward sweep
- * with adjoint vectors, lambda_n = exp(+i H_{A_n} dt) R_n^T lambda_{n+1},
- * psi_n recomputed from checkpoints taken every `ckpt_every` steps; the
- * time integral of <lambda| dH/dtheta |psi> over each step by 5-point
- * Gauss-Legendre with SIL propagators (negative times for the adjoint).
- * Precision: the forward run (sets, checkpoints, C, P) in the state's
- * precision; for a PQ_FP32MIX state the backward sweep (adjoint kets, the
- * recomputed kets from the exactly widened checkpoints, the integrands) runs
- * on an internal FP64 copy of the state, so the gradient is that of the FP32
- * run's frozen sets without FP32 rounding in the time integrals.
+ * (the map is differentiable only with the sets frozen).  The gradient is
+ * that of the discrete propagation: a reverse sweep through every SIL step
+ * (its Lanczos recurrence repeated in FP64 and run backwards, the derivative
+ * of the tridiagonal exponential in its eigenbasis), psi_n recomputed from
+ * checkpoints taken every `ckpt_every` steps, so it agrees with finite
+ * differences of the propagation whether or not the step has converged.
+ * Precision: the forward run (sets, C, P) in the state's precision; for a
+ * PQ_FP32MIX state an internal FP64 copy of the state replays the run on its
+ * recorded sets for the checkpoints, and the reverse sweep is FP64.
+ * Errors: PQ_ENUMERIC for a non-finite Lanczos scalar or gradient.
  * Parameters:
  *   PQ_PARAM_POTENTIAL  dH/dtheta as diagonal SoP terms on the DVR grid
  *                       (PQ_FACTOR_DIAG / PQ_FACTOR_IDENTITY factors);
