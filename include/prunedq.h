@@ -229,8 +229,13 @@ pq_status pq_prune(pq_state* state, double theta, int radius, double rel_excl, v
  * observables of the new state: t, C(t) = <Psi(0)|Psi(t)>, ||psi||^2,
  * E = Re<psi|H psi>/||psi||^2, |A|, and the number of active points with
  * |a| < theta.  Observables accumulate in the state (pq_observables_get).
- * Asynchronous except for one synchronisation at the end that reads the
- * device error word. */
+ * PQ_FP32MIX states: the SIL step keeps the norm in exact arithmetic, so the
+ * run carries in FP64 the norm each step's output should have (following the
+ * adaption) and folds the correction into the next step's combination
+ * coefficients; FP32 rounding then no longer adds up into a norm drift.
+ * Asynchronous except for one synchronisation at the start and one at the
+ * end that reads the device error word (and non-blocking reads of the set
+ * size that choose between two H.psi paths of equal results). */
 typedef struct pq_prop_desc {
     int K;           /* Krylov dimension (H.psi products per step), 1..32     */
     double dt;       /* time step                                            */
