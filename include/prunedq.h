@@ -235,7 +235,7 @@ pq_status pq_prune(pq_state* state, double theta, int radius, double rel_excl, v
  * coefficients; FP32 rounding then no longer adds up into a norm drift.
  * Asynchronous except for one synchronisation at the start and one at the
  * end that reads the device error word (and non-blocking reads of the set
- * size that choose between two H.psi paths of equal results). */
+ * size that choose between two H.psi paths, equal up to rounding). */
 typedef struct pq_prop_desc {
     int K;           /* Krylov dimension (H.psi products per step), 1..32     */
     double dt;       /* time step                                            */
