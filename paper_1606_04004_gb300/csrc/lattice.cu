@@ -488,8 +488,17 @@ pq_status init_bits_from_packet(State& s, double theta, cudaStream_t st) {
     return rebuild_from_bits(s, false, st);
 }
 
+pq_status reset_norm_keeping(State& s, cudaStream_t st) {
+    if (s.ks)
+        PQ_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(s.ks) + offsetof(KrylovScalars, renorm), 0,
+                                    3 * sizeof(double), st));
+    return PQ_OK;
+}
+
 pq_status set_psi_from_packet(State& s, cudaStream_t st) {
     const int G = grid_size() * 8;
+    pq_status rc = reset_norm_keeping(s, st);   // a new state: no pending correction
+    if (rc) return rc;
     if (s.prec == PQ_FP64)
         k_packet_on_set<double2><<<G, 256, 0, st>>>(s.keys, s.cnt + CNT_NA, (int64_t)s.cap,
                                                     s.lat, (const double2*)s.fac64,
@@ -513,9 +522,10 @@ __global__ void k_set_bits(const uint32_t* __restrict__ keys, int64_t n, uint64_
 pq_status load_set(State& s, const uint32_t* d_keys, int64_t n, cudaStream_t st, bool remap) {
     const Lattice& L = s.lat;
     s.dense_hint = 2 * n >= (int64_t)L.nfull ? 1 : 0;
-    if (!remap && s.ks)   // new coefficients: no pending FP32-mix norm correction
-        PQ_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(s.ks) + offsetof(KrylovScalars, renorm), 0,
-                                    3 * sizeof(double), st));
+    if (!remap) {   // new coefficients: no pending FP32-mix norm correction
+        pq_status rc = reset_norm_keeping(s, st);
+        if (rc) return rc;
+    }
     if (!remap) PQ_CUDA_TRY(cudaMemsetAsync(s.cnt + CNT_ERR, 0, sizeof(int64_t), st));
     PQ_CUDA_TRY(cudaMemsetAsync(s.bits_alt, 0, (size_t)L.nwords * 8, st));
     if (n > 0) {

@@ -256,6 +256,9 @@ pq_status check_neighbour_rule(const Lattice& L, int radius);
 pq_status prune_launch(State& s, double theta, int radius, double rel_excl, cudaStream_t st);
 pq_status init_bits_from_packet(State& s, double theta, cudaStream_t st);
 pq_status set_psi_from_packet(State& s, cudaStream_t st);
+// FP32-mix norm keeping (see krylov.cu): forget the target norm and the pending
+// correction (the coefficients were replaced)
+pq_status reset_norm_keeping(State& s, cudaStream_t st);
 // Replace the active set by n sorted keys on the device; with remap the
 // current coefficients are carried over (kept where the point stays, zero
 // where it is new), else they are left undefined.

@@ -111,3 +111,23 @@ def test_autograd_function():
     P.backward()
     _, g = _gpu_grad(cfg, 0, 2)
     np.testing.assert_allclose(theta.grad.numpy(), g, rtol=1e-12, atol=0)
+
+
+def test_adjoint_fp32_after_propagation_matches_fresh_state():
+    """An FP32-mix state that was propagated before gives the same P and
+    gradient as a fresh one: the gradient's run restarts from the packet, and
+    the norm keeping of the earlier propagation does not carry over."""
+    pq = lib()
+    cfg = _reduced(4)
+    b = pq.build_model(cfg)
+    grids = [b.grid(k)[0] for k in range(cfg["D"])]
+    derivs = pq.henon_heiles_param_derivs(grids, cfg["lam"])
+    res = []
+    for warm in (0, 30):
+        s = pq.State(b, cfg["q0"], cfg["p0"], cfg["width"], cfg["theta"], precision=pq.FP32MIX)
+        if warm:
+            s.propagate(cfg["K"], cfg["dt"], cfg["theta"], warm)
+        res.append(s.survival_grad(cfg["K"], cfg["dt"], cfg["theta"], cfg["nsteps"], 2, derivs))
+        s.free()
+    assert res[0][0] == res[1][0]
+    np.testing.assert_array_equal(res[0][1], res[1][1])
