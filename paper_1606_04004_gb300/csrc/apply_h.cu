@@ -1720,13 +1720,13 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
 
 // Stage points [c0, c0 + n) of a lattice row with row-table entry ri at sdst
 // (16-byte aligned, n even), zero where inactive: 16-byte copies when the span
-// is fully active and starts on an even position, else one 8-byte copy (or
-// zero fill) per point.
+// is fully active and its source address is 16-byte aligned, else one 8-byte
+// copy (or zero fill) per point.
 __device__ __forceinline__ void stage_row(float2* sdst, const float2* in, uint2 ri, int c0, int n) {
     const uint32_t full = n >= 32 ? ~0u : (1u << n) - 1u;
     const uint32_t m = (ri.y >> c0) & full;
     uint32_t pos = ri.x + (uint32_t)__popc(ri.y & ((1u << c0) - 1u));
-    if (m == full && !(pos & 1u)) {
+    if (m == full && !(reinterpret_cast<uintptr_t>(in + pos) & 15u)) {
         for (int h = 0; h < n / 2; ++h) cp_async16(sdst + 2 * h, in + pos + 2 * h);
         return;
     }
@@ -1867,7 +1867,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_inner(ApplyArgs<float> 
                 }
             }
             // potential; active outputs only, 16-byte stores for four active
-            // points that start on an even position
+            // points at a 16-byte aligned address
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const uint2 ri = R[p * n2 + i0 + r];
@@ -1884,7 +1884,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_inner(ApplyArgs<float> 
                     acc[r][q].y *= scale;
                 }
                 uint32_t pos = ri.x + (uint32_t)__popc(ri.y & ((1u << c0) - 1u));
-                if (mk == 0xFu && !(pos & 1u)) {
+                if (mk == 0xFu && !(reinterpret_cast<uintptr_t>(a.out + pos) & 15u)) {
                     st4(a.out + pos, acc[r]);
                 } else {
 #pragma unroll
@@ -1998,8 +1998,8 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_pair(ApplyArgs<float> a
             }
             // y += scale acc on the active points, two rows at a time with both
             // rows' loads before their stores (the positions are distinct);
-            // 16-byte accesses for four active points that start on an even
-            // position
+            // 16-byte accesses for four active points at a 16-byte aligned
+            // address
             const int cc = c0 + cq;
 #pragma unroll
             for (int r0 = 0; r0 < 4; r0 += 2) {
@@ -2010,7 +2010,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_pair(ApplyArgs<float> a
                     const uint2 ri = R[(a0 + r0 + h) * nb + rb];
                     mk[h] = (ri.y >> cc) & 0xFu;
                     pos0[h] = ri.x + (uint32_t)__popc(ri.y & ((1u << cc) - 1u));
-                    if (mk[h] == 0xFu && !(pos0[h] & 1u)) {
+                    if (mk[h] == 0xFu && !(reinterpret_cast<uintptr_t>(a.out + pos0[h]) & 15u)) {
                         ld4(a.out + pos0[h], y[h]);
                     } else {
                         uint32_t pp = pos0[h];
@@ -2026,7 +2026,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_pair(ApplyArgs<float> a
                         y[h][q].x = fmaf(scale, acc[r0 + h][q].x, y[h][q].x);
                         y[h][q].y = fmaf(scale, acc[r0 + h][q].y, y[h][q].y);
                     }
-                    if (mk[h] == 0xFu && !(pos0[h] & 1u)) {
+                    if (mk[h] == 0xFu && !(reinterpret_cast<uintptr_t>(a.out + pos0[h]) & 15u)) {
                         st4(a.out + pos0[h], y[h]);
                     } else {
                         uint32_t pp = pos0[h];

@@ -198,6 +198,30 @@ def test_apply_dense_set_from_packet(dims):
     assert np.all(err <= TOL[1] * bound + 1e-300), (err / np.maximum(bound, 1e-300)).max()
 
 
+@pytest.mark.parametrize("dims", [(4, 8, 4, 8, 8, 8), (8, 12, 16, 24)])
+def test_apply_dense_set_unaligned_vectors(dims):
+    """Input and output views starting 8 bytes past a 16-byte boundary (the
+    dense-tile passes take 16-byte copies only where the address allows):
+    the same result as aligned vectors, element for element."""
+    import torch
+    pq = lib()
+    b, Ts, pot = ho_problem(dims, 23, 3)
+    A = np.arange(int(np.prod(dims)), dtype=np.int64)
+    psi = W.random_psi(len(A), 29).astype(np.complex64)
+    s = state_with(b, A, psi, pq.FP32MIX)
+    x = torch.from_numpy(psi).to("cuda")
+    y = torch.empty_like(x)
+    s.apply_H(x, y)
+    xb = torch.zeros(len(A) + 1, dtype=torch.complex64, device="cuda")
+    yb = torch.zeros(len(A) + 1, dtype=torch.complex64, device="cuda")
+    xu, yu = xb[1:], yb[1:]
+    xu.copy_(x)
+    assert xu.data_ptr() % 16 == 8 and yu.data_ptr() % 16 == 8
+    s.apply_H(xu, yu)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(yu.cpu().numpy(), y.cpu().numpy())
+
+
 def test_apply_hh6d_full_lattice_sampled():
     """The 6D Henon-Heiles Hamiltonian on the whole 24^6 lattice (the set the
     propagation reaches after about 100 steps), FP32, in the launch
