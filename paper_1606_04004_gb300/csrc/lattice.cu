@@ -238,7 +238,13 @@ pq_status rebuild_tables(State& s, cudaStream_t st) {
         PQ_CUDA_TRY(cudaMemsetAsync(s.cnt + CNT_LEAD0, 0, sizeof(int64_t) * (kMaxD - 1), st));
         return PQ_OK;
     }
-    for (int k = 0; k + 1 < L.D; ++k) {   // fibre leaders of every mode but the last
+    // fibre leaders of every mode but the last; a DVR Hamiltonian's passes take
+    // mode D-2 in the inner pass (planes), so its leaders serve only the
+    // generic (phase-space) passes
+    const int kend = s.generic ? L.D - 1 : L.D - 2;
+    PQ_CUDA_TRY(cudaMemsetAsync(s.cnt + CNT_LEAD0 + std::max(kend, 0), 0,
+                                sizeof(int64_t) * (size_t)(L.D - 1 - std::max(kend, 0)), st));
+    for (int k = 0; k < kend; ++k) {
         OpLeaders ol{s.rows, s.cnt + CNT_ROWS, s.bits, s.leaders + (size_t)k * s.rows_cap,
                      L.rstride[k], L.n[k], L.nlast, s.rows_cap, s.cnt};
         if ((rc = run_scan(ol, s.scan_tmp, s.cnt + CNT_LEAD0 + k, -1, nullptr, 0, st))) return rc;
