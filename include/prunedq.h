@@ -47,7 +47,7 @@ typedef enum pq_status {
     PQ_ENUMERIC = 5,    /* NaN / Inf met in a norm or Lanczos coefficient     */
     PQ_ETIMEOUT = 6,    /* a bounded device wait ran out                      */
     PQ_EBREAKDOWN = 7,  /* Lanczos breakdown where it is not allowed          */
-    PQ_ENOTSUP = 8      /* valid request that this build does not implement   */
+    PQ_ENOTSUP = 8      /* valid request that the library does not implement */
 } pq_status;
 
 typedef enum pq_basis_kind {
