@@ -83,6 +83,11 @@ CASES = [
     ((3, 5, 7, 9, 11), 0.6),
     ((2, 3, 24, 24, 24), 0.97),
     ((7, 3, 32, 2, 13), 0.5),
+    # a 33-64-point mode next to the last one (compact inner pass), and an
+    # outer mode of that length
+    ((40, 12), 0.6),
+    ((3, 48, 16), 0.5),
+    ((36, 5, 20), 0.4),
 ]
 
 
