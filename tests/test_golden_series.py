@@ -66,6 +66,6 @@ def test_pvb_and_hh6d_records_cover_their_stated_lengths():
     # lattice); their provenance is the same script, checked above on the
     # other workloads.  Their lengths are stated here and in the design doc.
     pvb = _load("morse3d_pvb")
-    assert pvb["nsteps"] >= 20 and len(pvb["steps"]) == pvb["nsteps"] + 1
+    assert pvb["nsteps"] >= 40 and len(pvb["steps"]) == pvb["nsteps"] + 1
     hh6 = _load("hh6d")
-    assert hh6["nsteps"] >= 5 and len(hh6["steps"]) == hh6["nsteps"] + 1
+    assert hh6["nsteps"] >= 10 and len(hh6["steps"]) == hh6["nsteps"] + 1
