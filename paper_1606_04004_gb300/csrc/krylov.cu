@@ -265,33 +265,48 @@ __global__ void __launch_bounds__(kRedThreads) k_update(const void* psi, const v
     }
 }
 
-// Launch k_dots / k_update for a run-time count m in [1, kMaxM].
-template <typename R, int M = 1>
-static void launch_dots(int m, int G, cudaStream_t st, const void* psi, const void* Vb,
-                        size_t cap, const typename Cx<R>::T* W, const int64_t* na, int i0,
-                        const KrylovScalars* ks, int k, double* partials) {
-    if constexpr (M < kMaxM) {
-        if (m != M) {
-            launch_dots<R, M + 1>(m, G, st, psi, Vb, cap, W, na, i0, ks, k, partials);
-            return;
-        }
+// Grid of a grid-stride reduction kernel: at most G blocks, and no more than
+// fit on the GPU at once (the kernel's occupancy x SMs), so that a launch is
+// one full wave, with no partly filled second wave, and fewer partials to sum.
+template <typename F>
+static int one_wave_grid(F kernel, int G) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRedThreads, 0) !=
+            cudaSuccess ||
+        per_sm <= 0) {
+        cudaGetLastError();   // clear the query's error; keep the default grid
+        return G;
     }
-    k_dots<R, M><<<G, kRedThreads, 0, st>>>(psi, Vb, cap, W, na, i0, ks, k, partials);
+    return std::max(1, std::min(G, per_sm * grid_size()));
+}
+
+// Launch k_dots / k_update for a run-time count m in [1, kMaxM] on at most G
+// blocks; returns the block count used (the row count of the partials).
+template <typename R, int M = 1>
+static int launch_dots(int m, int G, cudaStream_t st, const void* psi, const void* Vb,
+                       size_t cap, const typename Cx<R>::T* W, const int64_t* na, int i0,
+                       const KrylovScalars* ks, int k, double* partials) {
+    if constexpr (M < kMaxM) {
+        if (m != M) return launch_dots<R, M + 1>(m, G, st, psi, Vb, cap, W, na, i0, ks, k, partials);
+    }
+    static const int g = one_wave_grid(k_dots<R, M>, G);
+    k_dots<R, M><<<g, kRedThreads, 0, st>>>(psi, Vb, cap, W, na, i0, ks, k, partials);
+    return g;
 }
 
 template <typename R, int M = 1>
-static void launch_update(int m, int G, cudaStream_t st, const void* psi, const void* Vb,
-                          size_t cap, typename Cx<R>::T* W, const int64_t* na, int i0,
-                          const KrylovScalars* ks, int k, int want_norm, double* partials) {
+static int launch_update(int m, int G, cudaStream_t st, const void* psi, const void* Vb,
+                         size_t cap, typename Cx<R>::T* W, const int64_t* na, int i0,
+                         const KrylovScalars* ks, int k, int want_norm, double* partials) {
     if constexpr (M < kMaxM) {
-        if (m != M) {
-            launch_update<R, M + 1>(m, G, st, psi, Vb, cap, W, na, i0, ks, k, want_norm,
-                                    partials);
-            return;
-        }
+        if (m != M)
+            return launch_update<R, M + 1>(m, G, st, psi, Vb, cap, W, na, i0, ks, k, want_norm,
+                                           partials);
     }
-    k_update<R, M><<<G, kRedThreads, 0, st>>>(psi, Vb, cap, W, na, i0, ks, k, want_norm,
+    static const int g = one_wave_grid(k_update<R, M>, G);
+    k_update<R, M><<<g, kRedThreads, 0, st>>>(psi, Vb, cap, W, na, i0, ks, k, want_norm,
                                                partials);
+    return g;
 }
 
 // beta_k = ||W||; breakdown test; sigma_{k+1} = 1/beta_k.
@@ -636,20 +651,22 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
         else if (!d.reorth) i0 = k > 0 ? k - 1 : 0;
         for (int c0 = i0; c0 <= k; c0 += kMaxM) {
             const int m = min(kMaxM, k - c0 + 1);
-            launch_dots<R>(m, G, st, s.psi, s.V, cap, W, s.cnt + CNT_NA, c0, s.ks, k, s.red_tmp);
+            const int g = launch_dots<R>(m, G, st, s.psi, s.V, cap, W, s.cnt + CNT_NA, c0, s.ks,
+                                         k, s.red_tmp);
             PQ_CHECK_LAUNCH();
-            k_dots_done<<<1, 256, 0, st>>>(s.red_tmp, G, c0, m, s.ks, k, prev_E, s.cnt + CNT_ERR);
+            k_dots_done<<<1, 256, 0, st>>>(s.red_tmp, g, c0, m, s.ks, k, prev_E, s.cnt + CNT_ERR);
             PQ_CHECK_LAUNCH();
         }
         if (k == K - 1) break;
+        int g_norm = G;   // blocks of the update that summed ||W||^2
         for (int c0 = i0; c0 <= k; c0 += kMaxM) {
             const int m = min(kMaxM, k - c0 + 1);
             const bool last = c0 + m > k;
-            launch_update<R>(m, G, st, s.psi, s.V, cap, W, s.cnt + CNT_NA, c0, s.ks, k,
-                             last ? 1 : 0, s.red_tmp);
+            g_norm = launch_update<R>(m, G, st, s.psi, s.V, cap, W, s.cnt + CNT_NA, c0, s.ks, k,
+                                      last ? 1 : 0, s.red_tmp);
             PQ_CHECK_LAUNCH();
         }
-        k_update_done<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks, k, s.cnt + CNT_ERR);
+        k_update_done<<<1, 256, 0, st>>>(s.red_tmp, g_norm, s.ks, k, s.cnt + CNT_ERR);
         PQ_CHECK_LAUNCH();
         if (d.sil_tol > 0.0) {
             k_sil_errcheck<<<1, 32, 0, st>>>(s.ks, k, d.dt, d.sil_tol);
