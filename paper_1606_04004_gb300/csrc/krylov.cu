@@ -479,17 +479,35 @@ __global__ void __launch_bounds__(kRedThreads) k_combine(void* psi, const void* 
                                                           const int64_t* na,
                                                           const KrylovScalars* ks, double* partials) {
     using V = typename Cx<R>::T;
+    constexpr int kBatch = 4;   // vector loads in flight per thread
+    __shared__ R sc[2 * kMaxK];
     const int n_k = ks->keff;
     if (n_k <= 0) return;   // uniform; the norm keeping then ignores the partials
+    for (int j = threadIdx.x; j < 2 * n_k; j += blockDim.x) sc[j] = (R)ks->coef[j];
+    __syncthreads();
     const int64_t n = min(*na, (int64_t)cap);
     Acc<R> an;
     an.init();
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         R ax = 0, ay = 0;
-        for (int j = 0; j < n_k; ++j) {
+        // j ascending, as a plain loop would sum; the loads of a batch issue
+        // before its products
+        int j = 0;
+        for (; j + kBatch <= n_k; j += kBatch) {
+            V v[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) v[u] = kvec<R>(psi, Vb, cap, j + u)[p];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const R cr = sc[2 * (j + u)], ci = sc[2 * (j + u) + 1];
+                ax += cr * v[u].x - ci * v[u].y;
+                ay += cr * v[u].y + ci * v[u].x;
+            }
+        }
+        for (; j < n_k; ++j) {
             const V v = kvec<R>(psi, Vb, cap, j)[p];
-            const R cr = (R)ks->coef[2 * j], ci = (R)ks->coef[2 * j + 1];
+            const R cr = sc[2 * j], ci = sc[2 * j + 1];
             ax += cr * v.x - ci * v.y;
             ay += cr * v.y + ci * v.x;
         }
@@ -677,11 +695,12 @@ static pq_status sil_step(State& s, const pq_prop_desc& d, double* prev_E, cudaS
     PQ_CHECK_LAUNCH();
     // FP32-mix: the combination also sums the output's norm for the next step's
     // norm correction
-    k_combine<R><<<G, kRedThreads, 0, st>>>(s.psi, s.V, cap, s.cnt + CNT_NA, s.ks,
-                                            sizeof(R) == 4 ? s.red_tmp : nullptr);
+    static const int g_comb = one_wave_grid(k_combine<R>, G);
+    k_combine<R><<<g_comb, kRedThreads, 0, st>>>(s.psi, s.V, cap, s.cnt + CNT_NA, s.ks,
+                                                 sizeof(R) == 4 ? s.red_tmp : nullptr);
     PQ_CHECK_LAUNCH();
     if (sizeof(R) == 4) {
-        k_renorm_factor<<<1, 256, 0, st>>>(s.red_tmp, G, s.ks);
+        k_renorm_factor<<<1, 256, 0, st>>>(s.red_tmp, g_comb, s.ks);
         PQ_CHECK_LAUNCH();
     }
     return PQ_OK;
