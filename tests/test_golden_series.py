@@ -64,9 +64,9 @@ def test_adjoint_record_is_the_oracle_run():
 def test_pvb_and_hh6d_records_cover_their_stated_lengths():
     # recomputing these takes an hour or more (full-grid conjugate gradients, a
     # 24^6 lattice); their provenance is the same script, checked above on the
-    # other workloads.  The lengths asserted here: pvB 40 steps, hh6d 20 (the
+    # other workloads.  The lengths asserted here: pvB 60 steps, hh6d 20 (the
     # window the hh6d benchmark times, steps 3-23, up to step 20).
     pvb = _load("morse3d_pvb")
-    assert pvb["nsteps"] >= 40 and len(pvb["steps"]) == pvb["nsteps"] + 1
+    assert pvb["nsteps"] >= 60 and len(pvb["steps"]) == pvb["nsteps"] + 1
     hh6 = _load("hh6d")
     assert hh6["nsteps"] >= 20 and len(hh6["steps"]) == hh6["nsteps"] + 1
